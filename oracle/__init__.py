@@ -1,0 +1,265 @@
+"""FP64 CPU oracle for two-point ray tracing: ctypes wrapper around oracle.c.
+
+TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use it; the library never does. It shares no code
+with the CUDA path. The C source is compiled on first use (gcc, OpenMP,
+``-ffp-contract=off`` so that x86 and Arm hosts round identically).
+
+Every function takes plain numpy arrays in the library's units: lengths in mm,
+sound speed in m/s, times in us.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "oracle.c")]
+_HDR = os.path.join(_HERE, "oracle.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RAY_OK, RAY_MAXITER, RAY_STEPCAP, RAY_BADINPUT = 0, 1, 2, 4
+
+
+def compile_to(out_path: str, sources=None) -> str:
+    """gcc-compile the oracle sources (default: oracle.c) into a shared library."""
+    sources = list(sources or _SRC)
+    tmp = out_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-Wall", "-I", _HERE, "-o", tmp] + sources + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out_path)
+    return out_path
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so if missing or stale; returns its path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _SRC + [_HDR])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    return compile_to(_LIB_PATH)
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("h", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double)]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+
+
+def load(path: str):
+    """Open an oracle shared library and declare its C signatures."""
+    L = C.CDLL(path)
+    G = C.POINTER(_Grid)
+    L.orc_field.argtypes = [G, _dp, _dp, _dp, _dp, _dp]
+    L.orc_sample.argtypes = [G, _dp, C.c_int32, _dp, _dp]
+    L.orc_march.argtypes = [G, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                            C.c_int32, _dp]
+    L.orc_trace.argtypes = [G, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                            C.c_double, C.c_double, C.c_double, C.c_int64, _dp, _dp,
+                            _lp, _dp, _ip]
+    L.orc_link.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
+                           C.c_double, C.c_double, C.c_int32, _dp, _dp, _dp, _ip, _ip,
+                           C.c_int32]
+    L.orc_tof.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip, C.c_double,
+                          _dp, _dp, _dp, C.c_int32]
+    L.orc_path_matrix.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
+                                  C.c_double, _dp, _lp, _ip, _dp, C.c_int64, C.c_int32]
+    L.orc_path_matrix.restype = C.c_int64
+    L.orc_adjoint.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
+                              C.c_double, _dp, _dp, _dp, C.c_int32]
+    L.orc_num_threads.argtypes = []
+    return L
+
+
+_current = None
+
+
+def lib():
+    """The library the functions below call (the built oracle unless overridden)."""
+    global _lib
+    with _lock:
+        if _current is not None:
+            return _current
+        if _lib is None:
+            _lib = load(build())
+    return _lib
+
+
+class using:
+    """Context manager: route the functions below to another oracle library
+    (used by the mutation tests, which compile deliberately broken copies)."""
+
+    def __init__(self, L):
+        self.L = L
+
+    def __enter__(self):
+        global _current
+        self.prev, _current = _current, self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _current
+        _current = self.prev
+
+
+def _grid(grid) -> _Grid:
+    return _Grid(int(grid.nx), int(grid.ny), float(grid.h), float(grid.x0), float(grid.y0))
+
+
+def _d(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return None if a is None else a.ctypes.data_as(_ip)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def field(grid, c_mps):
+    """Nodal (c, dc/dx, dc/dy, s) in mm/us units, each [ny, nx]."""
+    c = _f64(c_mps)
+    outs = [np.empty_like(c) for _ in range(4)]
+    g = _grid(grid)
+    _check(lib().orc_field(C.byref(g), _d(c), *[_d(o) for o in outs]), "field")
+    return tuple(outs)
+
+
+def sample(grid, c_mps, xy):
+    """Bilinear (c, dc/dx, dc/dy, s) at points xy[n, 2] -> [n, 4]."""
+    c = _f64(c_mps)
+    xy = _f64(xy).reshape(-1, 2)
+    out = np.empty((xy.shape[0], 4))
+    g = _grid(grid)
+    _check(lib().orc_sample(C.byref(g), _d(c), xy.shape[0], _d(xy), _d(out)), "sample")
+    return out
+
+
+def march(grid, c_mps, x, y, theta, ds, n_steps):
+    """Positions of n_steps fixed RK4 steps -> [n_steps+1, 2]."""
+    c = _f64(c_mps)
+    out = np.empty((n_steps + 1, 2))
+    g = _grid(grid)
+    _check(lib().orc_march(C.byref(g), _d(c), x, y, theta, ds, n_steps, _d(out)), "march")
+    return out
+
+
+def trace(grid, c_mps, R, xe, xr, theta, ds, record=True):
+    """One trace; returns dict(T, hit, dir, dsp, flags, pts, alpha)."""
+    c = _f64(c_mps)
+    cap = int(np.ceil(8.0 * R / ds)) + 2 if record else 0
+    pts = np.empty((max(cap, 1), 2))
+    alpha = np.empty(max(cap, 1))
+    n = C.c_int64(0)
+    out6 = np.empty(6)
+    flags = C.c_int32(0)
+    g = _grid(grid)
+    rc = lib().orc_trace(C.byref(g), _d(c), R, xe[0], xe[1], xr[0], xr[1], theta, ds, cap,
+                         _d(pts) if record else None, _d(alpha) if record else None,
+                         C.byref(n), _d(out6), C.byref(flags))
+    _check(rc, "trace")
+    res = dict(T=out6[0], hit=out6[1:3].copy(), dir=out6[3:5].copy(), dsp=out6[5],
+               flags=int(flags.value), n_pts=int(n.value))
+    if record:
+        res["pts"] = pts[: n.value].copy()
+        res["alpha"] = alpha[: n.value].copy()
+    return res
+
+
+def _pairs_arg(pairs, n_tx):
+    if pairs is None:
+        return None, n_tx * (n_tx - 1)
+    p = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    return p, p.shape[0]
+
+
+def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None, nthreads=0):
+    """Link all pairs; returns dict(theta, tof, hit, status, iters)."""
+    c = _f64(c_mps)
+    tx = _f64(tx).reshape(-1, 2)
+    p, n_pairs = _pairs_arg(pairs, tx.shape[0])
+    theta = np.full(n_pairs, np.nan) if theta0 is None else _f64(theta0).copy()
+    tof = np.empty(n_pairs)
+    hit = np.empty((n_pairs, 2))
+    status = np.empty(n_pairs, np.int32)
+    iters = np.empty(n_pairs, np.int32)
+    g = _grid(grid)
+    rc = lib().orc_link(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds, tol,
+                        max_iter, _d(theta), _d(tof), _d(hit), _i(status), _i(iters), nthreads)
+    _check(rc, "link")
+    return dict(theta=theta, tof=tof, hit=hit, status=status, iters=iters)
+
+
+def tof(grid, c_mps, tx, R, ds, theta, pairs=None, nthreads=0):
+    """Travel time and hit of every pair at fixed angles -> (tof, hit)."""
+    c = _f64(c_mps)
+    tx = _f64(tx).reshape(-1, 2)
+    p, n_pairs = _pairs_arg(pairs, tx.shape[0])
+    th = _f64(theta)
+    out = np.empty(n_pairs)
+    hit = np.empty((n_pairs, 2))
+    g = _grid(grid)
+    rc = lib().orc_tof(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds, _d(th),
+                       _d(out), _d(hit), nthreads)
+    _check(rc, "tof")
+    return out, hit
+
+
+def path_matrix(grid, c_mps, tx, R, ds, theta, pairs=None, nthreads=0):
+    """Explicit CSR system matrix -> (row_ptr, col, val) with T = L s."""
+    c = _f64(c_mps)
+    tx = _f64(tx).reshape(-1, 2)
+    p, n_pairs = _pairs_arg(pairs, tx.shape[0])
+    th = _f64(theta)
+    row_ptr = np.empty(n_pairs + 1, np.int64)
+    g = _grid(grid)
+    L = lib()
+    nnz = L.orc_path_matrix(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds,
+                            _d(th), row_ptr.ctypes.data_as(_lp), None, None, 0, nthreads)
+    if nnz < 0:
+        raise ValueError("oracle path_matrix failed")
+    col = np.empty(max(nnz, 1), np.int32)
+    val = np.empty(max(nnz, 1))
+    nnz2 = L.orc_path_matrix(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds,
+                             _d(th), row_ptr.ctypes.data_as(_lp), _i(col), _d(val), nnz, nthreads)
+    if nnz2 != nnz:
+        raise ValueError("oracle path_matrix changed size between passes")
+    return row_ptr, col[:nnz], val[:nnz]
+
+
+def adjoint(grid, c_mps, tx, R, ds, theta, g_tof, pairs=None, nthreads=0):
+    """d(sum g_tof*T)/dc per node in us/(m/s), rays frozen at theta -> [ny, nx]."""
+    c = _f64(c_mps)
+    tx = _f64(tx).reshape(-1, 2)
+    p, n_pairs = _pairs_arg(pairs, tx.shape[0])
+    th = _f64(theta)
+    gt = _f64(g_tof)
+    out = np.empty_like(c)
+    g = _grid(grid)
+    rc = lib().orc_adjoint(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds,
+                           _d(th), _d(gt), _d(out), nthreads)
+    _check(rc, "adjoint")
+    return out

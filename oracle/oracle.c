@@ -1,0 +1,659 @@
+/*
+ * FP64 CPU oracle for two-point ray tracing (ToF, system matrix, adjoint).
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the library. It shares no code with
+ * the CUDA path. Written for clarity, not speed: plain FP64, absolute
+ * coordinates, one ray per OpenMP iteration, every sample interpolated afresh.
+ *
+ * Where the paper (arXiv:2511.18511) is silent, the readings below are used
+ * (each is also listed in the design notes):
+ *   R1 gradient: dc/dx, dc/dy from grid values by central differences (one-sided
+ *      at edges), then interpolated bilinearly like c itself (Sec. 3.3.1: the
+ *      gradient is obtained by interpolating grid values, not by differentiating
+ *      the interpolant);
+ *   R2 out-of-grid samples clamp the cell index (never reached: the ring lies
+ *      inside the grid with a margin, which is checked);
+ *   R3 ray equations dx/ds = d, dd/ds = -(grad c - (grad c . d) d)/c (the
+ *      refractive-index form of Sec. 3.2.3 with n = c0/c), classic RK4 at fixed
+ *      ds, d renormalised after every step;
+ *   R4 a trace ends at the first step, after the first one, whose end lies on
+ *      or outside |x| = R; the last point is then replaced by the boundary
+ *      interception, reached by an RK4 step of length ds' <= ds (Sec. 4.2: last
+ *      point replaced, shortened last step). ds' starts from the chord-circle
+ *      root and takes two Newton corrections. A first step that already ends
+ *      outside means the ray left outward: its interception is the emitter;
+ *   R5 travel time = trapezoid rule over the sample points with the
+ *      interpolated nodal slowness (Sec. 4.2's acoustic-length formula with the
+ *      slowness in place of n), plus the first-order endpoint correction
+ *      s(x_M) d_M.(x_r - x_M) that follows from grad T = s d (Appendix,
+ *      grad T . grad T = c^-2); the correction is a weight on the last point,
+ *      so T = L s still holds exactly;
+ *   R6 linking (Sec. 3.4): misfit m = R (psi_hit - psi_r), the signed arc from
+ *      the receiver to the boundary interception (the discrepancy of the two in
+ *      the angular domain), with both angles measured counter-clockwise from
+ *      the emitter in [0, 2pi) so that m is continuous over the inward fan of
+ *      launch angles; converged when |x_hit - x_r| <= tol; first angle the
+ *      straight line to the receiver (Sec. 3.4.1) or a warm start, second from
+ *      the straight-chord slope dm/dtheta = 2R; the fan ends bracket the root;
+ *      then Secant updates from the two latest angles (Sec. 3.4, default) while
+ *      they stay inside the bracket, else Regula-Falsi (Sec. 3.4) with the
+ *      Illinois halving; at most max_iter traces; the reported ray is the
+ *      evaluated one closest to the receiver;
+ *   R7 adjoint: the rays are frozen at the linked angles (Fermat: the first
+ *      order path change does not move T), so the gradient is the transpose
+ *      of the system matrix whose rows are interpolation-weighted path lengths
+ *      (Sec. 3.1.1), chained with ds/dc = -1/c^2.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int nx, ny;
+    double h, x0, y0;
+    double *c, *gx, *gy, *s;
+} Field;
+
+static void field_free(Field* F) {
+    free(F->c); free(F->gx); free(F->gy); free(F->s);
+    memset(F, 0, sizeof(*F));
+}
+
+/* R1: nodal c (mm/us), central-difference gradient, slowness. */
+static int field_make(Field* F, const orc_grid* g, const double* c_mps) {
+    memset(F, 0, sizeof(*F));
+    if (!g || !c_mps || g->nx < 3 || g->ny < 3 || !(g->h > 0)) return ORC_EINVAL;
+    F->nx = g->nx; F->ny = g->ny; F->h = g->h; F->x0 = g->x0; F->y0 = g->y0;
+    size_t n = (size_t)g->nx * (size_t)g->ny;
+    F->c = malloc(n * sizeof(double)); F->gx = malloc(n * sizeof(double));
+    F->gy = malloc(n * sizeof(double)); F->s = malloc(n * sizeof(double));
+    if (!F->c || !F->gx || !F->gy || !F->s) { field_free(F); return ORC_ENOMEM; }
+    for (size_t k = 0; k < n; ++k) {
+        double v = c_mps[k];
+        if (!(v > 0) || !isfinite(v)) { field_free(F); return ORC_EINVAL; }
+        F->c[k] = v * 1e-3;
+        F->s[k] = 1.0 / F->c[k];
+    }
+    const int nx = F->nx, ny = F->ny;
+    const double h = F->h;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t k = (size_t)j * nx + i;
+            if (i == 0) F->gx[k] = (F->c[k + 1] - F->c[k]) / h;
+            else if (i == nx - 1) F->gx[k] = (F->c[k] - F->c[k - 1]) / h;
+            else F->gx[k] = (F->c[k + 1] - F->c[k - 1]) / (2.0 * h);
+            if (j == 0) F->gy[k] = (F->c[k + nx] - F->c[k]) / h;
+            else if (j == ny - 1) F->gy[k] = (F->c[k] - F->c[k - nx]) / h;
+            else F->gy[k] = (F->c[k + nx] - F->c[k - nx]) / (2.0 * h);
+        }
+    }
+    return ORC_OK;
+}
+
+/* Bilinear weights of the four vertices of the enclosing cell (R2 clamps). */
+typedef struct { size_t k[4]; double w[4]; } Stencil;
+
+static void stencil_at(const Field* F, double x, double y, Stencil* S) {
+    double u = (x - F->x0) / F->h, v = (y - F->y0) / F->h;
+    double fi = floor(u), fj = floor(v);
+    if (!(fi >= 0)) fi = 0;
+    if (fi > F->nx - 2) fi = F->nx - 2;
+    if (!(fj >= 0)) fj = 0;
+    if (fj > F->ny - 2) fj = F->ny - 2;
+    int i = (int)fi, j = (int)fj;
+    double tx = u - i, ty = v - j;
+    S->k[0] = (size_t)j * F->nx + i;        S->w[0] = (1 - tx) * (1 - ty);
+    S->k[1] = S->k[0] + 1;                  S->w[1] = tx * (1 - ty);
+    S->k[2] = S->k[0] + F->nx;              S->w[2] = (1 - tx) * ty;
+    S->k[3] = S->k[2] + 1;                  S->w[3] = tx * ty;
+}
+
+/* f = (c, dc/dx, dc/dy, s) at (x, y). */
+static void sample(const Field* F, double x, double y, double f[4]) {
+    Stencil S;
+    stencil_at(F, x, y, &S);
+    f[0] = f[1] = f[2] = f[3] = 0;
+    for (int q = 0; q < 4; ++q) {
+        f[0] += S.w[q] * F->c[S.k[q]];
+        f[1] += S.w[q] * F->gx[S.k[q]];
+        f[2] += S.w[q] * F->gy[S.k[q]];
+        f[3] += S.w[q] * F->s[S.k[q]];
+    }
+}
+
+/* R3: right-hand side of the ray equations for the state (x, y, dx, dy). */
+static void rhs(const Field* F, const double st[4], double k[4]) {
+    double f[4];
+    sample(F, st[0], st[1], f);
+    double gd = f[1] * st[2] + f[2] * st[3];
+    k[0] = st[2];
+    k[1] = st[3];
+    k[2] = -(f[1] - gd * st[2]) / f[0];
+    k[3] = -(f[2] - gd * st[3]) / f[0];
+}
+
+/* R3: one classic RK4 step of length hs, then d renormalised. */
+static void rk4(const Field* F, const double st[4], double hs, double out[4]) {
+    double k1[4], k2[4], k3[4], k4[4], t[4];
+    rhs(F, st, k1);
+    for (int q = 0; q < 4; ++q) t[q] = st[q] + 0.5 * hs * k1[q];
+    rhs(F, t, k2);
+    for (int q = 0; q < 4; ++q) t[q] = st[q] + 0.5 * hs * k2[q];
+    rhs(F, t, k3);
+    for (int q = 0; q < 4; ++q) t[q] = st[q] + hs * k3[q];
+    rhs(F, t, k4);
+    for (int q = 0; q < 4; ++q) out[q] = st[q] + hs / 6.0 * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
+    double n = sqrt(out[2] * out[2] + out[3] * out[3]);
+    out[2] /= n;
+    out[3] /= n;
+}
+
+/* R4: from an inside state st, the step length ds' in [0, ds] whose RK4 end
+ * lies on |x| = R: chord-circle root, then two Newton corrections. */
+static double land(const Field* F, const double st[4], double R, double ds, double out[4]) {
+    double b = st[0] * st[2] + st[1] * st[3];
+    double q = st[0] * st[0] + st[1] * st[1] - R * R;
+    double disc = b * b - q;
+    if (disc < 0) disc = 0;
+    double sq = sqrt(disc);
+    double t = (b >= 0) ? (-q) / (b + sq) : (sq - b);
+    if (!(t >= 0)) t = 0;
+    if (t > ds) t = ds;
+    for (int it = 0; it < 2; ++it) {
+        rk4(F, st, t, out);
+        double r = sqrt(out[0] * out[0] + out[1] * out[1]);
+        double drdt = (out[0] * out[2] + out[1] * out[3]) / r;
+        if (drdt > 0) t -= (r - R) / drdt;
+        if (!(t >= 0)) t = 0;
+        if (t > ds) t = ds;
+    }
+    rk4(F, st, t, out);
+    return t;
+}
+
+typedef struct {
+    double T, hit[2], dir[2], dsp;
+    int64_t n_pts;
+    int flags;
+} TraceRes;
+
+static int64_t step_cap(double R, double ds) { return (int64_t)ceil(8.0 * R / ds); }
+
+/* R4 + R5. pts/alpha (capacity cap) optional. */
+static void trace(const Field* F, double R, double xe, double ye, double xr, double yr,
+                  double theta, double ds, double* pts, double* alpha, int64_t cap,
+                  TraceRes* res) {
+    const int64_t maxstep = step_cap(R, ds);
+    double st[4] = {xe, ye, cos(theta), sin(theta)}, nx[4], f[4];
+    sample(F, st[0], st[1], f);
+    double s_prev = f[3];
+    double T = 0.0, dsp = ds;
+    int64_t m = 0;
+    int flags = 0;
+    if (pts && cap > 0) { pts[0] = st[0]; pts[1] = st[1]; }
+    for (;;) {
+        if (m >= maxstep) { flags |= 1; dsp = ds; break; }
+        rk4(F, st, ds, nx);
+        if (nx[0] * nx[0] + nx[1] * nx[1] >= R * R) {
+            if (m == 0) { flags |= 2; break; }
+            dsp = land(F, st, R, ds, nx);
+            sample(F, nx[0], nx[1], f);
+            T += dsp * 0.5 * (s_prev + f[3]);
+            s_prev = f[3];
+            memcpy(st, nx, sizeof(st));
+            ++m;
+            if (pts && m < cap) { pts[2 * m] = st[0]; pts[2 * m + 1] = st[1]; }
+            break;
+        }
+        sample(F, nx[0], nx[1], f);
+        T += ds * 0.5 * (s_prev + f[3]);
+        s_prev = f[3];
+        memcpy(st, nx, sizeof(st));
+        ++m;
+        if (pts && m < cap) { pts[2 * m] = st[0]; pts[2 * m + 1] = st[1]; }
+    }
+    double corr = 0.0;
+    if (flags & 2) {
+        /* left outward: no path; the interception is the emitter itself */
+        T = 0.0;
+        res->hit[0] = xe; res->hit[1] = ye;
+        res->dir[0] = cos(theta); res->dir[1] = sin(theta);
+        res->dsp = 0.0;
+        m = 0;
+    } else {
+        res->hit[0] = st[0]; res->hit[1] = st[1];
+        res->dir[0] = st[2]; res->dir[1] = st[3];
+        res->dsp = dsp;
+        if (!(flags & 1)) {
+            corr = st[2] * (xr - st[0]) + st[3] * (yr - st[1]);
+            T += s_prev * corr;
+        }
+    }
+    res->T = T;
+    res->n_pts = m + 1;
+    res->flags = flags;
+    if (alpha && cap >= m + 1) {
+        /* alpha_k = (l_k + l_{k+1})/2 with l_0 = l_{M+1} = 0, l_M = ds' */
+        for (int64_t k = 0; k <= m; ++k) {
+            double lk = (k == 0) ? 0.0 : ((k == m) ? res->dsp : ds);
+            double lk1 = (k == m) ? 0.0 : ((k + 1 == m) ? res->dsp : ds);
+            alpha[k] = 0.5 * (lk + lk1);
+        }
+        alpha[m] += corr;
+    }
+}
+
+static int ring_ok(const orc_grid* g, double R, double ds) {
+    if (!(R > 0) || !(ds > 0)) return 0;
+    double lo_x = g->x0, hi_x = g->x0 + (g->nx - 1) * g->h;
+    double lo_y = g->y0, hi_y = g->y0 + (g->ny - 1) * g->h;
+    double need = R + ds + g->h;
+    return (-need >= lo_x) && (need <= hi_x) && (-need >= lo_y) && (need <= hi_y);
+}
+
+static int pair_of(int32_t n_tx, const int32_t* pairs, int64_t k, int* e, int* r) {
+    if (pairs) { *e = pairs[2 * k]; *r = pairs[2 * k + 1]; }
+    else {
+        int64_t ee = k / (n_tx - 1), rr = k % (n_tx - 1);
+        *e = (int)ee; *r = (int)(rr + (rr >= ee));
+    }
+    return (*e >= 0 && *e < n_tx && *r >= 0 && *r < n_tx && *e != *r);
+}
+
+static int on_ring(const double* p, double R) {
+    double r = sqrt(p[0] * p[0] + p[1] * p[1]);
+    return fabs(r - R) <= 1e-9 * R;
+}
+
+typedef struct { double theta, m, dist; TraceRes tr; } Eval;
+
+static double mod_2pi(double a) { return a - 2.0 * M_PI * floor(a / (2.0 * M_PI)); }
+
+/* R6: misfit of one trace. psi = angle of the interception measured
+ * counter-clockwise from the emitter, in [0, 2pi); m = R (psi - psi_r), the
+ * signed arc from the receiver, unwrapped at the emitter so that it is
+ * continuous over the whole inward fan. A ray that left outward at once has no
+ * interception; it gets the value of the fan end it is closest to. */
+static void evaluate(const Field* F, double R, const double* xe, const double* xr, double phi_e,
+                     double psi_r, double th_lo, double th_hi, double psi_at_lo, double ds,
+                     double theta, Eval* E) {
+    E->theta = theta;
+    trace(F, R, xe[0], xe[1], xr[0], xr[1], theta, ds, NULL, NULL, 0, &E->tr);
+    double dx = E->tr.hit[0] - xr[0], dy = E->tr.hit[1] - xr[1];
+    E->dist = sqrt(dx * dx + dy * dy);
+    double psi;
+    if (E->tr.flags & 3) {
+        /* no interception (left outward at once, or still inside after the
+         * step cap, which near-tangent rays that circle back to the emitter
+         * can do): the fan-end value, and never the reported ray */
+        psi = (theta - th_lo < th_hi - theta) ? psi_at_lo : 2.0 * M_PI - psi_at_lo;
+        E->dist = INFINITY;
+    } else {
+        psi = mod_2pi(atan2(E->tr.hit[1], E->tr.hit[0]) - phi_e);
+    }
+    E->m = R * (psi - psi_r);
+}
+
+/* R6 linking of one pair: shooting over the inward fan of launch angles
+ * (phi_e + pi/2, phi_e + 3pi/2). Over that fan the interception sweeps the
+ * whole ring once, so the fan's two ends bracket the root; whether the sweep
+ * runs counter-clockwise (straight-like media) or clockwise (rays that cross
+ * through a focus, e.g. the fish-eye lens) is read from the first two traces.
+ * Secant steps (Sec. 3.4, default) are taken while they stay inside the
+ * bracket; otherwise a Regula-Falsi step on the bracket with the Illinois
+ * halving of a twice-retained end. */
+static void link_pair(const Field* F, double R, const double* xe, const double* xr, double ds,
+                      double tol, int max_iter, double theta_in, Eval* best, int* status,
+                      int* n_eval_out) {
+    const double phi_e = atan2(xe[1], xe[0]);
+    const double psi_r = mod_2pi(atan2(xr[1], xr[0]) - phi_e);
+    const double th_lo = phi_e + 0.5 * M_PI, th_hi = phi_e + 1.5 * M_PI;
+    double margin = ds / R;
+    if (margin < 1e-9) margin = 1e-9;
+    const double a_min = th_lo + margin, a_max = th_hi - margin;
+    if (max_iter < 2) max_iter = 2;
+
+    double th0 = isnan(theta_in) ? atan2(xr[1] - xe[1], xr[0] - xe[0]) : theta_in;
+    th0 = th_lo + mod_2pi(th0 - th_lo);
+    if (th0 < a_min) th0 = a_min;
+    if (th0 > a_max) th0 = a_max;
+
+    Eval e0, e1, cur;
+    int n_eval = 0, conv = 0;
+    double psi_at_lo = 0.0; /* interception angle at the lo end of the fan (0 or 2pi) */
+
+    evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, th0, &e0);
+    ++n_eval;
+    *best = e0;
+    if (e0.dist <= tol) conv = 1;
+    if (!conv) {
+        double th1 = th0 - e0.m / (2.0 * R);
+        if (th1 < a_min) th1 = a_min;
+        if (th1 > a_max) th1 = a_max;
+        if (th1 == th0) th1 = (th0 - a_min > a_max - th0) ? th0 - margin : th0 + margin;
+        evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, th1, &e1);
+        ++n_eval;
+        if (e1.dist < best->dist) *best = e1;
+        if (e1.dist <= tol) conv = 1;
+        if (!conv) {
+            /* orientation of the sweep, then the fan-end bracket: (ta, fa) with
+             * misfit < 0 and (tb, fb) with misfit > 0 */
+            int ccw = !((e1.m - e0.m) * (th1 - th0) < 0.0);
+            psi_at_lo = ccw ? 0.0 : 2.0 * M_PI;
+            double ta = ccw ? th_lo : th_hi, fa = -R * psi_r;
+            double tb = ccw ? th_hi : th_lo, fb = R * (2.0 * M_PI - psi_r);
+            const Eval* seen[2] = {&e0, &e1};
+            for (int q = 0; q < 2; ++q) {
+                double t = seen[q]->theta, m = seen[q]->m;
+                if (t > fmin(ta, tb) && t < fmax(ta, tb)) {
+                    if (m < 0) { ta = t; fa = m; } else { tb = t; fb = m; }
+                }
+            }
+            Eval prev = e0;
+            cur = e1;
+            int last_side = 0; /* -1: a replaced last, +1: b replaced last */
+            while (n_eval < max_iter) {
+                double next = 0.0;
+                double den = cur.m - prev.m;
+                int ok = (den != 0.0);
+                if (ok) next = cur.theta - cur.m * (cur.theta - prev.theta) / den;
+                ok = ok && isfinite(next) && next > fmin(ta, tb) && next < fmax(ta, tb);
+                if (!ok) next = (ta * fb - tb * fa) / (fb - fa);
+                Eval e;
+                evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, next, &e);
+                ++n_eval;
+                if (e.dist < best->dist) *best = e;
+                if (e.dist <= tol) { conv = 1; break; }
+                if (e.m < 0) {
+                    ta = e.theta; fa = e.m;
+                    if (last_side == -1) fb *= 0.5;
+                    last_side = -1;
+                } else {
+                    tb = e.theta; fb = e.m;
+                    if (last_side == 1) fa *= 0.5;
+                    last_side = 1;
+                }
+                prev = cur;
+                cur = e;
+            }
+        }
+    }
+    /* a pair none of whose traces reached the ring reports the step cap */
+    *status = conv ? ORC_RAY_OK : (isinf(best->dist) ? ORC_RAY_STEPCAP : ORC_RAY_MAXITER);
+    *n_eval_out = n_eval;
+}
+
+static int nthreads_of(int32_t n) {
+#ifdef _OPENMP
+    return n > 0 ? n : omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+int orc_num_threads(void) { return nthreads_of(0); }
+
+int orc_field(const orc_grid* g, const double* c_mps, double* c, double* gx, double* gy, double* s) {
+    Field F;
+    int rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    size_t n = (size_t)F.nx * F.ny;
+    if (c) memcpy(c, F.c, n * sizeof(double));
+    if (gx) memcpy(gx, F.gx, n * sizeof(double));
+    if (gy) memcpy(gy, F.gy, n * sizeof(double));
+    if (s) memcpy(s, F.s, n * sizeof(double));
+    field_free(&F);
+    return ORC_OK;
+}
+
+int orc_sample(const orc_grid* g, const double* c_mps, int32_t n, const double* xy, double* out) {
+    Field F;
+    int rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    for (int32_t k = 0; k < n; ++k) sample(&F, xy[2 * k], xy[2 * k + 1], out + 4 * k);
+    field_free(&F);
+    return ORC_OK;
+}
+
+int orc_march(const orc_grid* g, const double* c_mps, double x, double y, double theta,
+              double ds, int32_t n_steps, double* xy_out) {
+    Field F;
+    int rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    double st[4] = {x, y, cos(theta), sin(theta)}, nx[4];
+    xy_out[0] = x; xy_out[1] = y;
+    for (int32_t k = 1; k <= n_steps; ++k) {
+        rk4(&F, st, ds, nx);
+        memcpy(st, nx, sizeof(st));
+        xy_out[2 * k] = st[0];
+        xy_out[2 * k + 1] = st[1];
+    }
+    field_free(&F);
+    return ORC_OK;
+}
+
+int orc_trace(const orc_grid* g, const double* c_mps, double R, double xe, double ye,
+              double xr, double yr, double theta, double ds, int64_t cap, double* pts,
+              double* alpha, int64_t* n_pts, double* out6, int32_t* flags) {
+    if (!ring_ok(g, R, ds)) return ORC_EINVAL;
+    Field F;
+    int rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    TraceRes res;
+    trace(&F, R, xe, ye, xr, yr, theta, ds, pts, alpha, cap, &res);
+    if (n_pts) *n_pts = res.n_pts;
+    if (out6) {
+        out6[0] = res.T; out6[1] = res.hit[0]; out6[2] = res.hit[1];
+        out6[3] = res.dir[0]; out6[4] = res.dir[1]; out6[5] = res.dsp;
+    }
+    if (flags) *flags = res.flags;
+    field_free(&F);
+    return ORC_OK;
+}
+
+static int check_common(const orc_grid* g, int32_t n_tx, const double* tx, double R, double ds,
+                        int32_t n_pairs, const int32_t* pairs) {
+    if (!g || !tx || n_tx < 2 || n_pairs < 0 || !ring_ok(g, R, ds)) return ORC_EINVAL;
+    if (!pairs && (int64_t)n_pairs != (int64_t)n_tx * (n_tx - 1)) return ORC_EINVAL;
+    for (int32_t t = 0; t < n_tx; ++t)
+        if (!on_ring(tx + 2 * t, R)) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+             double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
+             int32_t max_iter, double* theta_io, double* tof, double* hit_xy,
+             int32_t* status, int32_t* iters, int32_t nthreads) {
+    int rc = check_common(g, n_tx, tx, R, ds, n_pairs, pairs);
+    if (rc) return rc;
+    if (!theta_io || !(tol > 0)) return ORC_EINVAL;
+    Field F;
+    rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads_of(nthreads)) reduction(| : bad)
+    for (int32_t k = 0; k < n_pairs; ++k) {
+        int e, r;
+        if (!pair_of(n_tx, pairs, k, &e, &r)) {
+            bad = 1;
+            if (status) status[k] = ORC_RAY_BADINPUT;
+            continue;
+        }
+        Eval best;
+        memset(&best, 0, sizeof(best));
+        int st, ne;
+        link_pair(&F, R, tx + 2 * e, tx + 2 * r, ds, tol, max_iter, theta_io[k], &best, &st, &ne);
+        theta_io[k] = best.theta;
+        if (tof) tof[k] = best.tr.T;
+        if (hit_xy) { hit_xy[2 * k] = best.tr.hit[0]; hit_xy[2 * k + 1] = best.tr.hit[1]; }
+        if (status) status[k] = st;
+        if (iters) iters[k] = ne;
+    }
+    field_free(&F);
+    return bad ? ORC_EINVAL : ORC_OK;
+}
+
+int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+            double R, int32_t n_pairs, const int32_t* pairs, double ds, const double* theta,
+            double* tof, double* hit_xy, int32_t nthreads) {
+    int rc = check_common(g, n_tx, tx, R, ds, n_pairs, pairs);
+    if (rc) return rc;
+    Field F;
+    rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads_of(nthreads)) reduction(| : bad)
+    for (int32_t k = 0; k < n_pairs; ++k) {
+        int e, r;
+        if (!pair_of(n_tx, pairs, k, &e, &r)) { bad = 1; continue; }
+        TraceRes res;
+        trace(&F, R, tx[2 * e], tx[2 * e + 1], tx[2 * r], tx[2 * r + 1], theta[k], ds, NULL, NULL, 0,
+              &res);
+        if (tof) tof[k] = res.T;
+        if (hit_xy) { hit_xy[2 * k] = res.hit[0]; hit_xy[2 * k + 1] = res.hit[1]; }
+    }
+    field_free(&F);
+    return bad ? ORC_EINVAL : ORC_OK;
+}
+
+/* One row of L: (node, weight) entries of every sample point, sorted by node
+ * and merged. Returns the entry count; ent holds 4 * n_pts slots. */
+typedef struct { int64_t node; double w; } Entry;
+
+static int cmp_entry(const void* a, const void* b) {
+    int64_t x = ((const Entry*)a)->node, y = ((const Entry*)b)->node;
+    return (x > y) - (x < y);
+}
+
+static int64_t build_row(const Field* F, const double* pts, const double* alpha, int64_t n_pts,
+                         Entry* ent) {
+    int64_t n = 0;
+    for (int64_t m = 0; m < n_pts; ++m) {
+        Stencil S;
+        stencil_at(F, pts[2 * m], pts[2 * m + 1], &S);
+        for (int q = 0; q < 4; ++q) { ent[n].node = (int64_t)S.k[q]; ent[n].w = alpha[m] * S.w[q]; ++n; }
+    }
+    qsort(ent, (size_t)n, sizeof(Entry), cmp_entry);
+    int64_t out = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        if (out > 0 && ent[out - 1].node == ent[t].node) ent[out - 1].w += ent[t].w;
+        else ent[out++] = ent[t];
+    }
+    return out;
+}
+
+int64_t orc_path_matrix(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+                        double R, int32_t n_pairs, const int32_t* pairs, double ds,
+                        const double* theta, int64_t* row_ptr, int32_t* col, double* val,
+                        int64_t cap, int32_t nthreads) {
+    if (check_common(g, n_tx, tx, R, ds, n_pairs, pairs) || !theta || !row_ptr) return -1;
+    Field F;
+    if (field_make(&F, g, c_mps)) return -1;
+    const int64_t pcap = step_cap(R, ds) + 2;
+    int64_t* counts = calloc((size_t)n_pairs + 1, sizeof(int64_t));
+    int bad = 0;
+    /* pass 1: row lengths */
+#pragma omp parallel num_threads(nthreads_of(nthreads)) reduction(| : bad)
+    {
+        double* pts = malloc((size_t)pcap * 2 * sizeof(double));
+        double* alpha = malloc((size_t)pcap * sizeof(double));
+        Entry* ent = malloc((size_t)pcap * 4 * sizeof(Entry));
+#pragma omp for schedule(dynamic, 8)
+        for (int32_t k = 0; k < n_pairs; ++k) {
+            int e, r;
+            if (!pair_of(n_tx, pairs, k, &e, &r)) { bad = 1; continue; }
+            TraceRes res;
+            trace(&F, R, tx[2 * e], tx[2 * e + 1], tx[2 * r], tx[2 * r + 1], theta[k], ds, pts,
+                  alpha, pcap, &res);
+            counts[k] = build_row(&F, pts, alpha, res.n_pts, ent);
+        }
+        free(pts); free(alpha); free(ent);
+    }
+    row_ptr[0] = 0;
+    for (int32_t k = 0; k < n_pairs; ++k) row_ptr[k + 1] = row_ptr[k] + counts[k];
+    int64_t nnz = row_ptr[n_pairs];
+    free(counts);
+    if (bad) { field_free(&F); return -1; }
+    if (!col || !val || cap < nnz) { field_free(&F); return nnz; }
+    /* pass 2: fill */
+#pragma omp parallel num_threads(nthreads_of(nthreads))
+    {
+        double* pts = malloc((size_t)pcap * 2 * sizeof(double));
+        double* alpha = malloc((size_t)pcap * sizeof(double));
+        Entry* ent = malloc((size_t)pcap * 4 * sizeof(Entry));
+#pragma omp for schedule(dynamic, 8)
+        for (int32_t k = 0; k < n_pairs; ++k) {
+            int e, r;
+            pair_of(n_tx, pairs, k, &e, &r);
+            TraceRes res;
+            trace(&F, R, tx[2 * e], tx[2 * e + 1], tx[2 * r], tx[2 * r + 1], theta[k], ds, pts,
+                  alpha, pcap, &res);
+            int64_t n = build_row(&F, pts, alpha, res.n_pts, ent);
+            for (int64_t t = 0; t < n; ++t) {
+                col[row_ptr[k] + t] = (int32_t)ent[t].node;
+                val[row_ptr[k] + t] = ent[t].w;
+            }
+        }
+        free(pts); free(alpha); free(ent);
+    }
+    field_free(&F);
+    return nnz;
+}
+
+int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+                double R, int32_t n_pairs, const int32_t* pairs, double ds, const double* theta,
+                const double* g_tof, double* g_c, int32_t nthreads) {
+    int rc = check_common(g, n_tx, tx, R, ds, n_pairs, pairs);
+    if (rc) return rc;
+    if (!theta || !g_tof || !g_c) return ORC_EINVAL;
+    Field F;
+    rc = field_make(&F, g, c_mps);
+    if (rc) return rc;
+    const size_t nn = (size_t)F.nx * F.ny;
+    const int64_t pcap = step_cap(R, ds) + 2;
+    const int nt = nthreads_of(nthreads);
+    double* acc = calloc((size_t)nt * nn, sizeof(double));
+    if (!acc) { field_free(&F); return ORC_ENOMEM; }
+    int bad = 0;
+#pragma omp parallel num_threads(nt) reduction(| : bad)
+    {
+#ifdef _OPENMP
+        double* gs = acc + (size_t)omp_get_thread_num() * nn;
+#else
+        double* gs = acc;
+#endif
+        double* pts = malloc((size_t)pcap * 2 * sizeof(double));
+        double* alpha = malloc((size_t)pcap * sizeof(double));
+#pragma omp for schedule(dynamic, 8)
+        for (int32_t k = 0; k < n_pairs; ++k) {
+            int e, r;
+            if (!pair_of(n_tx, pairs, k, &e, &r)) { bad = 1; continue; }
+            TraceRes res;
+            trace(&F, R, tx[2 * e], tx[2 * e + 1], tx[2 * r], tx[2 * r + 1], theta[k], ds, pts,
+                  alpha, pcap, &res);
+            /* (L^T g)_j = sum_i g_i L_ij with L_ij = sum_m alpha_m phi_j(x_m) */
+            for (int64_t m = 0; m < res.n_pts; ++m) {
+                Stencil S;
+                stencil_at(&F, pts[2 * m], pts[2 * m + 1], &S);
+                for (int q = 0; q < 4; ++q) gs[S.k[q]] += g_tof[k] * alpha[m] * S.w[q];
+            }
+        }
+        free(pts); free(alpha);
+    }
+    for (size_t j = 0; j < nn; ++j) {
+        double sum = 0.0;
+        for (int t = 0; t < nt; ++t) sum += acc[(size_t)t * nn + j];
+        /* s = 1000 / c_mps (us/mm)  =>  ds/dc = -1000 / c_mps^2 */
+        g_c[j] = -1000.0 * sum / (c_mps[j] * c_mps[j]);
+    }
+    free(acc);
+    field_free(&F);
+    return bad ? ORC_EINVAL : ORC_OK;
+}

@@ -1,0 +1,94 @@
+/*
+ * FP64 CPU oracle for two-point ray tracing in a gridded 2D sound-speed image.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path links, loads or calls
+ * this code: only the tests, the smoke check and the benchmark's CPU baseline
+ * do. It shares no code, header, table or helper with the CUDA library.
+ *
+ * The oracle follows the paper (arXiv:2511.18511) step by step:
+ *   - the field and its gradient live on grid nodes and are sampled off-grid by
+ *     bilinear interpolation, the gradient being interpolated from grid values
+ *     (Sec. 3.3.1, "Bilinear interpolation");
+ *   - rays evolve position x and unit direction d from the sound speed and its
+ *     gradient (Sec. 3.2.3; the eikonal/Fermat model of the Appendix), marched
+ *     with classic RK4 at a fixed step ds;
+ *   - the shooting method links each emitter-receiver pair by a root search on
+ *     the launch angle for the boundary-interception misfit (Sec. 3.4, Secant
+ *     default with Regula-Falsi safeguard);
+ *   - the travel time is the trapezoid line integral of slowness with the last
+ *     point replaced by the boundary interception (Sec. 4.2, acoustic-length
+ *     trapezoid rule with the shortened last step ds');
+ *   - the system-matrix row of a pair holds interpolation-weighted path
+ *     lengths (Sec. 3.1.1), and the adjoint is its transpose.
+ *
+ * Units: mm, us, mm/us inside; sound speed is passed in m/s (1 m/s = 1e-3
+ * mm/us), travel times come back in us, gradients per (m/s).
+ * Grid node (i, j) sits at (x0 + i h, y0 + j h), row-major index j*nx + i.
+ */
+#ifndef RT_ORACLE_H
+#define RT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { int32_t nx, ny; double h, x0, y0; } orc_grid;
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
+/* per-ray status */
+enum { ORC_RAY_OK = 0, ORC_RAY_MAXITER = 1, ORC_RAY_STEPCAP = 2, ORC_RAY_BADINPUT = 4 };
+
+/* Nodal field in mm/us units: c, dc/dx, dc/dy (central differences inside,
+ * one-sided at the edges) and slowness s = 1/c. */
+int orc_field(const orc_grid* g, const double* c_mps, double* c, double* gx, double* gy, double* s);
+
+/* Bilinear samples of (c, dc/dx, dc/dy, s) at n points xy[2n]; out[4n]. */
+int orc_sample(const orc_grid* g, const double* c_mps, int32_t n, const double* xy, double* out);
+
+/* n_steps fixed RK4 steps of size ds from (x, y) at angle theta; writes the
+ * n_steps+1 positions to xy_out[2(n_steps+1)]. */
+int orc_march(const orc_grid* g, const double* c_mps, double x, double y, double theta,
+              double ds, int32_t n_steps, double* xy_out);
+
+/* One trace from (xe, ye) at angle theta until the first boundary crossing of
+ * the circle |x| = R, landing exactly on it. out6 = {T, hit_x, hit_y, d_x, d_y, ds'};
+ * T includes the endpoint correction toward (xr, yr). If pts/alpha are given
+ * (capacity cap) the sample points and their trapezoid weights are written and
+ * *n_pts is set. *flags: bit0 step cap hit, bit1 ray left outward at once. */
+int orc_trace(const orc_grid* g, const double* c_mps, double R, double xe, double ye,
+              double xr, double yr, double theta, double ds, int64_t cap, double* pts,
+              double* alpha, int64_t* n_pts, double* out6, int32_t* flags);
+
+/* Link every pair (pairs[2k], pairs[2k+1]) or, with pairs == NULL, all e != r
+ * emitter-major. theta_io: NaN = straight-line start, else warm start; on
+ * return the linked angle. Outputs may be NULL. */
+int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+             double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
+             int32_t max_iter, double* theta_io, double* tof, double* hit_xy,
+             int32_t* status, int32_t* iters, int32_t nthreads);
+
+/* Travel time (and hit) of every pair at the given angles, no linking. */
+int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+            double R, int32_t n_pairs, const int32_t* pairs, double ds, const double* theta,
+            double* tof, double* hit_xy, int32_t nthreads);
+
+/* Explicit CSR system matrix L (rows = pairs, cols = nodes), T = L s.
+ * Returns nnz (>= 0) or -1 on error. With col == NULL only counts. */
+int64_t orc_path_matrix(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+                        double R, int32_t n_pairs, const int32_t* pairs, double ds,
+                        const double* theta, int64_t* row_ptr, int32_t* col, double* val,
+                        int64_t cap, int32_t nthreads);
+
+/* Adjoint: g_c[node] = d(sum_i g_tof[i] T_i)/d c_node in us/(m/s) with the
+ * rays frozen at theta, i.e. -(L^T g)_j * 1000 / c_j^2. */
+int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
+                double R, int32_t n_pairs, const int32_t* pairs, double ds, const double* theta,
+                const double* g_tof, double* g_c, int32_t nthreads);
+
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
