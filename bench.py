@@ -1,0 +1,325 @@
+"""Benchmark: linked rays/s of the ToF forward + adjoint step on the breast
+workload (1024^2 grid at 0.2 mm, 512-element ring at 95 mm, 261,632 pairs,
+RK4 step 0.02 mm, linking tolerance 1e-4 mm), FP32-compensated (headline)
+next to the plain FP64 GPU form, with the roofline of the dominant kernel
+and the FP64 CPU oracle timed on the host as a baseline.
+
+One step = rt_link from straight-line launch angles (cold start, travel time
+fused) + rt_tof_adjoint of the L2 misfit 0.5*||T - T_meas||^2, on inputs
+already resident in HBM. L2 is flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank traces its own independent phantom (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "linked rays/s (ToF fwd+adjoint, 512-ring, 1024² grid) FP32 vs FP64 GPU; % roofline"
+UNIT = "linked rays/s"
+# FLOPs of one RK4 step of the method as written (4 bilinear samples of c and
+# grad c with their weights, the ray RHS, the RK4 stage updates and final
+# combination, renormalisation, the trapezoid slowness sample and the exit
+# test; FMA = 2, div/sqrt = 1); the derivation is in the design notes.
+FLOP_PER_STEP = 219
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "link_traffic.json"))
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int):
+    from paper_2511_18511_gb300 import phantoms as P
+    return P.cfg_breast(seed=3 + rank)
+
+
+class Clocks:
+    """nvidia-smi sampling (every 200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, n_emit: int = 32, steps: int = 1):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    n_emit emitters spread over the ring, each with all its receivers."""
+    import oracle
+    from paper_2511_18511_gb300 import phantoms as P
+    oracle.build()
+    pairs = P.all_pairs(w.n_tx)
+    emit = np.arange(0, w.n_tx, max(1, w.n_tx // n_emit))[:n_emit]
+    sub = pairs[np.isin(pairs[:, 0], emit)]
+    t_meas, _ = None, None
+    ref = oracle.link(w.grid, w.c_true, w.tx, w.ring_radius, w.ds, tol=w.tol, pairs=sub)
+    t_meas = ref["tof"]
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        r = oracle.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, pairs=sub)
+        oracle.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, r["theta"], r["tof"] - t_meas, pairs=sub)
+        times.append(time.perf_counter() - t0)
+    dt = float(np.median(times))
+    return {"value": len(sub) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(sub)} pairs ({len(emit)} emitters x {w.n_tx - 1} receivers) of the "
+                      f"{w.name} workload, link + adjoint, {dt:.2f} s per pass"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(0)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, n_emit=4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, n_emit=4))
+    total = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "grid": w.grid.nx, "ring": w.n_tx,
+                                            "pairs_per_step": "4 emitters x 511 receivers (bounded sample)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2511_18511_gb300 as rt
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = workload(rank)
+    ctx = rt.Context(local)
+    ctx.reserve(w.grid.nx * w.grid.ny)
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, device=dev)
+    c_true = torch.as_tensor(w.c_true, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    n = prob.n_pairs
+
+    # "measured" travel times from the true medium (outside any timed region)
+    meas = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp64", c=c_true, ctx=ctx)
+    t_meas = meas["tof"].clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(prec, out, g):
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, ctx=ctx, out=out)
+        rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, ctx=ctx, out=g)
+        return r
+
+    def buffers():
+        return dict(theta=torch.empty(n, dtype=torch.float64, device=dev),
+                    tof=torch.empty(n, dtype=torch.float64, device=dev),
+                    hit=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                    status=torch.empty(n, dtype=torch.int32, device=dev),
+                    iters=torch.empty(n, dtype=torch.int32, device=dev))
+
+    def timed(prec, steps, warmup, clocks=None):
+        out, g = buffers(), torch.empty_like(prob.c)
+        for _ in range(warmup):
+            step(prec, out, g)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, ctx=ctx, out=out)
+            ev[k][1].record(stream)
+            rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, ctx=ctx, out=g)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        if dist is not None:
+            dist.barrier()
+        step_ms = [a.elapsed_time(c) for a, b, c in ev]
+        link_ms = [a.elapsed_time(b) for a, b, c in ev]
+        ok, counts = rt.rt_status_counts(ctx)
+        return dict(step_ms=step_ms, link_ms=link_ms, counts=counts, ok=ok, clocks=clk,
+                    iters=out["iters"].float().mean().item(), g=g, out=out)
+
+    clocks = Clocks(local)
+    res = timed("fp32c", args.steps, args.warmup, clocks)
+    total_ms = float(np.sum(res["step_ms"]))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n / (ms_per_step / 1e3)
+
+    # the plain FP64 GPU form on the same workload (fewer steps: it is slow on GB300)
+    r64 = timed("fp64", max(1, args.fp64_steps), 1)
+    ms64 = float(np.mean(r64["step_ms"]))
+
+    # roofline of the dominant kernel (the FP32 link kernel), from its live events
+    steps_per_launch = res["counts"][7]
+    link_ms = float(np.mean(res["link_ms"]))
+    achieved = steps_per_launch * FLOP_PER_STEP / (link_ms / 1e3) / 1e12
+    traffic = None
+    if os.path.exists(args.traffic_json):
+        try:
+            tj = json.load(open(args.traffic_json))
+            if tj.get("kernel_source_hash") == _kernel_hash():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # e2e through the public API with host buffers (pinned), copies timed
+    c_host = torch.as_tensor(w.c).pin_memory()
+    tm_host = t_meas.cpu().pin_memory()
+    T_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    g_host = torch.empty_like(c_host).pin_memory()
+    c_dev = torch.empty_like(prob.c)
+    tm_dev = torch.empty_like(t_meas)
+    out_e, g_e = buffers(), torch.empty_like(prob.c)
+    e2e_steps = max(2, min(args.steps, 3))
+
+    def e2e_step():
+        c_dev.copy_(c_host, non_blocking=True)
+        tm_dev.copy_(tm_host, non_blocking=True)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp32c", c=c_dev, ctx=ctx, out=out_e)
+        rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=tm_dev, precision="fp32c", c=c_dev, ctx=ctx,
+                          out=g_e)
+        T_host.copy_(r["tof"], non_blocking=True)
+        g_host.copy_(g_e, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = c_host.numel() * 8 + tm_host.numel() * 8
+    d2h = T_host.numel() * 8 + g_host.numel() * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "grid": f"{w.grid.nx}x{w.grid.ny}", "h_mm": w.grid.h, "ring": w.n_tx,
+                   "ring_radius_mm": w.ring_radius, "pairs": n, "ds_mm": w.ds, "tol_mm": w.tol,
+                   "start": "straight-line launch angles (cold)", "step": "rt_link + rt_tof_adjoint (L2 misfit)",
+                   "precision": "fp32c (FP32 march, compensated direction/sums, FP64 linking)",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "k_link<float> (+ its field pack)",
+                     "flop_per_rk4_step": FLOP_PER_STEP, "rk4_steps_per_launch": steps_per_launch,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"},
+        "fp64_gpu": {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                     "speedup_fp32c_over_fp64": ms64 / ms_per_step},
+        "link": {"mean_traces_per_pair": res["iters"], "all_linked": res["ok"],
+                 "status_counts": res["counts"][:7], "link_ms": link_ms,
+                 "adjoint_ms": float(np.mean(res["step_ms"]) - link_ms)},
+        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 5 * args.steps,
+        "clocks": res["clocks"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("rt_trace.cuh", "rt_ray.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2511_18511_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    main()

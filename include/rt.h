@@ -1,0 +1,183 @@
+/*
+ * rt.h — C ABI of the GB300-native two-point ray-tracing library
+ * (libraytof.so): travel times, their adjoint and the ray-Born operator for
+ * ultrasound sound-speed tomography on a 2D grid with a transducer ring,
+ * following arXiv:2511.18511.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: lengths in mm, sound speed in m/s (converted internally to mm/us),
+ * travel times in us, frequencies in MHz.
+ * Grid: node (i, j), i along x, sits at (x0_mm + i*h_mm, y0_mm + j*h_mm) and
+ * is stored row-major at index j*nx + i. The field is sampled off-grid by
+ * bilinear interpolation of nodal values, its gradient by bilinear
+ * interpolation of central-difference nodal gradients (paper Sec. 3.3.1).
+ * Ring: transducer k at tx_xy_mm[2k], tx_xy_mm[2k+1], all on the circle of
+ * radius ring_radius_mm centred on (0, 0); the circle plus one step and one
+ * cell must lie inside the grid. A pair (e, r) is an emitter-receiver pair
+ * (paper Sec. 1: one element fires, the others receive); pairs == NULL means
+ * all e != r in emitter-major order (pair k = e*(N-1) + r - (r > e)); n_pairs == 0
+ * is a valid empty call.
+ * Memory: every array argument is DEVICE memory owned by the caller unless a
+ * comment says "host". The library allocates only inside an rt_ctx
+ * (workspace that grows on demand and is reused; rt_ctx_reserve sizes it
+ * ahead of time). Output arrays are overwritten.
+ * Streams: work is enqueued asynchronously on `stream` (a cudaStream_t; NULL
+ * = legacy default stream); a call returns once the work is enqueued.
+ * Errors: calls return RT_OK or an RT_E* code and never throw. Argument
+ * errors are detected on the host before anything is enqueued; the message
+ * is available from rt_last_error. Per-pair outcomes are reported in the
+ * status arrays (RT_RAY_*), their counts by rt_status_counts.
+ * Threads: one rt_ctx must not be used by two host threads at once.
+ */
+#ifndef RAYTOF_RT_H
+#define RAYTOF_RT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_ABI_VERSION 1
+
+enum rt_code {
+    RT_OK = 0,
+    RT_EINVAL = 1,    /* bad argument: size, pointer, ring outside grid, option */
+    RT_ECUDA = 2,     /* a CUDA runtime call failed (message in rt_last_error) */
+    RT_ENOCONV = 3,   /* returned only by rt_status_counts: some pairs did not link */
+    RT_ETIMEOUT = 4,  /* a bounded device-side wait expired */
+    RT_ENOMEM = 5     /* workspace allocation failed, or capacity too small */
+};
+
+/* Per-pair status written by rt_link (and the batch call). */
+enum rt_ray_status {
+    RT_RAY_OK = 0,        /* |x_hit - x_r| <= tol */
+    RT_RAY_MAXITER = 1,   /* max_iter traces without reaching tol (closest ray kept) */
+    RT_RAY_STEPCAP = 2,   /* no trace reached the ring within ceil(8R/ds) steps */
+    RT_RAY_BADINPUT = 4,  /* invalid pair, transducer off the ring, or c <= 0 / NaN */
+};
+
+enum rt_precision {
+    RT_FP64 = 0,       /* everything in FP64 */
+    RT_FP32_COMP = 1   /* FP32 marching and interpolation with cell-local positions,
+                          a compensated (double-float) direction and Kahan travel-time
+                          sums; FP64 linking updates, landing and endpoint */
+};
+
+typedef struct {
+    int32_t nx, ny;      /* nodes per axis, >= 3 */
+    double h_mm;         /* node spacing */
+    double x0_mm, y0_mm; /* position of node (0, 0) */
+} rt_grid;
+
+typedef struct {
+    int32_t precision;   /* enum rt_precision */
+    int32_t max_iter;    /* traces per pair in rt_link, >= 2 (30 is the usual) */
+    double ds_mm;        /* fixed RK4 step length > 0 */
+    double tol_mm;       /* linking tolerance on |x_hit - x_r| > 0 */
+} rt_options;
+
+/* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
+ * matrix maps the N_n grid values to the N_e*N_r pair travel times). */
+typedef struct {
+    rt_grid grid;
+    const double* c_mps;      /* device [ny*nx], sound speed > 0 */
+    int32_t n_tx;             /* transducers, >= 2 */
+    const double* tx_xy_mm;   /* device [2*n_tx] */
+    double ring_radius_mm;
+    int32_t n_pairs;          /* number of pairs; n_tx*(n_tx-1) when pairs == NULL */
+    const int32_t* pairs;     /* device [2*n_pairs] (e, r), or NULL */
+} rt_problem;
+
+typedef struct rt_ctx rt_ctx;
+
+/* Library ABI version (RT_ABI_VERSION of the build). */
+int rt_version(void);
+
+/* Create a context bound to CUDA device `device`; *out receives it. */
+int rt_ctx_create(rt_ctx** out, int device);
+/* Free the context and its workspace (NULL is ignored). */
+void rt_ctx_destroy(rt_ctx* ctx);
+/* Last error message of this context ("" if none); valid until the next call. */
+const char* rt_last_error(const rt_ctx* ctx);
+/* Pre-size the workspace for grids of up to max_nodes nodes, so that later
+ * calls allocate nothing (needed before capturing calls in a CUDA graph). */
+int rt_ctx_reserve(rt_ctx* ctx, int64_t max_nodes);
+
+/*
+ * rt_link — shooting-method ray linking with the travel time fused in.
+ * Paper Sec. 3.4 (ray linking: the launch direction is adjusted until the
+ * misfit between the ray's boundary interception and the receiver centre,
+ * parameterised by angle, vanishes; Secant default, Regula Falsi), Sec. 3.2.3
+ * (rays evolve x and unit d from the sound speed and its gradient; RK4 at a
+ * fixed step here), Sec. 4.2 (trapezoid travel time with the last point
+ * replaced by the interception, shortened last step), Sec. 3.4.1 (first
+ * linearisation starts from straight rays, later ones warm-start from the
+ * previous angles).
+ *   theta_io  [n_pairs] launch angle (rad, from +x). In: NaN = start from the
+ *             straight line to the receiver, else warm start. Out: angle of
+ *             the linked ray (the traced ray closest to the receiver).
+ *   tof_us    [n_pairs] travel time of the linked ray (or NULL).
+ *   hit_xy_mm [2*n_pairs] boundary interception of the linked ray (or NULL).
+ *   status    [n_pairs] enum rt_ray_status (or NULL).
+ *   iters     [n_pairs] traces used (or NULL).
+ * Status counts of this call can be read with rt_status_counts.
+ */
+int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* theta_io,
+            double* tof_us, double* hit_xy_mm, int32_t* status, int32_t* iters, void* stream);
+
+/*
+ * rt_tof_forward — travel time of every pair for fixed launch angles (one
+ * trace each, no linking): the forward ToF operator at the linked rays
+ * (paper Sec. 3.2.1, accumulated travel time; Sec. 4.2 quadrature).
+ *   theta     [n_pairs] launch angles.
+ *   tof_us    [n_pairs] out; hit_xy_mm [2*n_pairs] out (or NULL).
+ */
+int rt_tof_forward(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
+                   const double* theta, double* tof_us, double* hit_xy_mm, void* stream);
+
+/*
+ * rt_tof_adjoint — transpose of the system matrix applied to travel-time
+ * weights, chained to the sound speed (paper Sec. 3.1.1: each row holds the
+ * interpolation-weighted path lengths of a pair's ray; Fermat keeps the rays
+ * frozen at the linked angles):
+ *   g_c[j] = sum_i w_i * dT_i/dc_j = -(1000 / c_j^2) * sum_i w_i L_ij
+ * with w_i = g_tof[i] - (tof_ref ? tof_ref[i] : 0). With g_tof = T and
+ * tof_ref = measured times this is the gradient of 0.5*||T - T_ref||^2.
+ *   theta [n_pairs], g_tof [n_pairs], tof_ref [n_pairs] or NULL,
+ *   g_c   [ny*nx] out, in us/(m/s), FP64 (accumulated with FP64 atomics).
+ */
+int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
+                   const double* theta, const double* g_tof, const double* tof_ref,
+                   double* g_c, void* stream);
+
+/*
+ * rt_path_matrix — the explicit sparse system matrix (paper Sec. 3.1.1,
+ * "because of its sparsity, it can be computed and stored explicitly"):
+ * row i = pair i, column j = node j, L_ij = sum over the ray's sample points
+ * of (trapezoid weight * bilinear weight of node j), so that T = L s with
+ * s = 1000/c (us/mm). CSR with one group of 4 entries per cell the ray visits;
+ * a node shared by two visits appears twice (entries sum; column order is the
+ * ray's order, not sorted).
+ *   row_ptr   [n_pairs+1] int64 out (always written).
+ *   col, val  [capacity] out; filled only when capacity >= nnz.
+ *   nnz_out   HOST int64 out: number of entries. The call synchronises the
+ *             stream to read it; RT_ENOMEM if capacity < nnz (row_ptr valid).
+ */
+int rt_path_matrix(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
+                   const double* theta, int64_t* row_ptr, int32_t* col, double* val,
+                   int64_t capacity, int64_t* nnz_out, void* stream);
+
+/*
+ * rt_status_counts — synchronises `stream` and copies the per-status pair
+ * counts of the last rt_link on this context: counts[s] for s = 0..7 (HOST
+ * array), plus counts[7] = total RK4 steps taken by that call. Returns RT_OK
+ * when every pair linked, RT_ENOCONV otherwise.
+ */
+int rt_status_counts(rt_ctx* ctx, int64_t counts[8], void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAYTOF_RT_H */

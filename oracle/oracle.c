@@ -34,12 +34,14 @@
  *      the angular domain), with both angles measured counter-clockwise from
  *      the emitter in [0, 2pi) so that m is continuous over the inward fan of
  *      launch angles; converged when |x_hit - x_r| <= tol; first angle the
- *      straight line to the receiver (Sec. 3.4.1) or a warm start, second from
- *      the straight-chord slope dm/dtheta = 2R; the fan ends bracket the root;
- *      then Secant updates from the two latest angles (Sec. 3.4, default) while
- *      they stay inside the bracket, else Regula-Falsi (Sec. 3.4) with the
- *      Illinois halving; at most max_iter traces; the reported ray is the
- *      evaluated one closest to the receiver;
+ *      straight line to the receiver (Sec. 3.4.1) or a warm start; the fan
+ *      ends bracket the root, a probe ray next to the fan's lower end tells
+ *      whether the sweep runs counter-clockwise or (through a focus) clockwise;
+ *      second angle from the straight-chord slope |dm/dtheta| = 2R; then Secant
+ *      updates from the two latest angles (Sec. 3.4, default) while they stay
+ *      inside the bracket, else Regula-Falsi (Sec. 3.4) with the Illinois
+ *      halving; at most max_iter traces (the probe counts); the reported ray
+ *      is the evaluated one closest to the receiver;
  *   R7 adjoint: the rays are frozen at the linked angles (Fermat: the first
  *      order path change does not move T), so the gradient is the transpose
  *      of the system matrix whose rows are interpolation-weighted path lengths
@@ -300,11 +302,29 @@ static void evaluate(const Field* F, double R, const double* xe, const double* x
     E->m = R * (psi - psi_r);
 }
 
+/* Sign-changing bracket (ta, fa < 0), (tb, fb > 0) with the Illinois rule:
+ * when the same end is replaced twice in a row, the other end's value halves. */
+typedef struct { double ta, fa, tb, fb; int last; } Bracket;
+
+static void br_insert(Bracket* B, double t, double m) {
+    if (!(t > fmin(B->ta, B->tb) && t < fmax(B->ta, B->tb))) return;
+    if (m < 0) {
+        B->ta = t; B->fa = m;
+        if (B->last == -1) B->fb *= 0.5;
+        B->last = -1;
+    } else {
+        B->tb = t; B->fb = m;
+        if (B->last == 1) B->fa *= 0.5;
+        B->last = 1;
+    }
+}
+
 /* R6 linking of one pair: shooting over the inward fan of launch angles
  * (phi_e + pi/2, phi_e + 3pi/2). Over that fan the interception sweeps the
- * whole ring once, so the fan's two ends bracket the root; whether the sweep
- * runs counter-clockwise (straight-like media) or clockwise (rays that cross
- * through a focus, e.g. the fish-eye lens) is read from the first two traces.
+ * whole ring once, so the fan's two ends bracket the root. The sweep runs
+ * counter-clockwise in straight-like media and clockwise when rays cross
+ * through a focus (the fish-eye lens); a probe ray launched next to the fan's
+ * lower end tells which, since it returns next to the emitter on that side.
  * Secant steps (Sec. 3.4, default) are taken while they stay inside the
  * bracket; otherwise a Regula-Falsi step on the bracket with the Illinois
  * halving of a twice-retained end. */
@@ -324,7 +344,7 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
     if (th0 < a_min) th0 = a_min;
     if (th0 > a_max) th0 = a_max;
 
-    Eval e0, e1, cur;
+    Eval e0, ep;
     int n_eval = 0, conv = 0;
     double psi_at_lo = 0.0; /* interception angle at the lo end of the fan (0 or 2pi) */
 
@@ -333,55 +353,46 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
     *best = e0;
     if (e0.dist <= tol) conv = 1;
     if (!conv) {
-        double th1 = th0 - e0.m / (2.0 * R);
-        if (th1 < a_min) th1 = a_min;
-        if (th1 > a_max) th1 = a_max;
-        if (th1 == th0) th1 = (th0 - a_min > a_max - th0) ? th0 - margin : th0 + margin;
-        evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, th1, &e1);
+        /* orientation probe next to the lo end of the fan */
+        evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, a_min, &ep);
         ++n_eval;
-        if (e1.dist < best->dist) *best = e1;
-        if (e1.dist <= tol) conv = 1;
-        if (!conv) {
-            /* orientation of the sweep, then the fan-end bracket: (ta, fa) with
-             * misfit < 0 and (tb, fb) with misfit > 0 */
-            int ccw = !((e1.m - e0.m) * (th1 - th0) < 0.0);
-            psi_at_lo = ccw ? 0.0 : 2.0 * M_PI;
-            double ta = ccw ? th_lo : th_hi, fa = -R * psi_r;
-            double tb = ccw ? th_hi : th_lo, fb = R * (2.0 * M_PI - psi_r);
-            const Eval* seen[2] = {&e0, &e1};
-            for (int q = 0; q < 2; ++q) {
-                double t = seen[q]->theta, m = seen[q]->m;
-                if (t > fmin(ta, tb) && t < fmax(ta, tb)) {
-                    if (m < 0) { ta = t; fa = m; } else { tb = t; fb = m; }
-                }
-            }
-            Eval prev = e0;
-            cur = e1;
-            int last_side = 0; /* -1: a replaced last, +1: b replaced last */
-            while (n_eval < max_iter) {
-                double next = 0.0;
+        if (ep.dist < best->dist) *best = ep;
+        if (ep.dist <= tol) conv = 1;
+        const int ccw = (ep.m / R + psi_r) < M_PI;
+        psi_at_lo = ccw ? 0.0 : 2.0 * M_PI;
+        if (e0.tr.flags & 3)
+            evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, th0, &e0);
+        if (ep.tr.flags & 3)
+            ep.m = R * (psi_at_lo - psi_r);
+        Bracket B;
+        B.ta = ccw ? th_lo : th_hi; B.fa = -R * psi_r;
+        B.tb = ccw ? th_hi : th_lo; B.fb = R * (2.0 * M_PI - psi_r);
+        B.last = 0;
+        br_insert(&B, ep.theta, ep.m);
+        br_insert(&B, e0.theta, e0.m);
+        B.last = 0;
+        /* second angle from the straight-chord slope |dm/dtheta| = 2R */
+        double next = th0 - e0.m / (ccw ? 2.0 * R : -2.0 * R);
+        Eval prev = e0, cur = e0;
+        int first = 1;
+        while (!conv && n_eval < max_iter) {
+            if (!first) {
                 double den = cur.m - prev.m;
                 int ok = (den != 0.0);
-                if (ok) next = cur.theta - cur.m * (cur.theta - prev.theta) / den;
-                ok = ok && isfinite(next) && next > fmin(ta, tb) && next < fmax(ta, tb);
-                if (!ok) next = (ta * fb - tb * fa) / (fb - fa);
-                Eval e;
-                evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, next, &e);
-                ++n_eval;
-                if (e.dist < best->dist) *best = e;
-                if (e.dist <= tol) { conv = 1; break; }
-                if (e.m < 0) {
-                    ta = e.theta; fa = e.m;
-                    if (last_side == -1) fb *= 0.5;
-                    last_side = -1;
-                } else {
-                    tb = e.theta; fb = e.m;
-                    if (last_side == 1) fa *= 0.5;
-                    last_side = 1;
-                }
-                prev = cur;
-                cur = e;
+                next = ok ? cur.theta - cur.m * (cur.theta - prev.theta) / den : 0.0;
+                if (!ok) next = NAN;
             }
+            first = 0;
+            if (!(isfinite(next) && next > fmin(B.ta, B.tb) && next < fmax(B.ta, B.tb)))
+                next = (B.ta * B.fb - B.tb * B.fa) / (B.fb - B.fa);
+            Eval e;
+            evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, next, &e);
+            ++n_eval;
+            if (e.dist < best->dist) *best = e;
+            if (e.dist <= tol) { conv = 1; break; }
+            br_insert(&B, e.theta, e.m);
+            prev = cur;
+            cur = e;
         }
     }
     /* a pair none of whose traces reached the ring reports the step cap */

@@ -1,0 +1,226 @@
+"""GB300-native two-point ray tracing for ultrasound sound-speed tomography.
+
+Python binding of ``libraytof.so`` (C ABI in ``include/rt.h``). Every array is
+a CUDA torch tensor; the functions only marshal pointers and sizes, all work
+runs in the library's kernels on the current torch stream. PyTorch supplies
+device memory, streams and the autograd wrapper.
+
+Units: mm, m/s, us (see ``include/rt.h``). Paper: arXiv:2511.18511.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional
+
+import torch
+
+from . import _lib as _L
+from .phantoms import Grid
+
+__all__ = ["Context", "Problem", "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix",
+           "rt_status_counts", "ToF", "tof", "PRECISIONS"]
+
+PRECISIONS = {"fp64": _L.RT_FP64, "fp32c": _L.RT_FP32_COMP}
+
+
+class Context:
+    """An ``rt_ctx`` on one CUDA device (workspace owner)."""
+
+    def __init__(self, device: Optional[int] = None):
+        self.lib = _L.load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        _L.check(None, self.lib.rt_ctx_create(C.byref(h), self.device))
+        self.h = h
+
+    def reserve(self, max_nodes: int):
+        _L.check(self.h, self.lib.rt_ctx_reserve(self.h, int(max_nodes)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts: dict[int, Context] = {}
+
+
+def default_context(device: Optional[int] = None) -> Context:
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _contexts:
+        _contexts[d] = Context(d)
+    return _contexts[d]
+
+
+def _stream(stream) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev_f64(x, device) -> torch.Tensor:
+    t = torch.as_tensor(x, dtype=torch.float64, device=device)
+    return t.contiguous()
+
+
+@dataclasses.dataclass
+class Problem:
+    """Grid + sound speed + ring (device tensors), the rt_problem of the ABI."""
+    grid: Grid
+    c: torch.Tensor                   # float64 [ny, nx] m/s, CUDA
+    tx: torch.Tensor                  # float64 [N, 2] mm, CUDA
+    ring_radius: float
+    pairs: Optional[torch.Tensor] = None   # int32 [P, 2] or None = all e != r
+
+    @staticmethod
+    def create(grid: Grid, c, tx, ring_radius: float, pairs=None, device="cuda") -> "Problem":
+        p = None if pairs is None else torch.as_tensor(pairs, dtype=torch.int32, device=device).contiguous()
+        return Problem(grid, _dev_f64(c, device), _dev_f64(tx, device), float(ring_radius), p)
+
+    @property
+    def n_tx(self) -> int:
+        return int(self.tx.shape[0])
+
+    @property
+    def n_pairs(self) -> int:
+        return self.n_tx * (self.n_tx - 1) if self.pairs is None else int(self.pairs.shape[0])
+
+    def struct(self, c: Optional[torch.Tensor] = None) -> _L.RtProblem:
+        c = self.c if c is None else c
+        if c.dtype != torch.float64 or not c.is_cuda or not c.is_contiguous():
+            raise ValueError("c must be a contiguous float64 CUDA tensor")
+        if c.numel() != self.grid.nx * self.grid.ny:
+            raise ValueError("c has the wrong number of nodes")
+        g = _L.RtGrid(self.grid.nx, self.grid.ny, self.grid.h, self.grid.x0, self.grid.y0)
+        return _L.RtProblem(g, c.data_ptr(), self.n_tx, self.tx.data_ptr(), self.ring_radius,
+                            self.n_pairs, None if self.pairs is None else self.pairs.data_ptr())
+
+
+def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c") -> _L.RtOptions:
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol))
+
+
+def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
+            theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
+            ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None) -> dict:
+    """Link every pair (shooting method, paper Sec. 3.4) and return the linked
+    angles, travel times (us), interceptions (mm), per-pair status and traces."""
+    ctx = ctx or default_context(prob.c.device.index)
+    dev = prob.c.device
+    n = prob.n_pairs
+    if out is None:
+        out = dict(theta=torch.empty(n, dtype=torch.float64, device=dev),
+                   tof=torch.empty(n, dtype=torch.float64, device=dev),
+                   hit=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev),
+                   iters=torch.empty(n, dtype=torch.int32, device=dev))
+    if theta0 is None:
+        out["theta"].fill_(float("nan"))
+    else:
+        out["theta"].copy_(theta0)
+    ps = prob.struct(c)
+    o = _opts(ds, tol, max_iter, precision)
+    _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
+                                    _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
+    return out
+
+
+def rt_tof_forward(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
+                   c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None):
+    """Travel time and interception of every pair at fixed launch angles."""
+    ctx = ctx or default_context(prob.c.device.index)
+    dev = prob.c.device
+    tof_ = torch.empty(prob.n_pairs, dtype=torch.float64, device=dev)
+    hit = torch.empty((prob.n_pairs, 2), dtype=torch.float64, device=dev)
+    ps = prob.struct(c)
+    o = _opts(ds, precision=precision)
+    _L.check(ctx.h, ctx.lib.rt_tof_forward(ctx.h, C.byref(ps), C.byref(o), _ptr(theta.contiguous()), _ptr(tof_),
+                                           _ptr(hit), _stream(stream)))
+    return tof_, hit
+
+
+def rt_tof_adjoint(prob: Problem, theta: torch.Tensor, g_tof: torch.Tensor, ds: float,
+                   tof_ref: Optional[torch.Tensor] = None, precision: str = "fp32c",
+                   c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None,
+                   out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """g_c = sum_i (g_tof_i - tof_ref_i) dT_i/dc (us per m/s) with the rays
+    frozen at theta: the transpose of the system matrix (paper Sec. 3.1.1)."""
+    ctx = ctx or default_context(prob.c.device.index)
+    cc = prob.c if c is None else c
+    g = torch.empty_like(cc) if out is None else out
+    ps = prob.struct(c)
+    o = _opts(ds, precision=precision)
+    _L.check(ctx.h, ctx.lib.rt_tof_adjoint(ctx.h, C.byref(ps), C.byref(o), _ptr(theta.contiguous()),
+                                           _ptr(g_tof.contiguous()),
+                                           _ptr(None if tof_ref is None else tof_ref.contiguous()),
+                                           _ptr(g), _stream(stream)))
+    return g
+
+
+def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
+                   ctx: Optional[Context] = None, stream=None):
+    """Explicit CSR system matrix (row_ptr int64, col int32, val float64) with
+    T = L s, s = 1000/c; duplicate (row, col) entries sum."""
+    ctx = ctx or default_context(prob.c.device.index)
+    dev = prob.c.device
+    row_ptr = torch.empty(prob.n_pairs + 1, dtype=torch.int64, device=dev)
+    nnz = C.c_int64(0)
+    ps = prob.struct()
+    o = _opts(ds, precision=precision)
+    th = theta.contiguous()
+    rc = ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), None, None, 0,
+                                C.byref(nnz), _stream(stream))
+    if rc not in (_L.RT_OK, _L.RT_ENOMEM):
+        _L.check(ctx.h, rc)
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
+    _L.check(ctx.h, ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), _ptr(col),
+                                           _ptr(val), nnz.value, C.byref(nnz), _stream(stream)))
+    return row_ptr, col[: nnz.value], val[: nnz.value]
+
+
+def rt_status_counts(ctx: Optional[Context] = None, stream=None):
+    """(all_linked, counts[8]) of the last rt_link on ctx; counts[7] = RK4 steps."""
+    ctx = ctx or default_context()
+    arr = (C.c_int64 * 8)()
+    rc = ctx.lib.rt_status_counts(ctx.h, arr, _stream(stream))
+    if rc not in (_L.RT_OK, _L.RT_ENOCONV):
+        _L.check(ctx.h, rc)
+    return rc == _L.RT_OK, list(arr)
+
+
+class ToF(torch.autograd.Function):
+    """T = ToF(c): linked travel times; backward = the adjoint scatter kernel."""
+
+    @staticmethod
+    def forward(fctx, c, prob: Problem, ds: float, tol: float, max_iter: int, precision: str, theta0):
+        r = rt_link(prob, ds, tol, max_iter, precision, theta0=theta0, c=c.detach().contiguous())
+        fctx.prob, fctx.ds, fctx.precision = prob, ds, precision
+        fctx.save_for_backward(c, r["theta"])
+        fctx.link = r
+        return r["tof"]
+
+    @staticmethod
+    def backward(fctx, g_tof):
+        c, theta = fctx.saved_tensors
+        g = rt_tof_adjoint(fctx.prob, theta, g_tof.contiguous(), fctx.ds, precision=fctx.precision,
+                           c=c.detach().contiguous())
+        return g, None, None, None, None, None, None
+
+
+def tof(c: torch.Tensor, prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30,
+        precision: str = "fp32c", theta0: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Differentiable travel times of all pairs of ``prob`` for sound speed c."""
+    return ToF.apply(c, prob, ds, tol, max_iter, precision, theta0)

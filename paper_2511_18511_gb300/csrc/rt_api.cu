@@ -1,0 +1,266 @@
+// rt_api.cu — the C ABI declared in include/rt.h: context, argument checks,
+// workspace and kernel launches. No exception crosses the ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "rt_internal.h"
+#include "rt_trace.cuh"
+
+namespace {
+
+int fail(rt_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(rt_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, RT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Grows the packed-field buffer; refuses to allocate while `s` is being captured.
+int ensure_field(rt_ctx* ctx, size_t bytes, cudaStream_t s) {
+    if (ctx->field_bytes >= bytes) return RT_OK;
+    if (capturing(s)) return fail(ctx, RT_EINVAL, "workspace too small during stream capture: call rt_ctx_reserve first");
+    if (ctx->field) cudaFree(ctx->field);
+    ctx->field = nullptr;
+    ctx->field_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->field, bytes);
+    if (e != cudaSuccess) return fail(ctx, RT_ENOMEM, std::string("field workspace: ") + cudaGetErrorString(e));
+    ctx->field_bytes = bytes;
+    return RT_OK;
+}
+
+int set_device(rt_ctx* ctx) {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "cudaSetDevice");
+}
+
+int check_options(rt_ctx* ctx, const rt_options* o, bool need_link) {
+    if (!o) return fail(ctx, RT_EINVAL, "options pointer is NULL");
+    if (o->precision != RT_FP64 && o->precision != RT_FP32_COMP) return fail(ctx, RT_EINVAL, "unknown precision");
+    if (!(o->ds_mm > 0) || !std::isfinite(o->ds_mm)) return fail(ctx, RT_EINVAL, "ds_mm must be > 0");
+    if (need_link && !(o->tol_mm > 0)) return fail(ctx, RT_EINVAL, "tol_mm must be > 0");
+    if (need_link && o->max_iter < 2) return fail(ctx, RT_EINVAL, "max_iter must be >= 2");
+    return RT_OK;
+}
+
+// Validate, pack the field into the workspace and fill the launch geometry.
+int prepare(rt_ctx* ctx, const rt_problem* p, const rt_options* o, bool need_link, cudaStream_t s,
+            rt::Geom* G) {
+    if (!ctx) return RT_EINVAL;
+    ctx->err.clear();
+    int rc = check_options(ctx, o, need_link);
+    if (rc) return rc;
+    rc = rt::make_geom(ctx, p, o, G);
+    if (rc) return rc;
+    rc = set_device(ctx);
+    if (rc) return rc;
+    const size_t bytes = rt::node_bytes(o->precision) * (size_t)p->grid.nx * (size_t)p->grid.ny;
+    rc = ensure_field(ctx, bytes, s);
+    if (rc) return rc;
+    cudaError_t e = rt::launch_pack(p->grid, p->c_mps, ctx->field, ctx->dflag, o->precision, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pack kernel");
+    G->bad_field = ctx->dflag;
+    ctx->last_stream = s;
+    return RT_OK;
+}
+
+}  // namespace
+
+namespace rt {
+
+int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
+    if (!p) return fail(ctx, RT_EINVAL, "problem pointer is NULL");
+    const rt_grid& g = p->grid;
+    if (g.nx < 3 || g.ny < 3) return fail(ctx, RT_EINVAL, "grid must have at least 3 nodes per axis");
+    if ((int64_t)g.nx * g.ny > (int64_t)INT32_MAX / 2) return fail(ctx, RT_EINVAL, "grid too large");
+    if (!(g.h_mm > 0) || !std::isfinite(g.h_mm) || !std::isfinite(g.x0_mm) || !std::isfinite(g.y0_mm))
+        return fail(ctx, RT_EINVAL, "grid spacing/origin invalid");
+    if (!p->c_mps) return fail(ctx, RT_EINVAL, "c_mps is NULL");
+    if (p->n_tx < 2 || !p->tx_xy_mm) return fail(ctx, RT_EINVAL, "need >= 2 transducers and their positions");
+    if (p->n_pairs < 0) return fail(ctx, RT_EINVAL, "n_pairs < 0");
+    if (!p->pairs && p->n_pairs != 0 && (int64_t)p->n_pairs != (int64_t)p->n_tx * (p->n_tx - 1))
+        return fail(ctx, RT_EINVAL, "pairs == NULL requires n_pairs == n_tx*(n_tx-1)");
+    const double R = p->ring_radius_mm;
+    if (!(R > 0) || !std::isfinite(R)) return fail(ctx, RT_EINVAL, "ring radius must be > 0");
+    const double need = R + o->ds_mm + g.h_mm;
+    const double xl = g.x0_mm, xh = g.x0_mm + (g.nx - 1) * g.h_mm;
+    const double yl = g.y0_mm, yh = g.y0_mm + (g.ny - 1) * g.h_mm;
+    if (!(-need >= xl && need <= xh && -need >= yl && need <= yh))
+        return fail(ctx, RT_EINVAL, "ring (plus one step and one cell) must lie inside the grid");
+    const double Rc = R / g.h_mm;
+    if (Rc * Rc > 9.0e15) return fail(ctx, RT_EINVAL, "ring too large in cells");
+    G->nx = g.nx;
+    G->ny = g.ny;
+    G->h = g.h_mm;
+    G->x0 = g.x0_mm;
+    G->y0 = g.y0_mm;
+    G->R = R;
+    G->ds = o->ds_mm;
+    const double ox = -g.x0_mm / g.h_mm, oy = -g.y0_mm / g.h_mm;
+    G->Ox = (int)std::floor(ox);
+    G->Oy = (int)std::floor(oy);
+    G->oxf = ox - G->Ox;
+    G->oyf = oy - G->Oy;
+    const double R2 = Rc * Rc;
+    G->Q = (long long)std::floor(R2);
+    G->q = R2 - (double)G->Q;
+    G->max_steps = (long long)std::ceil(8.0 * R / o->ds_mm);
+    G->tx = p->tx_xy_mm;
+    G->n_tx = p->n_tx;
+    G->pairs = p->pairs;
+    G->n_pairs = p->n_pairs;
+    G->bad_field = nullptr;
+    return RT_OK;
+}
+
+}  // namespace rt
+
+extern "C" {
+
+int rt_version(void) { return RT_ABI_VERSION; }
+
+int rt_ctx_create(rt_ctx** out, int device) {
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    rt_ctx* ctx = new (std::nothrow) rt_ctx();
+    if (!ctx) return RT_ENOMEM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->counters, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dflag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dflag, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        rt_ctx_destroy(ctx);
+        return RT_ECUDA;
+    }
+    *out = ctx;
+    return RT_OK;
+}
+
+void rt_ctx_destroy(rt_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->field) cudaFree(ctx->field);
+    if (ctx->counters) cudaFree(ctx->counters);
+    if (ctx->dflag) cudaFree(ctx->dflag);
+    if (ctx->queue) cudaFree(ctx->queue);
+    if (ctx->scan_tmp) cudaFree(ctx->scan_tmp);
+    delete ctx;
+}
+
+const char* rt_last_error(const rt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rt_ctx_reserve(rt_ctx* ctx, int64_t max_nodes) {
+    if (!ctx) return RT_EINVAL;
+    ctx->err.clear();
+    if (max_nodes < 0) return fail(ctx, RT_EINVAL, "max_nodes < 0");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    return ensure_field(ctx, rt::node_bytes(RT_FP64) * (size_t)max_nodes, nullptr);
+}
+
+int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* theta_io, double* tof_us,
+            double* hit_xy_mm, int32_t* status, int32_t* iters, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx && !theta_io && prob && prob->n_pairs > 0) return fail(ctx, RT_EINVAL, "theta_io is NULL");
+    rt::Geom G;
+    int rc = prepare(ctx, prob, opt, true, s, &G);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
+    e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
+                        status, iters, ctx->counters, ctx->queue, s);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
+}
+
+int rt_tof_forward(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const double* theta,
+                   double* tof_us, double* hit_xy_mm, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx && (!theta || !tof_us) && prob && prob->n_pairs > 0)
+        return fail(ctx, RT_EINVAL, "theta and tof_us are required");
+    rt::Geom G;
+    int rc = prepare(ctx, prob, opt, false, s, &G);
+    if (rc) return rc;
+    cudaError_t e = rt::launch_tof(G, ctx->field, opt->precision, theta, tof_us, hit_xy_mm, s);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "tof kernel");
+}
+
+int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const double* theta,
+                   const double* g_tof, const double* tof_ref, double* g_c, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx && !g_c) return fail(ctx, RT_EINVAL, "g_c is required");
+    if (ctx && (!theta || !g_tof) && prob && prob->n_pairs > 0)
+        return fail(ctx, RT_EINVAL, "theta and g_tof are required");
+    rt::Geom G;
+    int rc = prepare(ctx, prob, opt, false, s, &G);
+    if (rc) return rc;
+    cudaError_t e = rt::launch_adjoint(G, ctx->field, opt->precision, theta, g_tof, tof_ref, prob->c_mps, g_c, s);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "adjoint kernel");
+}
+
+int rt_path_matrix(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const double* theta,
+                   int64_t* row_ptr, int32_t* col, double* val, int64_t capacity, int64_t* nnz_out,
+                   void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx && (!row_ptr || !nnz_out)) return fail(ctx, RT_EINVAL, "row_ptr and nnz_out are required");
+    if (ctx && !theta && prob && prob->n_pairs > 0) return fail(ctx, RT_EINVAL, "theta is required");
+    rt::Geom G;
+    int rc = prepare(ctx, prob, opt, false, s, &G);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "row_ptr reset");
+    e = rt::launch_rows(G, ctx->field, opt->precision, theta, row_ptr, nullptr, nullptr, false, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "row count kernel");
+    if (G.n_pairs > 0) {
+        size_t need = 0;
+        e = rt::launch_scan(row_ptr, G.n_pairs, nullptr, &need, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scan size");
+        if (ctx->scan_bytes < need) {
+            if (ctx->scan_tmp) cudaFree(ctx->scan_tmp);
+            ctx->scan_tmp = nullptr;
+            ctx->scan_bytes = 0;
+            e = cudaMalloc(&ctx->scan_tmp, need);
+            if (e != cudaSuccess) return fail(ctx, RT_ENOMEM, "scan workspace");
+            ctx->scan_bytes = need;
+        }
+        size_t have = ctx->scan_bytes;
+        e = rt::launch_scan(row_ptr, G.n_pairs, ctx->scan_tmp, &have, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scan");
+    }
+    int64_t nnz = 0;
+    e = cudaMemcpyAsync(&nnz, row_ptr + G.n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "nnz readback");
+    *nnz_out = nnz;
+    if (capacity < nnz || !col || !val) return fail(ctx, RT_ENOMEM, "capacity smaller than nnz (row_ptr is valid)");
+    e = rt::launch_rows(G, ctx->field, opt->precision, theta, row_ptr, col, val, true, s);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "row fill kernel");
+}
+
+int rt_status_counts(rt_ctx* ctx, int64_t counts[8], void* stream) {
+    if (!ctx || !counts) return RT_EINVAL;
+    ctx->err.clear();
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->last_stream;
+    unsigned long long h[8];
+    cudaError_t e = cudaMemcpyAsync(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status readback");
+    for (int k = 0; k < 8; ++k) counts[k] = (int64_t)h[k];
+    int64_t bad = 0;
+    for (int k = 1; k < 7; ++k) bad += counts[k];
+    return bad ? RT_ENOCONV : RT_OK;
+}
+
+}  // extern "C"

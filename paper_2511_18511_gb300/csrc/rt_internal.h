@@ -1,0 +1,48 @@
+// rt_internal.h — host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rt.h"
+
+struct rt_ctx {
+    int device = 0;
+    std::string err;
+    void* field = nullptr;          // packed nodes (float4 or 32-byte double4)
+    size_t field_bytes = 0;
+    unsigned long long* counters = nullptr;   // [8]: per-status counts, [7] RK4 steps
+    int* dflag = nullptr;           // [1]: set by the pack kernel when c <= 0 or NaN
+    int* queue = nullptr;           // [1]: work-queue head of the persistent linking kernel
+    void* scan_tmp = nullptr;       // prefix-sum workspace (path matrix)
+    size_t scan_bytes = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace rt {
+
+struct Geom;
+
+// Fills a Geom for a validated problem; returns RT_OK or RT_EINVAL (message in ctx).
+int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G);
+
+// Kernel launchers (rt_ray.cu). All enqueue on `s` and return a cudaError_t.
+cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
+                        cudaStream_t s);
+cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
+                        double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
+                        unsigned long long* counters, int* queue, cudaStream_t s);
+cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double* theta, double* tof,
+                       double* hit, cudaStream_t s);
+cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,
+                           const double* g_tof, const double* tof_ref, const double* c_mps,
+                           double* g_c, cudaStream_t s);
+cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double* theta,
+                        int64_t* row_ptr, int32_t* col, double* val, bool fill, cudaStream_t s);
+cudaError_t launch_scan(int64_t* row_ptr, int n, void* tmp, size_t* tmp_bytes, cudaStream_t s);
+
+size_t node_bytes(int prec);
+
+}  // namespace rt

@@ -1,0 +1,441 @@
+// rt_trace.cuh — device-side ray tracer for the two-point ray-tracing library.
+//
+// One ray per thread. The sound-speed field is packed per node as
+// (c, h*dc/dx, h*dc/dy, s=1/c) (float4 or 32-byte double4), L2-resident, and
+// sampled bilinearly (paper Sec. 3.3.1: field and gradient are interpolated
+// from the four vertices of the enclosing cell). Positions are kept
+// cell-local: an integer cell (ci, cj) plus a fraction in [0, 1) per axis,
+// so FP32 keeps ~1e-8 of a cell of resolution anywhere on a 1024^2 grid. The
+// current cell's bilinear coefficients are cached in registers and reloaded
+// only when a sample falls in another cell (about once per 8 steps at
+// ds = h/10), which turns the march from L2-gather-bound into FMA-bound.
+//
+// Ray equations (paper Sec. 3.2.3: x and unit d evolve from the sound speed
+// and its gradient), written in cell units s~ = s/h:
+//     dX/ds~ = d,    dd/ds~ = -(g - (g.d) d) / c,    g = h grad c,
+// marched with classic RK4 at a fixed step and d renormalised after each step.
+// A trace ends at the first step (after the first) that ends on or outside the
+// ring |x| = R; the last point is replaced by the boundary interception, reached
+// by a shortened RK4 step ds' (paper Sec. 4.2), found from the chord-circle
+// root plus two Newton corrections in FP64. The travel time is the trapezoid
+// rule over the points with the interpolated slowness plus the first-order
+// endpoint correction s(x_M) d_M.(x_r - x_M) (Appendix: grad T.grad T = c^-2,
+// so grad T = s d along the ray).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rt {
+
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+template <typename T> struct NodeT;
+template <> struct NodeT<float> { using type = float4; };
+template <> struct NodeT<double> { using type = D4; };
+
+// Per-launch geometry (kernel parameter).
+struct Geom {
+    int nx, ny;
+    double h, x0, y0, R;
+    double ds;              // mm
+    int Ox, Oy;             // floor of the ring centre in cell coordinates (-x0/h, -y0/h)
+    double oxf, oyf;        // fractional parts of the ring centre
+    long long Q;            // floor((R/h)^2)
+    double q;               // (R/h)^2 - Q
+    long long max_steps;    // ceil(8 R / ds)
+    const double* tx;       // [2 n_tx]
+    int n_tx;
+    const int* pairs;       // [2 n_pairs] or null
+    int n_pairs;
+    const int* bad_field;   // device flag set by the pack kernel (c <= 0 or NaN)
+};
+
+__device__ __forceinline__ void pair_of(const Geom& G, int k, int& e, int& r) {
+    if (G.pairs) {
+        e = G.pairs[2 * k];
+        r = G.pairs[2 * k + 1];
+    } else {
+        int n1 = G.n_tx - 1;
+        e = k / n1;
+        int rr = k - e * n1;
+        r = rr + (rr >= e);
+    }
+}
+
+__device__ __forceinline__ float rcp_approx(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
+
+// ---------------------------------------------------------------- field cache
+
+template <typename T>
+struct Cell {
+    using V = typename NodeT<T>::type;
+    const V* __restrict__ F;
+    int nx, ny;
+    int pi, pj;                       // cached cell
+    T ca, cbx, cby, cbxy;             // c      = ca + tx cbx + ty (cby + tx cbxy)
+    T xa, xbx, xby, xbxy;             // h dc/dx
+    T ya, ybx, yby, ybxy;             // h dc/dy
+    T sa, sbx, sby, sbxy;             // s
+
+    __device__ __forceinline__ void load(int i, int j) {
+        pi = i;
+        pj = j;
+        // clamp for memory safety; rays stay inside by the ring/grid check
+        i = min(max(i, 0), nx - 2);
+        j = min(max(j, 0), ny - 2);
+        const V* p = F + (size_t)j * nx + i;
+        V n00 = p[0], n10 = p[1], n01 = p[nx], n11 = p[nx + 1];
+        ca = n00.x; cbx = n10.x - n00.x; cby = n01.x - n00.x; cbxy = (n11.x - n10.x) - (n01.x - n00.x);
+        xa = n00.y; xbx = n10.y - n00.y; xby = n01.y - n00.y; xbxy = (n11.y - n10.y) - (n01.y - n00.y);
+        ya = n00.z; ybx = n10.z - n00.z; yby = n01.z - n00.z; ybxy = (n11.z - n10.z) - (n01.z - n00.z);
+        sa = n00.w; sbx = n10.w - n00.w; sby = n01.w - n00.w; sbxy = (n11.w - n10.w) - (n01.w - n00.w);
+    }
+
+    // (u, v): fractions relative to cell (ci, cj), possibly outside [0, 1)
+    __device__ __forceinline__ void at(int ci, int cj, T u, T v, T& c, T& gx, T& gy, T& tx, T& ty) {
+        T fu = floor(u), fv = floor(v);
+        int i = ci + (int)fu, j = cj + (int)fv;
+        tx = u - fu;
+        ty = v - fv;
+        if (i != pi || j != pj) load(i, j);
+        c = ca + tx * cbx + ty * (cby + tx * cbxy);
+        gx = xa + tx * xbx + ty * (xby + tx * xbxy);
+        gy = ya + tx * ybx + ty * (yby + tx * ybxy);
+    }
+
+    // slowness at fractions (tx, ty) of the cached cell
+    __device__ __forceinline__ T slow(T tx, T ty) const { return sa + tx * sbx + ty * (sby + tx * sbxy); }
+};
+
+// ---------------------------------------------------------------- direction
+
+template <typename T> struct Dir;
+
+// FP64: plain unit vector
+template <> struct Dir<double> {
+    double x, y;
+    __device__ __forceinline__ void set(double th) { sincos(th, &y, &x); }
+    __device__ __forceinline__ double hx() const { return x; }
+    __device__ __forceinline__ double hy() const { return y; }
+    __device__ __forceinline__ double lx() const { return 0.0; }
+    __device__ __forceinline__ double ly() const { return 0.0; }
+    __device__ __forceinline__ void add_normalize(double ix, double iy) {
+        x += ix;
+        y += iy;
+        double n = sqrt(x * x + y * y);
+        x /= n;
+        y /= n;
+    }
+    __device__ __forceinline__ double dx() const { return x; }
+    __device__ __forceinline__ double dy() const { return y; }
+};
+
+// FP32-compensated: double-float unit vector (hi + lo), so that thousands of
+// small RK4 increments do not random-walk the ray angle by FP32 rounding.
+template <> struct Dir<float> {
+    float x, y, ex, ey;   // value = (x + ex, y + ey)
+    __device__ __forceinline__ void set(double th) {
+        double c, s;
+        sincos(th, &s, &c);
+        x = (float)c; ex = (float)(c - (double)x);
+        y = (float)s; ey = (float)(s - (double)y);
+    }
+    __device__ __forceinline__ float hx() const { return x; }
+    __device__ __forceinline__ float hy() const { return y; }
+    __device__ __forceinline__ float lx() const { return ex; }
+    __device__ __forceinline__ float ly() const { return ey; }
+    __device__ __forceinline__ void add_normalize(float ix, float iy) {
+        // two-sum of hi + increment, error into lo
+        float s = x + ix, bb = s - x;
+        ex += (x - (s - bb)) + (ix - bb);
+        x = s;
+        s = y + iy; bb = s - y;
+        ey += (y - (s - bb)) + (iy - bb);
+        y = s;
+        // |d|^2 - 1 to first order in lo, then d *= 1/sqrt(1+e) = 1 + delta
+        float e = fmaf(x, x, fmaf(y, y, -1.0f)) + 2.0f * (x * ex + y * ey);
+        float delta = e * fmaf(0.375f, e, -0.5f);
+        ex = fmaf(x + ex, delta, ex);
+        ey = fmaf(y + ey, delta, ey);
+        // renormalise the hi/lo split (fast two-sum, |hi| >= |lo|)
+        s = x + ex; ex -= s - x; x = s;
+        s = y + ey; ey -= s - y; y = s;
+    }
+    __device__ __forceinline__ double dx() const { return (double)x + (double)ex; }
+    __device__ __forceinline__ double dy() const { return (double)y + (double)ey; }
+};
+
+// ---------------------------------------------------------------- RK4 in cell units
+
+template <typename T>
+struct RayState {
+    int ci, cj;
+    T fx, fy;
+    Dir<T> d;
+};
+
+// (g.e) e - g over c for stage direction e
+template <typename T>
+__device__ __forceinline__ void ray_rhs(T c, T gx, T gy, T ex, T ey, T& kx, T& ky) {
+    T ic = rcp_approx(c);
+    T gd = gx * ex + gy * ey;
+    kx = (gd * ex - gx) * ic;
+    ky = (gd * ey - gy) * ic;
+}
+
+// One RK4 step of length H (cell units) from S into N. s_here receives the
+// slowness at S's position (stage-1 sample) for the trapezoid rule.
+template <typename T>
+__device__ __forceinline__ void rk4_step(Cell<T>& C, const RayState<T>& S, T H, RayState<T>& N, T& s_here,
+                                         T& tx1, T& ty1, int& i1, int& j1) {
+    const T Hh = (T)0.5 * H, H6 = H / (T)6;
+    const T dx = S.d.hx(), dy = S.d.hy();
+    T c, gx, gy, tx, ty, k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
+    C.at(S.ci, S.cj, S.fx, S.fy, c, gx, gy, tx1, ty1);
+    i1 = C.pi;
+    j1 = C.pj;
+    s_here = C.slow(tx1, ty1);
+    ray_rhs(c, gx, gy, dx, dy, k1x, k1y);
+    T e2x = dx + Hh * k1x, e2y = dy + Hh * k1y;
+    C.at(S.ci, S.cj, S.fx + Hh * dx, S.fy + Hh * dy, c, gx, gy, tx, ty);
+    ray_rhs(c, gx, gy, e2x, e2y, k2x, k2y);
+    T e3x = dx + Hh * k2x, e3y = dy + Hh * k2y;
+    C.at(S.ci, S.cj, S.fx + Hh * e2x, S.fy + Hh * e2y, c, gx, gy, tx, ty);
+    ray_rhs(c, gx, gy, e3x, e3y, k3x, k3y);
+    T e4x = dx + H * k3x, e4y = dy + H * k3y;
+    C.at(S.ci, S.cj, S.fx + H * e3x, S.fy + H * e3y, c, gx, gy, tx, ty);
+    ray_rhs(c, gx, gy, e4x, e4y, k4x, k4y);
+    T nfx = S.fx + H6 * ((dx + S.d.lx()) + (T)2 * (e2x + e3x) + e4x);
+    T nfy = S.fy + H6 * ((dy + S.d.ly()) + (T)2 * (e2y + e3y) + e4y);
+    N.d = S.d;
+    N.d.add_normalize(H6 * (k1x + (T)2 * (k2x + k3x) + k4x), H6 * (k1y + (T)2 * (k2y + k3y) + k4y));
+    N.ci = S.ci;
+    N.cj = S.cj;
+    if (nfx >= (T)1) { N.ci += 1; nfx -= (T)1; } else if (nfx < (T)0) { N.ci -= 1; nfx += (T)1; }
+    if (nfy >= (T)1) { N.cj += 1; nfy -= (T)1; } else if (nfy < (T)0) { N.cj -= 1; nfy += (T)1; }
+    N.fx = nfx;
+    N.fy = nfy;
+}
+
+// |x|^2 - (R/h)^2 in cell^2 units, exact integer part plus a small fractional
+// part, so the sign is reliable to ~1e-7 cell even in FP32.
+template <typename T>
+__device__ __forceinline__ T ring_excess(const Geom& G, const RayState<T>& S) {
+    int Ix = S.ci - G.Ox, Iy = S.cj - G.Oy;
+    T px = S.fx - (T)G.oxf, py = S.fy - (T)G.oyf;
+    long long I2 = (long long)Ix * Ix + (long long)Iy * Iy - G.Q;
+    T d0 = (T)I2 - (T)G.q;
+    return d0 + (T)2 * ((T)Ix * px + (T)Iy * py) + px * px + py * py;
+}
+
+template <typename T>
+__device__ __forceinline__ void abs_pos(const Geom& G, const RayState<T>& S, double& X, double& Y) {
+    X = G.x0 + G.h * ((double)S.ci + (double)S.fx);
+    Y = G.y0 + G.h * ((double)S.cj + (double)S.fy);
+}
+
+// ---------------------------------------------------------------- scatter (adjoint / matrix rows)
+
+// Accumulates the trapezoid-weighted bilinear weights of consecutive points
+// that fall in one cell, as (sum w, sum w tx, sum w ty, sum w tx ty).
+template <typename T>
+struct CellAcc {
+    int ai, aj;
+    T W, Wx, Wy, Wxy;
+    __device__ __forceinline__ void reset() { ai = INT_MIN; aj = INT_MIN; W = Wx = Wy = Wxy = (T)0; }
+    __device__ __forceinline__ void node_weights(double& w00, double& w10, double& w01, double& w11) const {
+        w11 = (double)Wxy;
+        w10 = (double)Wx - w11;
+        w01 = (double)Wy - w11;
+        w00 = (double)W - (double)Wx - (double)Wy + w11;
+    }
+};
+
+// Trace outcome.
+struct TraceOut {
+    double T;          // travel time (us) incl. endpoint correction
+    double hx, hy;     // interception
+    int flags;         // bit0: step cap, bit1: left outward at once
+    long long steps;   // RK4 steps taken (incl. landing)
+};
+
+// Sink interface used by trace(): add(ci, cj, tx, ty, w) for each point.
+struct NoSink {
+    template <typename T>
+    __device__ __forceinline__ void add(int, int, T, T, T) {}
+    __device__ __forceinline__ void finish() {}
+};
+
+// Resumable trace: begin / step (until it reports the end) / end. The
+// persistent linking kernel interleaves traces of different pairs per lane.
+template <typename T>
+struct TraceState {
+    RayState<T> S;
+    T s_first, s_cur;
+    T Ssum, Scomp;            // Kahan sum of s at points 1..M-1
+    int m;                    // index of the current point
+    int safe;                 // steps that cannot reach the ring (exit test skipped)
+    int flags;                // bit0 step cap, bit1 left outward at once
+    int iL, jL;               // cell and fractions of the last full-step point
+    T txL, tyL;
+    long long steps;
+};
+
+template <typename T>
+__device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, double xe, double ye, double theta) {
+    const double u = (xe - G.x0) / G.h, v = (ye - G.y0) / G.h;
+    const double fu = floor(u), fv = floor(v);
+    ts.S.ci = (int)fu;
+    ts.S.cj = (int)fv;
+    ts.S.fx = (T)(u - fu);
+    ts.S.fy = (T)(v - fv);
+    ts.S.d.set(theta);
+    ts.s_first = ts.s_cur = (T)0;
+    ts.Ssum = ts.Scomp = (T)0;
+    ts.m = 0;
+    ts.safe = 0;
+    ts.flags = 0;
+    ts.iL = ts.jL = 0;
+    ts.txL = ts.tyL = (T)0;
+    ts.steps = 0;
+}
+
+// One RK4 step. Returns true when the trace has ended: the step ended on or
+// outside the ring (flags bit1 if that was the very first step) or the step
+// cap was reached (flags bit0). On exit ts.S is still the last inside point.
+template <typename T, typename Sink>
+__device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState<T>& ts, Sink& sink) {
+    if (ts.m >= G.max_steps) {
+        ts.flags |= 1;
+        return true;
+    }
+    const T H = (T)(G.ds / G.h);
+    const T dsT = (T)G.ds;
+    RayState<T> N;
+    T tx1, ty1;
+    int i1, j1;
+    rk4_step(C, ts.S, H, N, ts.s_cur, tx1, ty1, i1, j1);
+    ++ts.steps;
+    bool ends_out = false;
+    if (--ts.safe < 0) {
+        const T ex = ring_excess(G, N);
+        ends_out = ex >= (T)0;
+        if (!ends_out) {
+            // distance to the ring in cells, -ex / (R + r); no step moves farther than ~H
+            const T Rc = (T)(G.R / G.h);
+            const T r = sqrt(Rc * Rc + ex);
+            const T dist = -ex / (Rc + r);
+            ts.safe = (int)(dist * (T)0.98 / H) - 1;
+        }
+    }
+    if (ts.m == 0) {
+        if (ends_out) {   // left outward: no path, no weights
+            ts.flags |= 2;
+            return true;
+        }
+        ts.s_first = ts.s_cur;
+        sink.add(i1, j1, tx1, ty1, (T)0.5 * dsT);
+    } else {
+        const T y = ts.s_cur - ts.Scomp;
+        const T t = ts.Ssum + y;
+        ts.Scomp = (t - ts.Ssum) - y;
+        ts.Ssum = t;
+        sink.add(i1, j1, tx1, ty1, dsT);
+        if (ends_out) {
+            ts.iL = i1; ts.jL = j1; ts.txL = tx1; ts.tyL = ty1;
+            return true;
+        }
+    }
+    ts.S = N;
+    ++ts.m;
+    return false;
+}
+
+// Landing, travel time and final weights of an ended trace. The endpoint
+// correction is taken toward (xr, yr).
+template <typename T, typename Sink>
+__device__ TraceOut trace_end(Cell<T>& C, const Geom& G, TraceState<T>& ts, double xe, double ye, double xr,
+                              double yr, Sink& sink) {
+    TraceOut out;
+    out.flags = ts.flags;
+    if (ts.flags & 1) {
+        // step cap: no interception; report the current point
+        abs_pos(G, ts.S, out.hx, out.hy);
+        out.T = G.ds * (0.5 * (double)ts.s_first + ((double)ts.Ssum - (double)ts.Scomp));
+        out.steps = ts.steps;
+        sink.finish();
+        return out;
+    }
+    if (ts.flags & 2) {
+        out.T = 0.0;
+        out.hx = xe;
+        out.hy = ye;
+        out.steps = ts.steps;
+        sink.finish();
+        return out;
+    }
+    const RayState<T>& S = ts.S;
+    RayState<T> N;
+    double X, Y;
+    abs_pos(G, S, X, Y);
+    double b = X * S.d.dx() + Y * S.d.dy();
+    double qq = X * X + Y * Y - G.R * G.R;
+    double disc = b * b - qq;
+    if (disc < 0) disc = 0;
+    double sq = sqrt(disc);
+    double t = (b >= 0) ? (-qq) / (b + sq) : (sq - b);
+    if (!(t >= 0)) t = 0;
+    if (t > G.ds) t = G.ds;
+    T s_dummy, txd, tyd;
+    int id, jd;
+    for (int it = 0; it < 2; ++it) {
+        rk4_step(C, S, (T)(t / G.h), N, s_dummy, txd, tyd, id, jd);
+        ++ts.steps;
+        double NX, NY;
+        abs_pos(G, N, NX, NY);
+        double r = sqrt(NX * NX + NY * NY);
+        double drdt = (NX * N.d.dx() + NY * N.d.dy()) / r;
+        if (drdt > 0) t -= (r - G.R) / drdt;
+        if (!(t >= 0)) t = 0;
+        if (t > G.ds) t = G.ds;
+    }
+    rk4_step(C, S, (T)(t / G.h), N, s_dummy, txd, tyd, id, jd);
+    ++ts.steps;
+    double MX, MY;
+    abs_pos(G, N, MX, MY);
+    T c_, gx_, gy_, txM, tyM;
+    C.at(N.ci, N.cj, N.fx, N.fy, c_, gx_, gy_, txM, tyM);
+    const int iM = C.pi, jM = C.pj;
+    const double sM = (double)C.slow(txM, tyM);
+    const double sL = (double)ts.s_cur;   // slowness at x_{M-1}
+    const double corr = N.d.dx() * (xr - MX) + N.d.dy() * (yr - MY);
+    const double S_int = (double)ts.Ssum - (double)ts.Scomp;   // s_1 + ... + s_{M-1}
+    out.T = G.ds * (0.5 * (double)ts.s_first + S_int - 0.5 * sL) + 0.5 * t * (sL + sM) + sM * corr;
+    out.hx = MX;
+    out.hy = MY;
+    out.steps = ts.steps;
+    // alpha_{M-1} = (ds + ds')/2 (ds was given by trace_step), alpha_M = ds'/2 + corr
+    sink.add(ts.iL, ts.jL, ts.txL, ts.tyL, (T)(0.5 * (t - G.ds)));
+    sink.add(iM, jM, txM, tyM, (T)(0.5 * t + corr));
+    sink.finish();
+    return out;
+}
+
+// Traces one ray from (xe, ye) at angle theta (begin + steps + end). With a
+// sink, every sample point m reports its trapezoid weight alpha_m (and the
+// endpoint weight) with its cell and fractions.
+template <typename T, typename Sink>
+__device__ TraceOut trace_ray(Cell<T>& C, const Geom& G, double xe, double ye, double theta, double xr,
+                              double yr, Sink& sink) {
+    TraceState<T> ts;
+    trace_begin(ts, G, xe, ye, theta);
+    while (!trace_step(C, G, ts, sink)) {
+    }
+    return trace_end(C, G, ts, xe, ye, xr, yr, sink);
+}
+
+}  // namespace rt

@@ -1,0 +1,53 @@
+"""CPU-side checks of the boundary: the shared library builds for sm_103a,
+loads, and exports every function include/rt.h declares (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt[a-z_]*)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_18511_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_ray_path_calls():
+    names = _declared()
+    for n in ("rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
+              "rt_ctx_create", "rt_ctx_destroy", "rt_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2511_18511_gb300 import _lib
+    for n in _declared():
+        assert hasattr(lib, n), f"{n} declared in rt.h but not exported"
+    assert set(_declared()) == set(_lib.EXPORTED)
+
+
+def test_version_without_gpu(lib):
+    assert lib.rt_version() == 1
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    from paper_2511_18511_gb300 import _lib
+    assert lib.rt_ctx_create(None, 0) == _lib.RT_EINVAL
+    assert lib.rt_link(None, None, None, None, None, None, None, None, None) == _lib.RT_EINVAL
+    counts = (ctypes.c_int64 * 8)()
+    assert lib.rt_status_counts(None, counts, None) == _lib.RT_EINVAL
+
+
+def test_library_built_for_sm103a_only():
+    from paper_2511_18511_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -28,8 +28,10 @@ MUTANTS = {
     "endpoint_correction_sign": ("T += s_prev * corr;", "T -= s_prev * corr;"),
     "endpoint_weight_missing": ("alpha[m] += corr;", "(void)corr;"),
     "landing_no_newton": ("for (int it = 0; it < 2; ++it) {", "for (int it = 0; it < 0; ++it) {"),
-    "secant_sign": ("if (ok) next = cur.theta - cur.m * (cur.theta - prev.theta) / den;",
-                    "if (ok) next = cur.theta + cur.m * (cur.theta - prev.theta) / den;"),
+    "secant_sign": ("next = ok ? cur.theta - cur.m * (cur.theta - prev.theta) / den : 0.0;",
+                    "next = ok ? cur.theta + cur.m * (cur.theta - prev.theta) / den : 0.0;"),
+    "orientation_probe_flipped": ("const int ccw = (ep.m / R + psi_r) < M_PI;",
+                                  "const int ccw = (ep.m / R + psi_r) > M_PI;"),
     "adjoint_missing_chain": ("g_c[j] = -1000.0 * sum / (c_mps[j] * c_mps[j]);",
                               "g_c[j] = -1000.0 * sum / c_mps[j];"),
     "adjoint_drop_alpha": ("gs[S.k[q]] += g_tof[k] * alpha[m] * S.w[q];",

@@ -95,8 +95,9 @@ def test_linear_gradient_closed_form(orc, gslope):
     pairs = P.all_pairs(64)
     r = orc.link(g, c, tx, R, 0.05, tol=1e-9)
     assert (r["status"] == 0).all()
-    # smooth monotone misfit: the secant converges superlinearly (measured <= 4 traces)
-    assert r["iters"].max() <= 5
+    # smooth monotone misfit: the secant converges superlinearly (measured <= 6
+    # traces at tol 1e-9, the orientation probe included)
+    assert r["iters"].max() <= 6
     T = _lin_closed_form(tx, pairs, 1500.0, gslope)
     bound = 1.5 * (g.h * gslope * 1e-3) ** 2 / (4 * 1.47 ** 2)
     assert np.abs(r["tof"] / T - 1).max() < bound
