@@ -48,7 +48,30 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "link_traffic.json"))
+    ap.add_argument("--profile", type=int, default=0, metavar="N_EMIT",
+                    help="small case for ncu: one warm-up and one rt_link (fp32c) over the pairs of the "
+                         "first N_EMIT emitters of the workload, then exit")
+    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"],
+                    help="precision of the --profile case")
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """One rt_link on a subset of pairs of the full-size workload (ncu captures)."""
+    import torch
+    import paper_2511_18511_gb300 as rt
+    from paper_2511_18511_gb300 import phantoms as P
+    w = workload(0)
+    pairs = P.all_pairs(w.n_tx)
+    pairs = pairs[pairs[:, 0] < args.profile]
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, pairs=pairs)
+    for _ in range(2):
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision)
+    torch.cuda.synchronize()
+    ok, counts = rt.rt_status_counts()
+    print(json.dumps({"profile_case": w.name, "pairs": int(len(pairs)), "precision": args.precision,
+                      "all_linked": ok, "rk4_steps": counts[7],
+                      "mean_traces": float(r["iters"].float().mean().item())}))
 
 
 def dist_env():
@@ -161,6 +184,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile_case(args)
     import torch
     import paper_2511_18511_gb300 as rt
 

@@ -98,7 +98,8 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     if (!(-need >= xl && need <= xh && -need >= yl && need <= yh))
         return fail(ctx, RT_EINVAL, "ring (plus one step and one cell) must lie inside the grid");
     const double Rc = R / g.h_mm;
-    if (Rc * Rc > 9.0e15) return fail(ctx, RT_EINVAL, "ring too large in cells");
+    if (Rc * Rc > 1.0e8 || g.nx > 16384 || g.ny > 16384)
+        return fail(ctx, RT_EINVAL, "ring or grid too large (at most 16384 nodes per axis)");
     G->nx = g.nx;
     G->ny = g.ny;
     G->h = g.h_mm;
@@ -120,6 +121,14 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     G->pairs = p->pairs;
     G->n_pairs = p->n_pairs;
     G->bad_field = nullptr;
+    if (G->Q > (long long)INT32_MAX / 2) return fail(ctx, RT_EINVAL, "ring too large in cells");
+    G->Qi = (int)G->Q;
+    G->Hf = (float)(o->ds_mm / g.h_mm);
+    G->dsf = (float)o->ds_mm;
+    G->Rcf = (float)Rc;
+    G->oxff = (float)G->oxf;
+    G->oyff = (float)G->oyf;
+    G->qf = (float)G->q;
     return RT_OK;
 }
 

@@ -182,6 +182,21 @@ __device__ bool link_update(const Geom& G, LinkState& L, const TraceOut& o, doub
     return false;
 }
 
+// Work order of the persistent kernel. For the all-pairs list, queue slot q
+// serves ring offsets o = r - e (mod N) from the longest chord (o = N/2) down to
+// the shortest (o = 1, N-1), N emitters per offset, so the launch's tail is
+// made of the shortest rays; the pair's own index k is returned. Explicit pair
+// lists are served in their order.
+__device__ __forceinline__ int queue_pair(const Geom& G, int q) {
+    if (G.pairs) return q;
+    const int N = G.n_tx;
+    const int t = q / N, e = q - t * N;
+    const int h = (N + 1) / 2;
+    const int o = (t & 1) ? h - (t + 1) / 2 : h + t / 2;
+    const int r = (e + o) % N;
+    return e * (N - 1) + r - (r > e);
+}
+
 // Warp-aggregated fetch of the next pair index from the work queue.
 __device__ __forceinline__ int fetch_pair(int* queue) {
     const unsigned mask = __activemask();
@@ -214,8 +229,9 @@ __global__ void __launch_bounds__(kLinkBlock) k_link(Geom G, const typename Node
     bool active = false;
     for (;;) {
         if (!active) {
-            const int k = fetch_pair(queue);
-            if (k >= G.n_pairs) break;
+            const int qslot = fetch_pair(queue);
+            if (qslot >= G.n_pairs) break;
+            const int k = queue_pair(G, qslot);
             LinkCtx X;
             if (!setup_pair(G, k, X)) {
                 theta[k] = nan("");

@@ -51,6 +51,28 @@ struct Geom {
     const int* pairs;       // [2 n_pairs] or null
     int n_pairs;
     const int* bad_field;   // device flag set by the pack kernel (c <= 0 or NaN)
+    // FP32 copies of the per-step constants, so the FP32 march issues no FP64
+    float Hf, dsf, Rcf, oxff, oyff, qf;
+    int Qi;                 // Q as 32-bit (grids up to 32k cells per side)
+};
+
+// Per-step constants in the marching precision.
+template <typename T> struct StepK;
+template <> struct StepK<float> {
+    __device__ __forceinline__ static float H(const Geom& G) { return G.Hf; }
+    __device__ __forceinline__ static float ds(const Geom& G) { return G.dsf; }
+    __device__ __forceinline__ static float Rc(const Geom& G) { return G.Rcf; }
+    __device__ __forceinline__ static float oxf(const Geom& G) { return G.oxff; }
+    __device__ __forceinline__ static float oyf(const Geom& G) { return G.oyff; }
+    __device__ __forceinline__ static float q(const Geom& G) { return G.qf; }
+};
+template <> struct StepK<double> {
+    __device__ __forceinline__ static double H(const Geom& G) { return G.ds / G.h; }
+    __device__ __forceinline__ static double ds(const Geom& G) { return G.ds; }
+    __device__ __forceinline__ static double Rc(const Geom& G) { return G.R / G.h; }
+    __device__ __forceinline__ static double oxf(const Geom& G) { return G.oxf; }
+    __device__ __forceinline__ static double oyf(const Geom& G) { return G.oyf; }
+    __device__ __forceinline__ static double q(const Geom& G) { return G.q; }
 };
 
 __device__ __forceinline__ void pair_of(const Geom& G, int k, int& e, int& r) {
@@ -65,7 +87,12 @@ __device__ __forceinline__ void pair_of(const Geom& G, int k, int& e, int& r) {
     }
 }
 
-__device__ __forceinline__ float rcp_approx(float x) { return __frcp_rn(x); }
+// 1/c for the ray equations: the hardware approximation (about 1 ulp) in FP32.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
 
 // ---------------------------------------------------------------- field cache
@@ -225,10 +252,10 @@ __device__ __forceinline__ void rk4_step(Cell<T>& C, const RayState<T>& S, T H, 
 // part, so the sign is reliable to ~1e-7 cell even in FP32.
 template <typename T>
 __device__ __forceinline__ T ring_excess(const Geom& G, const RayState<T>& S) {
-    int Ix = S.ci - G.Ox, Iy = S.cj - G.Oy;
-    T px = S.fx - (T)G.oxf, py = S.fy - (T)G.oyf;
-    long long I2 = (long long)Ix * Ix + (long long)Iy * Iy - G.Q;
-    T d0 = (T)I2 - (T)G.q;
+    const int Ix = S.ci - G.Ox, Iy = S.cj - G.Oy;
+    const T px = S.fx - StepK<T>::oxf(G), py = S.fy - StepK<T>::oyf(G);
+    const int I2 = Ix * Ix + Iy * Iy - G.Qi;
+    const T d0 = (T)I2 - StepK<T>::q(G);
     return d0 + (T)2 * ((T)Ix * px + (T)Iy * py) + px * px + py * py;
 }
 
@@ -313,8 +340,8 @@ __device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState
         ts.flags |= 1;
         return true;
     }
-    const T H = (T)(G.ds / G.h);
-    const T dsT = (T)G.ds;
+    const T H = StepK<T>::H(G);
+    const T dsT = StepK<T>::ds(G);
     RayState<T> N;
     T tx1, ty1;
     int i1, j1;
@@ -326,7 +353,7 @@ __device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState
         ends_out = ex >= (T)0;
         if (!ends_out) {
             // distance to the ring in cells, -ex / (R + r); no step moves farther than ~H
-            const T Rc = (T)(G.R / G.h);
+            const T Rc = StepK<T>::Rc(G);
             const T r = sqrt(Rc * Rc + ex);
             const T dist = -ex / (Rc + r);
             ts.safe = (int)(dist * (T)0.98 / H) - 1;
