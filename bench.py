@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "link_traffic.json"))
     ap.add_argument("--profile", type=int, default=0, metavar="N_EMIT",
-                    help="small case for ncu: one warm-up and one rt_link (fp32c) over the pairs of the "
-                         "first N_EMIT emitters of the workload, then exit")
+                    help="case for ncu captures: twice rt_link + rt_tof_adjoint (fp32c) over the pairs of "
+                         "the first N_EMIT emitters of the workload, then exit")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"],
                     help="precision of the --profile case")
     return ap.parse_args()
@@ -67,6 +67,7 @@ def run_profile_case(args):
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, pairs=pairs)
     for _ in range(2):
         r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision)
+        rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=r["tof"] * 0.999, precision=args.precision)
     torch.cuda.synchronize()
     ok, counts = rt.rt_status_counts()
     print(json.dumps({"profile_case": w.name, "pairs": int(len(pairs)), "precision": args.precision,

@@ -76,6 +76,12 @@ typedef struct {
     int32_t max_iter;    /* traces per pair in rt_link, >= 2 (30 is the usual) */
     double ds_mm;        /* fixed RK4 step length > 0 */
     double tol_mm;       /* linking tolerance on |x_hit - x_r| > 0 */
+    int32_t fan_rays;    /* cold starts: 0 = straight line to the receiver (paper
+                            Sec. 3.4.1) with a near-tangent orientation probe; K >= 2 =
+                            a fan of K rays per emitter predicts the first angle
+                            and a bracket (256 is the usual); ignored by the calls
+                            that take fixed angles */
+    int32_t reserved;    /* must be 0 */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
@@ -115,9 +121,10 @@ int rt_ctx_reserve(rt_ctx* ctx, int64_t max_nodes);
  * replaced by the interception, shortened last step), Sec. 3.4.1 (first
  * linearisation starts from straight rays, later ones warm-start from the
  * previous angles).
- *   theta_io  [n_pairs] launch angle (rad, from +x). In: NaN = start from the
- *             straight line to the receiver, else warm start. Out: angle of
- *             the linked ray (the traced ray closest to the receiver).
+ *   theta_io  [n_pairs] launch angle (rad, from +x). In: NaN = cold start
+ *             (straight line, or the fan prediction when opt->fan_rays >= 2),
+ *             else warm start. Out: angle of the linked ray (the traced ray
+ *             closest to the receiver).
  *   tof_us    [n_pairs] travel time of the linked ray (or NULL).
  *   hit_xy_mm [2*n_pairs] boundary interception of the linked ray (or NULL).
  *   status    [n_pairs] enum rt_ray_status (or NULL).

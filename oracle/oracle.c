@@ -42,6 +42,7 @@
  *      inside the bracket, else Regula-Falsi (Sec. 3.4) with the Illinois
  *      halving; at most max_iter traces (the probe counts); the reported ray
  *      is the evaluated one closest to the receiver;
+ *   R8 fan start for cold starts (optional, see link_pair_fan);
  *   R7 adjoint: the rays are frozen at the linked angles (Fermat: the first
  *      order path change does not move T), so the gradient is the transpose
  *      of the system matrix whose rows are interpolation-weighted path lengths
@@ -400,6 +401,139 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
     *n_eval_out = n_eval;
 }
 
+/* R8 fan start (an option; fan_rays = 0 keeps the straight-line start of
+ * Sec. 3.4.1). A fan of K rays per emitter at evenly spaced angles over the
+ * inward fan, theta_k = a_min + k (a_max - a_min)/(K-1), gives the
+ * interception angle psi_k of each; ray 0 (next to the fan's lower end) fixes
+ * the sweep orientation exactly as the probe does. For a pair, the sequence of
+ * misfits (fan end, rays 0..K-1, fan end) is scanned for sign changes; the one
+ * whose middle lies closest to the straight-line angle, both counted in fan-ray
+ * index units, is taken and its ends form the bracket. The first angle is the root of the inverse cubic
+ * through the four fan rays around the interval when they exist and their
+ * misfits are strictly monotone and the root falls inside the interval, else
+ * the linear interpolation of the interval. The end with the smaller |misfit|
+ * is the secant partner of the first trace. */
+static double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
+
+static void fan_for_emitter(const Field* F, double R, const double* xe, double ds, int K, double* psi) {
+    const double phi_e = atan2(xe[1], xe[0]);
+    const double th_lo = phi_e + 0.5 * M_PI, th_hi = phi_e + 1.5 * M_PI;
+    double margin = ds / R;
+    if (margin < 1e-9) margin = 1e-9;
+    const double a_min = th_lo + margin, a_max = th_hi - margin;
+    const double step = (a_max - a_min) / (K - 1);
+    for (int k = 0; k < K; ++k) {
+        TraceRes tr;
+        trace(F, R, xe[0], xe[1], xe[0], xe[1], fan_theta(a_min, step, k), ds, NULL, NULL, 0, &tr);
+        psi[k] = (tr.flags & 3) ? NAN : mod_2pi(atan2(tr.hit[1], tr.hit[0]) - phi_e);
+    }
+}
+
+static void link_pair_fan(const Field* F, double R, const double* xe, const double* xr, double ds,
+                          double tol, int max_iter, const double* psi, int K, Eval* best, int* status,
+                          int* n_eval_out) {
+    const double phi_e = atan2(xe[1], xe[0]);
+    const double psi_r = mod_2pi(atan2(xr[1], xr[0]) - phi_e);
+    const double th_lo = phi_e + 0.5 * M_PI, th_hi = phi_e + 1.5 * M_PI;
+    double margin = ds / R;
+    if (margin < 1e-9) margin = 1e-9;
+    const double a_min = th_lo + margin, a_max = th_hi - margin;
+    if (max_iter < 2) max_iter = 2;
+    const int ccw = isnan(psi[0]) ? 1 : (psi[0] < M_PI);
+    const double psi_at_lo = ccw ? 0.0 : 2.0 * M_PI;
+    const double step = (a_max - a_min) / (K - 1);
+    double th_s = atan2(xr[1] - xe[1], xr[0] - xe[0]);
+    th_s = th_lo + mod_2pi(th_s - th_lo);
+    const double u_s = (th_s - a_min) / step;   /* straight-line angle in fan-index units */
+    const double psi_hi_end = 2.0 * M_PI - psi_at_lo;
+    /* sequence index j: 0 fan lower end, 1..K rays 0..K-1, K+1 fan upper end;
+     * the interval (j-1, j) has its middle at fan index j - 1.5 */
+    int neg_prev = psi_at_lo < psi_r;
+    int jsel = K + 1;
+    double best_gap = INFINITY;
+    for (int j = 1; j <= K + 1; ++j) {
+        double p;
+        if (j <= K) {
+            const int k = j - 1;
+            p = isnan(psi[k]) ? ((k < K / 2) ? psi_at_lo : psi_hi_end) : psi[k];
+        } else {
+            p = psi_hi_end;
+        }
+        const int neg = p < psi_r;
+        if (neg != neg_prev) {
+            const double gap = fabs((j - 1.5) - u_s);
+            if (gap < best_gap) { best_gap = gap; jsel = j; }
+        }
+        neg_prev = neg;
+    }
+    /* ends of the chosen interval */
+    double t0, m0, t1, m1;
+    {
+        const int ja = jsel - 1, jb = jsel;
+        double pa, pb;
+        if (ja == 0) { t0 = th_lo; pa = psi_at_lo; }
+        else { const int k = ja - 1; t0 = fan_theta(a_min, step, k); pa = isnan(psi[k]) ? ((k < K / 2) ? psi_at_lo : psi_hi_end) : psi[k]; }
+        if (jb == K + 1) { t1 = th_hi; pb = psi_hi_end; }
+        else { const int k = jb - 1; t1 = fan_theta(a_min, step, k); pb = isnan(psi[k]) ? ((k < K / 2) ? psi_at_lo : psi_hi_end) : psi[k]; }
+        m0 = R * (pa - psi_r);
+        m1 = R * (pb - psi_r);
+    }
+    Bracket B;
+    if (m0 < 0) { B.ta = t0; B.fa = m0; B.tb = t1; B.fb = m1; }
+    else { B.ta = t1; B.fa = m1; B.tb = t0; B.fb = m0; }
+    B.last = 0;
+    double th0 = t0 - m0 * (t1 - t0) / (m1 - m0);
+    /* rays around the interval (j-1, j): k0 = j-2 and k0+1 = j-1 */
+    const int k0 = jsel - 2;
+    if (k0 >= 1 && k0 + 2 <= K - 1) {
+        double tt[4], mm[4];
+        int ok = 1;
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 - 1 + q;
+            if (isnan(psi[k])) ok = 0;
+            tt[q] = fan_theta(a_min, step, k);
+            mm[q] = R * (psi[k] - psi_r);
+        }
+        for (int q = 0; q < 3 && ok; ++q)
+            if (!((mm[q + 1] - mm[q]) * (mm[2] - mm[1]) > 0)) ok = 0;
+        if (ok) {
+            double v = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                double l = 1.0;
+                for (int b = 0; b < 4; ++b)
+                    if (b != a) l *= (0.0 - mm[b]) / (mm[a] - mm[b]);
+                v += l * tt[a];
+            }
+            if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
+        }
+    }
+    if (!(th0 > fmin(B.ta, B.tb) && th0 < fmax(B.ta, B.tb))) th0 = 0.5 * (B.ta + B.tb);
+    Eval prev, cur;
+    prev.theta = (fabs(m0) <= fabs(m1)) ? t0 : t1;
+    prev.m = (fabs(m0) <= fabs(m1)) ? m0 : m1;
+    cur = prev;
+    int n_eval = 0, conv = 0;
+    double next = th0;
+    while (n_eval < max_iter) {
+        if (n_eval > 0) {
+            double den = cur.m - prev.m;
+            next = (den != 0.0) ? cur.theta - cur.m * (cur.theta - prev.theta) / den : NAN;
+            if (!(isfinite(next) && next > fmin(B.ta, B.tb) && next < fmax(B.ta, B.tb)))
+                next = (B.ta * B.fb - B.tb * B.fa) / (B.fb - B.fa);
+        }
+        Eval e;
+        evaluate(F, R, xe, xr, phi_e, psi_r, th_lo, th_hi, psi_at_lo, ds, next, &e);
+        ++n_eval;
+        if (n_eval == 1 || e.dist < best->dist) *best = e;
+        if (e.dist <= tol) { conv = 1; break; }
+        br_insert(&B, e.theta, e.m);
+        prev = cur;
+        cur = e;
+    }
+    *status = conv ? ORC_RAY_OK : (isinf(best->dist) ? ORC_RAY_STEPCAP : ORC_RAY_MAXITER);
+    *n_eval_out = n_eval;
+}
+
 static int nthreads_of(int32_t n) {
 #ifdef _OPENMP
     return n > 0 ? n : omp_get_max_threads();
@@ -480,14 +614,28 @@ static int check_common(const orc_grid* g, int32_t n_tx, const double* tx, doubl
 
 int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
              double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
-             int32_t max_iter, double* theta_io, double* tof, double* hit_xy,
+             int32_t max_iter, int32_t fan_rays, double* theta_io, double* tof, double* hit_xy,
              int32_t* status, int32_t* iters, int32_t nthreads) {
     int rc = check_common(g, n_tx, tx, R, ds, n_pairs, pairs);
     if (rc) return rc;
-    if (!theta_io || !(tol > 0)) return ORC_EINVAL;
+    if (!theta_io || !(tol > 0) || fan_rays == 1 || fan_rays < 0) return ORC_EINVAL;
     Field F;
     rc = field_make(&F, g, c_mps);
     if (rc) return rc;
+    double* fan = NULL;
+    if (fan_rays > 0) {
+        fan = malloc((size_t)n_tx * fan_rays * sizeof(double));
+        if (!fan) { field_free(&F); return ORC_ENOMEM; }
+        char* need = calloc((size_t)n_tx, 1);
+        for (int32_t k = 0; k < n_pairs; ++k) {
+            int e, r;
+            if (pair_of(n_tx, pairs, k, &e, &r) && isnan(theta_io[k])) need[e] = 1;
+        }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads))
+        for (int32_t t = 0; t < n_tx; ++t)
+            if (need[t]) fan_for_emitter(&F, R, tx + 2 * t, ds, fan_rays, fan + (size_t)t * fan_rays);
+        free(need);
+    }
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads_of(nthreads)) reduction(| : bad)
     for (int32_t k = 0; k < n_pairs; ++k) {
@@ -500,13 +648,18 @@ int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double*
         Eval best;
         memset(&best, 0, sizeof(best));
         int st, ne;
-        link_pair(&F, R, tx + 2 * e, tx + 2 * r, ds, tol, max_iter, theta_io[k], &best, &st, &ne);
+        if (fan && isnan(theta_io[k]))
+            link_pair_fan(&F, R, tx + 2 * e, tx + 2 * r, ds, tol, max_iter, fan + (size_t)e * fan_rays, fan_rays,
+                          &best, &st, &ne);
+        else
+            link_pair(&F, R, tx + 2 * e, tx + 2 * r, ds, tol, max_iter, theta_io[k], &best, &st, &ne);
         theta_io[k] = best.theta;
         if (tof) tof[k] = best.tr.T;
         if (hit_xy) { hit_xy[2 * k] = best.tr.hit[0]; hit_xy[2 * k + 1] = best.tr.hit[1]; }
         if (status) status[k] = st;
         if (iters) iters[k] = ne;
     }
+    free(fan);
     field_free(&F);
     return bad ? ORC_EINVAL : ORC_OK;
 }

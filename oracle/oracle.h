@@ -61,11 +61,13 @@ int orc_trace(const orc_grid* g, const double* c_mps, double R, double xe, doubl
               double* alpha, int64_t* n_pts, double* out6, int32_t* flags);
 
 /* Link every pair (pairs[2k], pairs[2k+1]) or, with pairs == NULL, all e != r
- * emitter-major. theta_io: NaN = straight-line start, else warm start; on
- * return the linked angle. Outputs may be NULL. */
+ * emitter-major. theta_io: NaN = cold start, else warm start; on return the
+ * linked angle. Cold starts use the straight line to the receiver when
+ * fan_rays == 0, else a fan of fan_rays (>= 2) rays per emitter predicts the
+ * first angle and a bracket. Outputs may be NULL. */
 int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
              double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
-             int32_t max_iter, double* theta_io, double* tof, double* hit_xy,
+             int32_t max_iter, int32_t fan_rays, double* theta_io, double* tof, double* hit_xy,
              int32_t* status, int32_t* iters, int32_t nthreads);
 
 /* Travel time (and hit) of every pair at the given angles, no linking. */

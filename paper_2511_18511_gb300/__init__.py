@@ -106,17 +106,23 @@ class Problem:
                             self.n_pairs, None if self.pairs is None else self.pairs.data_ptr())
 
 
-def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c") -> _L.RtOptions:
+DEFAULT_FAN = 256
+
+
+def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN) -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
-    return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol))
+    return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays), 0)
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
             theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
-            ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None) -> dict:
+            ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
+            fan_rays: int = DEFAULT_FAN) -> dict:
     """Link every pair (shooting method, paper Sec. 3.4) and return the linked
-    angles, travel times (us), interceptions (mm), per-pair status and traces."""
+    angles, travel times (us), interceptions (mm), per-pair status and traces.
+    Cold starts (theta0 None / NaN) use a fan of fan_rays rays per emitter, or
+    the straight line to the receiver with fan_rays = 0."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     n = prob.n_pairs
@@ -131,7 +137,7 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     else:
         out["theta"].copy_(theta0)
     ps = prob.struct(c)
-    o = _opts(ds, tol, max_iter, precision)
+    o = _opts(ds, tol, max_iter, precision, fan_rays)
     _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                     _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
     return out
@@ -205,8 +211,10 @@ class ToF(torch.autograd.Function):
     """T = ToF(c): linked travel times; backward = the adjoint scatter kernel."""
 
     @staticmethod
-    def forward(fctx, c, prob: Problem, ds: float, tol: float, max_iter: int, precision: str, theta0):
-        r = rt_link(prob, ds, tol, max_iter, precision, theta0=theta0, c=c.detach().contiguous())
+    def forward(fctx, c, prob: Problem, ds: float, tol: float, max_iter: int, precision: str, theta0,
+                fan_rays: int = DEFAULT_FAN):
+        r = rt_link(prob, ds, tol, max_iter, precision, theta0=theta0, c=c.detach().contiguous(),
+                    fan_rays=fan_rays)
         fctx.prob, fctx.ds, fctx.precision = prob, ds, precision
         fctx.save_for_backward(c, r["theta"])
         fctx.link = r
@@ -217,10 +225,11 @@ class ToF(torch.autograd.Function):
         c, theta = fctx.saved_tensors
         g = rt_tof_adjoint(fctx.prob, theta, g_tof.contiguous(), fctx.ds, precision=fctx.precision,
                            c=c.detach().contiguous())
-        return g, None, None, None, None, None, None
+        return g, None, None, None, None, None, None, None
 
 
 def tof(c: torch.Tensor, prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30,
-        precision: str = "fp32c", theta0: Optional[torch.Tensor] = None) -> torch.Tensor:
+        precision: str = "fp32c", theta0: Optional[torch.Tensor] = None,
+        fan_rays: int = DEFAULT_FAN) -> torch.Tensor:
     """Differentiable travel times of all pairs of ``prob`` for sound speed c."""
-    return ToF.apply(c, prob, ds, tol, max_iter, precision, theta0)
+    return ToF.apply(c, prob, ds, tol, max_iter, precision, theta0, fan_rays)

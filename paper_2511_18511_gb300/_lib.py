@@ -30,7 +30,7 @@ class RtGrid(C.Structure):
 
 class RtOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("ds_mm", C.c_double),
-                ("tol_mm", C.c_double)]
+                ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("reserved", C.c_int32)]
 
 
 class RtProblem(C.Structure):

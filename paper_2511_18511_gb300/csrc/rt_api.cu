@@ -64,7 +64,7 @@ int prepare(rt_ctx* ctx, const rt_problem* p, const rt_options* o, bool need_lin
     if (rc) return rc;
     rc = set_device(ctx);
     if (rc) return rc;
-    const size_t bytes = rt::node_bytes(o->precision) * (size_t)p->grid.nx * (size_t)p->grid.ny;
+    const size_t bytes = rt::node_bytes(o->precision) * (size_t)(p->grid.nx - 1) * (size_t)(p->grid.ny - 1);
     rc = ensure_field(ctx, bytes, s);
     if (rc) return rc;
     cudaError_t e = rt::launch_pack(p->grid, p->c_mps, ctx->field, ctx->dflag, o->precision, s);
@@ -116,6 +116,8 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     G->Q = (long long)std::floor(R2);
     G->q = R2 - (double)G->Q;
     G->max_steps = (long long)std::ceil(8.0 * R / o->ds_mm);
+    if (G->max_steps > (long long)INT32_MAX - 16) return fail(ctx, RT_EINVAL, "ring too large for the step length");
+    G->max_steps_i = (int)G->max_steps;
     G->tx = p->tx_xy_mm;
     G->n_tx = p->n_tx;
     G->pairs = p->pairs;
@@ -166,6 +168,8 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (ctx->dflag) cudaFree(ctx->dflag);
     if (ctx->queue) cudaFree(ctx->queue);
     if (ctx->scan_tmp) cudaFree(ctx->scan_tmp);
+    if (ctx->fan) cudaFree(ctx->fan);
+    if (ctx->fan_need) cudaFree(ctx->fan_need);
     delete ctx;
 }
 
@@ -187,10 +191,33 @@ int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* 
     rt::Geom G;
     int rc = prepare(ctx, prob, opt, true, s, &G);
     if (rc) return rc;
+    if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536 || opt->reserved != 0)
+        return fail(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]; reserved must be 0");
+    if (opt->fan_rays >= 2) {
+        const size_t fan_bytes = sizeof(double) * (size_t)prob->n_tx * (size_t)opt->fan_rays;
+        const size_t need_bytes = sizeof(int) * (size_t)prob->n_tx;
+        if (ctx->fan_cap < fan_bytes || ctx->need_cap < need_bytes) {
+            if (capturing(s)) return fail(ctx, RT_EINVAL, "fan workspace too small during stream capture");
+            if (ctx->fan_cap < fan_bytes) {
+                if (ctx->fan) cudaFree(ctx->fan);
+                ctx->fan = nullptr;
+                ctx->fan_cap = 0;
+                if (cudaMalloc(&ctx->fan, fan_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "fan workspace");
+                ctx->fan_cap = fan_bytes;
+            }
+            if (ctx->need_cap < need_bytes) {
+                if (ctx->fan_need) cudaFree(ctx->fan_need);
+                ctx->fan_need = nullptr;
+                ctx->need_cap = 0;
+                if (cudaMalloc(&ctx->fan_need, need_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "fan workspace");
+                ctx->need_cap = need_bytes;
+            }
+        }
+    }
     cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
     e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
-                        status, iters, ctx->counters, ctx->queue, s);
+                        status, iters, ctx->counters, ctx->queue, opt->fan_rays, ctx->fan, ctx->fan_need, s);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
 }
 
@@ -215,7 +242,8 @@ int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, c
     rt::Geom G;
     int rc = prepare(ctx, prob, opt, false, s, &G);
     if (rc) return rc;
-    cudaError_t e = rt::launch_adjoint(G, ctx->field, opt->precision, theta, g_tof, tof_ref, prob->c_mps, g_c, s);
+    cudaError_t e =
+        rt::launch_adjoint(G, ctx->field, opt->precision, theta, g_tof, tof_ref, prob->c_mps, g_c, ctx->queue, s);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "adjoint kernel");
 }
 

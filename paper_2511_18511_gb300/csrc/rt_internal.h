@@ -16,6 +16,9 @@ struct rt_ctx {
     unsigned long long* counters = nullptr;   // [8]: per-status counts, [7] RK4 steps
     int* dflag = nullptr;           // [1]: set by the pack kernel when c <= 0 or NaN
     int* queue = nullptr;           // [1]: work-queue head of the persistent linking kernel
+    double* fan = nullptr;          // [n_tx * fan_rays] interception angles of the emitter fans
+    int* fan_need = nullptr;        // [n_tx] emitters with at least one cold-start pair
+    size_t fan_cap = 0, need_cap = 0;
     void* scan_tmp = nullptr;       // prefix-sum workspace (path matrix)
     size_t scan_bytes = 0;
     cudaStream_t last_stream = nullptr;
@@ -33,12 +36,13 @@ cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int*
                         cudaStream_t s);
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
-                        unsigned long long* counters, int* queue, cudaStream_t s);
+                        unsigned long long* counters, int* queue, int fan_rays, double* fan,
+                        int* fan_need, cudaStream_t s);
 cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double* theta, double* tof,
                        double* hit, cudaStream_t s);
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,
                            const double* g_tof, const double* tof_ref, const double* c_mps,
-                           double* g_c, cudaStream_t s);
+                           double* g_c, int* queue, cudaStream_t s);
 cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double* theta,
                         int64_t* row_ptr, int32_t* col, double* val, bool fill, cudaStream_t s);
 cudaError_t launch_scan(int64_t* row_ptr, int n, void* tmp, size_t* tmp_bytes, cudaStream_t s);

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include <cub/device/device_scan.cuh>
+#include <math_constants.h>
 
 #include "rt_internal.h"
 #include "rt_trace.cuh"
@@ -15,44 +16,68 @@ namespace rt {
 constexpr double kPi = 3.141592653589793;
 constexpr int kBlock = 128;
 
-size_t node_bytes(int prec) { return prec == RT_FP64 ? sizeof(D4) : sizeof(float4); }
+static int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
+
+size_t node_bytes(int prec) { return prec == RT_FP64 ? sizeof(CellCoef<double>) : sizeof(CellCoef<float>); }
 
 // ---------------------------------------------------------------- A1: field pack
 
-// Node (i, j): c (mm/us), h*dc/dx and h*dc/dy by central differences inside and
-// one-sided differences at the edges (paper Sec. 3.3.1: gradient from grid
-// values), and s = 1/c.
+// Nodal values at node (i, j): c (mm/us), h*dc/dx and h*dc/dy by central
+// differences inside and one-sided differences at the edges (paper Sec. 3.3.1:
+// the gradient is interpolated from grid values), and s = 1/c.
+__device__ __forceinline__ void node_vals(const double* __restrict__ c_mps, int nx, int ny, int i, int j,
+                                          double v[4]) {
+    const size_t k = (size_t)j * nx + i;
+    const double c = 1e-3 * c_mps[k];
+    const double cxm = 1e-3 * c_mps[i > 0 ? k - 1 : k], cxp = 1e-3 * c_mps[i < nx - 1 ? k + 1 : k];
+    const double cym = 1e-3 * c_mps[j > 0 ? k - nx : k], cyp = 1e-3 * c_mps[j < ny - 1 ? k + nx : k];
+    v[0] = c;
+    v[1] = (i > 0 && i < nx - 1) ? 0.5 * (cxp - cxm) : (cxp - cxm);
+    v[2] = (j > 0 && j < ny - 1) ? 0.5 * (cyp - cym) : (cyp - cym);
+    v[3] = 1.0 / c;
+}
+
+// A1: per-cell bilinear coefficients of the four nodal fields, computed in FP64
+// and stored in the marching precision; flags c <= 0 or NaN.
 template <typename T>
-__global__ void k_pack(const double* __restrict__ c_mps, int nx, int ny, typename NodeT<T>::type* F,
-                       int* bad) {
-    const int n = nx * ny;
+__global__ void k_pack(const double* __restrict__ c_mps, int nx, int ny, CellCoef<T>* F, int* bad) {
+    const int ncx = nx - 1, n = ncx * (ny - 1);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int j = k / nx, i = k - j * nx;
-        const double c = 1e-3 * c_mps[k];
-        if (!(c > 0.0) || !isfinite(c)) atomicOr(bad, 1);
-        const double cxm = 1e-3 * c_mps[i > 0 ? k - 1 : k], cxp = 1e-3 * c_mps[i < nx - 1 ? k + 1 : k];
-        const double cym = 1e-3 * c_mps[j > 0 ? k - nx : k], cyp = 1e-3 * c_mps[j < ny - 1 ? k + nx : k];
-        const double gx = (i > 0 && i < nx - 1) ? 0.5 * (cxp - cxm) : (cxp - cxm);
-        const double gy = (j > 0 && j < ny - 1) ? 0.5 * (cyp - cym) : (cyp - cym);
-        typename NodeT<T>::type v;
-        v.x = (T)c;
-        v.y = (T)gx;
-        v.z = (T)gy;
-        v.w = (T)(1.0 / c);
-        F[k] = v;
+        const int j = k / ncx, i = k - j * ncx;
+        double v00[4], v10[4], v01[4], v11[4];
+        node_vals(c_mps, nx, ny, i, j, v00);
+        node_vals(c_mps, nx, ny, i + 1, j, v10);
+        node_vals(c_mps, nx, ny, i, j + 1, v01);
+        node_vals(c_mps, nx, ny, i + 1, j + 1, v11);
+        const double cs[4] = {v00[0], v10[0], v01[0], v11[0]};
+        for (int q = 0; q < 4; ++q)
+            if (!(cs[q] > 0.0) || !isfinite(cs[q])) atomicOr(bad, 1);
+        typename Vec4T<T>::type f[4];
+        for (int q = 0; q < 4; ++q) {
+            f[q].x = (T)v00[q];
+            f[q].y = (T)(v10[q] - v00[q]);
+            f[q].z = (T)(v01[q] - v00[q]);
+            f[q].w = (T)((v11[q] - v10[q]) - (v01[q] - v00[q]));
+        }
+        CellCoef<T> o;
+        o.c = f[0];
+        o.gx = f[1];
+        o.gy = f[2];
+        o.s = f[3];
+        F[k] = o;
     }
 }
 
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
                         cudaStream_t s) {
-    const int n = g.nx * g.ny;
+    const int n = (g.nx - 1) * (g.ny - 1);
     const int blocks = (n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16;
     cudaError_t e = cudaMemsetAsync(dflag, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (prec == RT_FP64)
-        k_pack<double><<<blocks, 256, 0, s>>>(c_mps, g.nx, g.ny, (D4*)field, dflag);
+        k_pack<double><<<blocks, 256, 0, s>>>(c_mps, g.nx, g.ny, (CellCoef<double>*)field, dflag);
     else
-        k_pack<float><<<blocks, 256, 0, s>>>(c_mps, g.nx, g.ny, (float4*)field, dflag);
+        k_pack<float><<<blocks, 256, 0, s>>>(c_mps, g.nx, g.ny, (CellCoef<float>*)field, dflag);
     return cudaGetLastError();
 }
 
@@ -139,7 +164,7 @@ __device__ bool link_update(const Geom& G, LinkState& L, const TraceOut& o, doub
     double m, dist;
     misfit_of(G, L, o, theta, m, dist);
     ++L.n_eval;
-    if (L.phase == 0 || dist < L.best_dist) {
+    if (dist < L.best_dist) {
         L.best_th = theta; L.best_T = o.T; L.best_hx = o.hx; L.best_hy = o.hy; L.best_dist = dist;
     }
     if (dist <= tol) return true;
@@ -182,6 +207,134 @@ __device__ bool link_update(const Geom& G, LinkState& L, const TraceOut& o, doub
     return false;
 }
 
+// ---------------------------------------------------------------- fan start
+
+// Cold-start prediction from a fan of K rays per emitter at evenly spaced
+// angles over the inward fan (an option; fan_rays = 0 keeps the paper's
+// straight-line start, Sec. 3.4.1). psi = interception angle counter-clockwise
+// from the emitter, NaN when the ray has no interception.
+__device__ __forceinline__ double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
+
+__global__ void k_fan_mark(Geom G, const double* __restrict__ theta, int* need) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.n_pairs) return;
+    int e, r;
+    pair_of(G, k, e, r);
+    if (e >= 0 && e < G.n_tx && isnan(theta[k])) need[e] = 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fan(Geom G, const CellCoef<T>* __restrict__ F, int K,
+                                                const int* __restrict__ need, double* fan,
+                                                unsigned long long* counters) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = id / K, k = id - e * K;
+    long long steps = 0;
+    if (id < G.n_tx * K && need[e] && !*G.bad_field) {
+        const double xe = G.tx[2 * e], ye = G.tx[2 * e + 1];
+        const double phi_e = atan2(ye, xe);
+        const double margin = fmax(G.ds / G.R, 1e-9);
+        const double a_min = phi_e + 0.5 * kPi + margin, a_max = phi_e + 1.5 * kPi - margin;
+        const double step = (a_max - a_min) / (K - 1);
+        Cell<T> C;
+        C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+        NoSink ns;
+        const TraceOut o = trace_ray<T>(C, G, xe, ye, fan_theta(a_min, step, k), xe, ye, ns);
+        fan[id] = (o.flags & 3) ? nan("") : mod_2pi(atan2(o.hy, o.hx) - phi_e);
+        steps = o.steps;
+    }
+    // every thread of the block reaches this point
+    __syncwarp();
+    unsigned long long v = (unsigned long long)steps;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&counters[7], v);
+}
+
+// Fan start of a cold pair (the rule of the CPU reference, written so that the
+// per-ray scan issues no FP64 instruction): the interval of the sequence (fan
+// end, rays 0..K-1, fan end) where psi crosses psi_r whose middle lies closest
+// to the straight-line angle in fan-index units; first angle from the inverse
+// cubic of the four rays around it (when monotone and inside), else linear.
+// psi values are non-negative, so "psi < psi_r" is the signed compare of their
+// IEEE bit patterns; NaN (no interception) has the largest patterns.
+__device__ void fan_start(const Geom& G, LinkState& L, const double* __restrict__ psi, int K) {
+    const bool ccw = isnan(psi[0]) ? true : (psi[0] < kPi);
+    L.psi_at_lo = ccw ? 0.0 : 2.0 * kPi;
+    const double psi_hi_end = 2.0 * kPi - L.psi_at_lo;
+    const double step = (L.a_max - L.a_min) / (K - 1);
+    double th_s = atan2(L.yr - L.ye, L.xr - L.xe);
+    th_s = L.th_lo + mod_2pi(th_s - L.th_lo);
+    const double u_s = (th_s - L.a_min) / step;
+    const long long* pb = reinterpret_cast<const long long*>(psi);
+    const long long b_r = __double_as_longlong(L.psi_r);
+    const long long b_lo = __double_as_longlong(L.psi_at_lo), b_hi = __double_as_longlong(psi_hi_end);
+    const long long b_nan = 0x7ff0000000000000ll;
+    bool neg_prev = b_lo < b_r;
+    int jsel = K + 1;
+    double best_gap = CUDART_INF;
+    for (int j = 1; j <= K + 1; ++j) {
+        long long b;
+        if (j <= K) {
+            const int k = j - 1;
+            b = pb[k];
+            if (b > b_nan) b = (k < K / 2) ? b_lo : b_hi;
+        } else {
+            b = b_hi;
+        }
+        const bool neg = b < b_r;
+        if (neg != neg_prev) {
+            const double gap = fabs((j - 1.5) - u_s);
+            if (gap < best_gap) { best_gap = gap; jsel = j; }
+        }
+        neg_prev = neg;
+    }
+    const double R = G.R;
+    double t0, t1, p0, p1;
+    {
+        const int ja = jsel - 1, jb = jsel;
+        if (ja == 0) { t0 = L.th_lo; p0 = L.psi_at_lo; }
+        else { const int k = ja - 1; t0 = fan_theta(L.a_min, step, k); p0 = psi[k]; if (isnan(p0)) p0 = (k < K / 2) ? L.psi_at_lo : psi_hi_end; }
+        if (jb == K + 1) { t1 = L.th_hi; p1 = psi_hi_end; }
+        else { const int k = jb - 1; t1 = fan_theta(L.a_min, step, k); p1 = psi[k]; if (isnan(p1)) p1 = (k < K / 2) ? L.psi_at_lo : psi_hi_end; }
+    }
+    const double m0 = R * (p0 - L.psi_r), m1 = R * (p1 - L.psi_r);
+    if (m0 < 0) { L.ta = t0; L.fa = m0; L.tb = t1; L.fb = m1; }
+    else { L.ta = t1; L.fa = m1; L.tb = t0; L.fb = m0; }
+    L.last = 0;
+    double th0 = t0 - m0 * (t1 - t0) / (m1 - m0);
+    const int k0 = jsel - 2;
+    if (k0 >= 1 && k0 + 2 <= K - 1) {
+        double tt[4], mm[4];
+        bool ok = true;
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 - 1 + q;
+            const double pk = psi[k];
+            if (isnan(pk)) ok = false;
+            tt[q] = fan_theta(L.a_min, step, k);
+            mm[q] = R * (pk - L.psi_r);
+        }
+        for (int q = 0; q < 3 && ok; ++q)
+            if (!((mm[q + 1] - mm[q]) * (mm[2] - mm[1]) > 0)) ok = false;
+        if (ok) {
+            double v = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                double l = 1.0;
+                for (int b = 0; b < 4; ++b)
+                    if (b != a) l *= (0.0 - mm[b]) / (mm[a] - mm[b]);
+                v += l * tt[a];
+            }
+            if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
+        }
+    }
+    if (!(th0 > fmin(L.ta, L.tb) && th0 < fmax(L.ta, L.tb))) th0 = 0.5 * (L.ta + L.tb);
+    const bool first = fabs(m0) <= fabs(m1);
+    L.cur_th = L.prev_th = first ? t0 : t1;
+    L.cur_m = L.prev_m = first ? m0 : m1;
+    L.th0 = th0;
+    L.next = th0;
+    L.phase = 2;
+}
+
 // Work order of the persistent kernel. For the all-pairs list, queue slot q
 // serves ring offsets o = r - e (mod N) from the longest chord (o = N/2) down to
 // the shortest (o = 1, N-1), N emitters per offset, so the launch's tail is
@@ -209,15 +362,20 @@ __device__ __forceinline__ int fetch_pair(int* queue) {
 }
 
 constexpr int kLinkBlock = 128;
+// Resident blocks per SM asked of the compiler: FP32 at <= 85 registers
+// (6 blocks, 24 warps), FP64 unconstrained.
+template <typename T> struct LinkOcc { static constexpr int blocks = 1; };
+template <> struct LinkOcc<float> { static constexpr int blocks = 6; };
 
 // Persistent linking kernel: each lane takes pairs from the queue, advances
 // its own trace one RK4 step per loop iteration, and updates the linking
 // state when a trace ends, so lanes never wait for other lanes' pairs.
 template <typename T>
-__global__ void __launch_bounds__(kLinkBlock) k_link(Geom G, const typename NodeT<T>::type* __restrict__ F,
+__global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks) k_link(Geom G, const typename NodeT<T>::type* __restrict__ F,
                                                      double tol, int max_iter, double* theta, double* tof,
                                                      double* hit, int32_t* status, int32_t* iters,
-                                                     unsigned long long* counters, int* queue) {
+                                                     unsigned long long* counters, int* queue, int fan_rays,
+                                                     const double* __restrict__ fan) {
     __shared__ LinkState sh[kLinkBlock];
     LinkState& L = sh[threadIdx.x];
     Cell<T> C;
@@ -257,7 +415,12 @@ __global__ void __launch_bounds__(kLinkBlock) k_link(Geom G, const typename Node
             L.n_eval = 0;
             L.phase = 0;
             L.psi_at_lo = 0.0;
-            L.best_dist = DBL_MAX;
+            L.best_dist = CUDART_INF;
+            if (fan_rays >= 2 && isnan(tin)) {
+                int e, r;
+                pair_of(G, k, e, r);
+                fan_start(G, L, fan + (size_t)e * fan_rays, fan_rays);
+            }
             trace_begin(ts, G, L.xe, L.ye, L.next);
             active = true;
         }
@@ -298,38 +461,52 @@ __global__ void __launch_bounds__(kLinkBlock) k_link(Geom G, const typename Node
     }
 }
 
-template <typename T>
-static int persistent_blocks() {
-    static int blocks = 0;
-    if (!blocks) {
+// Blocks of a persistent launch: resident blocks per SM x SMs (cached per slot).
+template <typename K>
+static int persistent_blocks(K kernel, int slot) {
+    static int cache[8] = {0};
+    if (!cache[slot]) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_link<T>, kLinkBlock, 0);
-        blocks = sms * (per_sm > 0 ? per_sm : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLinkBlock, 0);
+        cache[slot] = sms * (per_sm > 0 ? per_sm : 1);
     }
-    return blocks;
+    return cache[slot];
 }
 
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
-                        unsigned long long* counters, int* queue, cudaStream_t s) {
+                        unsigned long long* counters, int* queue, int fan_rays, double* fan,
+                        int* fan_need, cudaStream_t s) {
     if (G.n_pairs == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    if (fan_rays >= 2) {
+        e = cudaMemsetAsync(fan_need, 0, sizeof(int) * (size_t)G.n_tx, s);
+        if (e != cudaSuccess) return e;
+        k_fan_mark<<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, theta, fan_need);
+        const int nf = G.n_tx * fan_rays;
+        if (prec == RT_FP64)
+            k_fan<double><<<grid_for(nf), kBlock, 0, s>>>(G, (const CellCoef<double>*)field, fan_rays, fan_need, fan,
+                                                          counters);
+        else
+            k_fan<float><<<grid_for(nf), kBlock, 0, s>>>(G, (const CellCoef<float>*)field, fan_rays, fan_need, fan,
+                                                         counters);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (prec == RT_FP64) {
-        const int nb = min(persistent_blocks<double>(), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-        k_link<double><<<nb, kLinkBlock, 0, s>>>(G, (const D4*)field, tol, max_iter, theta, tof, hit, status,
-                                                 iters, counters, queue);
+        const int nb = min(persistent_blocks(k_link<double>, 3), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+        k_link<double><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<double>*)field, tol, max_iter, theta, tof, hit,
+                                                 status, iters, counters, queue, fan_rays, fan);
     } else {
-        const int nb = min(persistent_blocks<float>(), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-        k_link<float><<<nb, kLinkBlock, 0, s>>>(G, (const float4*)field, tol, max_iter, theta, tof, hit, status,
-                                                iters, counters, queue);
+        const int nb = min(persistent_blocks(k_link<float>, 4), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+        k_link<float><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<float>*)field, tol, max_iter, theta, tof, hit,
+                                                status, iters, counters, queue, fan_rays, fan);
     }
     return cudaGetLastError();
 }
-
-static int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
 
 // ---------------------------------------------------------------- A5: ToF at fixed angles
 
@@ -356,32 +533,33 @@ cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double*
                        double* hit, cudaStream_t s) {
     if (G.n_pairs == 0) return cudaSuccess;
     if (prec == RT_FP64)
-        k_tof<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const D4*)field, theta, tof, hit);
+        k_tof<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, tof, hit);
     else
-        k_tof<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const float4*)field, theta, tof, hit);
+        k_tof<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, tof, hit);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- A6: adjoint scatter
 
 // Scatters w * alpha_m * phi_j(x_m) into g (FP64 atomics), one flush of the
-// four nodes per run of consecutive points in one cell.
+// four nodes per run of consecutive points in one cell. The node weights are
+// formed in the marching precision and widened exactly to FP64 for the atomic.
 template <typename T>
 struct AdjSink {
     double* g;
-    double w;
+    T w;
     int nx, ny;
     CellAcc<T> acc;
     __device__ __forceinline__ void flush() {
         if (acc.ai == INT_MIN) return;
-        double w00, w10, w01, w11;
-        acc.node_weights(w00, w10, w01, w11);
+        const T w11 = acc.Wxy, w10 = acc.Wx - acc.Wxy, w01 = acc.Wy - acc.Wxy;
+        const T w00 = (acc.W - acc.Wx) - w01;
         const int i = min(max(acc.ai, 0), nx - 2), j = min(max(acc.aj, 0), ny - 2);
         double* p = g + (size_t)j * nx + i;
-        atomicAdd(p, w * w00);
-        atomicAdd(p + 1, w * w10);
-        atomicAdd(p + nx, w * w01);
-        atomicAdd(p + nx + 1, w * w11);
+        atomicAdd(p, to_double(w * w00));
+        atomicAdd(p + 1, to_double(w * w10));
+        atomicAdd(p + nx, to_double(w * w01));
+        atomicAdd(p + nx + 1, to_double(w * w11));
     }
     __device__ __forceinline__ void add(int ci, int cj, T tx, T ty, T a) {
         if (ci != acc.ai || cj != acc.aj) {
@@ -395,25 +573,50 @@ struct AdjSink {
         acc.Wy += a * ty;
         acc.Wxy += a * tx * ty;
     }
-    __device__ __forceinline__ void finish() { flush(); }
+    __device__ __forceinline__ void finish() {
+        flush();
+        acc.reset();
+    }
 };
 
+struct PairEnds {
+    double xe, ye, xr, yr;
+};
+
+// Persistent adjoint: each lane takes pairs from the queue (longest chords
+// first), retraces the ray at its angle and scatters its weights.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_adjoint(Geom G, const typename NodeT<T>::type* __restrict__ F,
-                                                    const double* theta, const double* g_tof,
-                                                    const double* tof_ref, double* g) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= G.n_pairs) return;
-    const double w = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
-    if (w == 0.0 || !isfinite(w)) return;
-    LinkCtx L;
-    if (!setup_pair(G, k, L)) return;
+__global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks)
+    k_adjoint(Geom G, const CellCoef<T>* __restrict__ F, const double* theta, const double* g_tof,
+              const double* tof_ref, double* g, int* queue) {
+    __shared__ PairEnds sh[kLinkBlock];
+    PairEnds& E = sh[threadIdx.x];
     Cell<T> C;
     C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+    TraceState<T> ts;
     AdjSink<T> sink;
-    sink.g = g; sink.w = w; sink.nx = G.nx; sink.ny = G.ny;
+    sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
     sink.acc.reset();
-    trace_ray<T>(C, G, L.xe, L.ye, theta[k], L.xr, L.yr, sink);
+    bool active = false;
+    for (;;) {
+        if (!active) {
+            const int qslot = fetch_pair(queue);
+            if (qslot >= G.n_pairs) break;
+            const int k = queue_pair(G, qslot);
+            const double w = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
+            if (w == 0.0 || !isfinite(w)) continue;
+            LinkCtx X;
+            if (!setup_pair(G, k, X)) continue;
+            E.xe = X.xe; E.ye = X.ye; E.xr = X.xr; E.yr = X.yr;
+            sink.w = (T)w;
+            trace_begin(ts, G, X.xe, X.ye, theta[k]);
+            active = true;
+        }
+        if (trace_step(C, G, ts, sink)) {
+            trace_end(C, G, ts, E.xe, E.ye, E.xr, E.yr, sink);
+            active = false;
+        }
+    }
 }
 
 // g_c = -1000 * (L^T w) / c_mps^2 : s = 1000/c_mps (us/mm)
@@ -426,17 +629,22 @@ __global__ void k_adjoint_finish(double* g, const double* __restrict__ c_mps, in
 
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,
                            const double* g_tof, const double* tof_ref, const double* c_mps,
-                           double* g_c, cudaStream_t s) {
+                           double* g_c, int* queue, cudaStream_t s) {
     const int n = G.nx * G.ny;
     cudaError_t e = cudaMemsetAsync(g_c, 0, sizeof(double) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     if (G.n_pairs > 0) {
-        if (prec == RT_FP64)
-            k_adjoint<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const D4*)field, theta, g_tof,
-                                                                     tof_ref, g_c);
-        else
-            k_adjoint<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const float4*)field, theta, g_tof,
-                                                                    tof_ref, g_c);
+        e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        if (prec == RT_FP64) {
+            const int nb = min(persistent_blocks(k_adjoint<double>, 1), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+            k_adjoint<double><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, g_tof, tof_ref,
+                                                        g_c, queue);
+        } else {
+            const int nb = min(persistent_blocks(k_adjoint<float>, 2), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+            k_adjoint<float><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, g_tof, tof_ref,
+                                                       g_c, queue);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -510,10 +718,10 @@ cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double
                         int32_t* col, double* val, bool fill, cudaStream_t s) {
     if (G.n_pairs == 0) return cudaSuccess;
     if (prec == RT_FP64)
-        k_rows<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const D4*)field, theta, row_ptr, col, val,
+        k_rows<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, row_ptr, col, val,
                                                               fill);
     else
-        k_rows<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const float4*)field, theta, row_ptr, col,
+        k_rows<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, row_ptr, col,
                                                              val, fill);
     return cudaGetLastError();
 }

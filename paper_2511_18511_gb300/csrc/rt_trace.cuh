@@ -32,9 +32,20 @@ struct __align__(32) D4 {
     double x, y, z, w;
 };
 
-template <typename T> struct NodeT;
-template <> struct NodeT<float> { using type = float4; };
-template <> struct NodeT<double> { using type = D4; };
+template <typename T> struct Vec4T;
+template <> struct Vec4T<float> { using type = float4; };
+template <> struct Vec4T<double> { using type = D4; };
+
+// Bilinear coefficients of one grid cell for the four sampled fields
+// (c, h dc/dx, h dc/dy, s): f(tx, ty) = a + tx bx + ty (by + tx bxy), each field
+// one vector (a, bx, by, bxy). Cell (i, j) spans nodes i..i+1, j..j+1 and is
+// stored at j*(nx-1) + i. A cell reload is four contiguous vector loads.
+template <typename T>
+struct CellCoef {
+    typename Vec4T<T>::type c, gx, gy, s;
+};
+
+template <typename T> struct NodeT { using type = CellCoef<T>; };
 
 // Per-launch geometry (kernel parameter).
 struct Geom {
@@ -46,6 +57,7 @@ struct Geom {
     long long Q;            // floor((R/h)^2)
     double q;               // (R/h)^2 - Q
     long long max_steps;    // ceil(8 R / ds)
+    int max_steps_i;
     const double* tx;       // [2 n_tx]
     int n_tx;
     const int* pairs;       // [2 n_pairs] or null
@@ -99,7 +111,7 @@ __device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
 
 template <typename T>
 struct Cell {
-    using V = typename NodeT<T>::type;
+    using V = CellCoef<T>;
     const V* __restrict__ F;
     int nx, ny;
     int pi, pj;                       // cached cell
@@ -114,21 +126,39 @@ struct Cell {
         // clamp for memory safety; rays stay inside by the ring/grid check
         i = min(max(i, 0), nx - 2);
         j = min(max(j, 0), ny - 2);
-        const V* p = F + (size_t)j * nx + i;
-        V n00 = p[0], n10 = p[1], n01 = p[nx], n11 = p[nx + 1];
-        ca = n00.x; cbx = n10.x - n00.x; cby = n01.x - n00.x; cbxy = (n11.x - n10.x) - (n01.x - n00.x);
-        xa = n00.y; xbx = n10.y - n00.y; xby = n01.y - n00.y; xbxy = (n11.y - n10.y) - (n01.y - n00.y);
-        ya = n00.z; ybx = n10.z - n00.z; yby = n01.z - n00.z; ybxy = (n11.z - n10.z) - (n01.z - n00.z);
-        sa = n00.w; sbx = n10.w - n00.w; sby = n01.w - n00.w; sbxy = (n11.w - n10.w) - (n01.w - n00.w);
+        const V* p = F + (size_t)j * (nx - 1) + i;
+        const auto c = p->c, x = p->gx, y = p->gy, w = p->s;
+        ca = c.x; cbx = c.y; cby = c.z; cbxy = c.w;
+        xa = x.x; xbx = x.y; xby = x.z; xbxy = x.w;
+        ya = y.x; ybx = y.y; yby = y.z; ybxy = y.w;
+        sa = w.x; sbx = w.y; sby = w.z; sbxy = w.w;
     }
 
     // (u, v): fractions relative to cell (ci, cj), possibly outside [0, 1)
     __device__ __forceinline__ void at(int ci, int cj, T u, T v, T& c, T& gx, T& gy, T& tx, T& ty) {
-        T fu = floor(u), fv = floor(v);
-        int i = ci + (int)fu, j = cj + (int)fv;
-        tx = u - fu;
-        ty = v - fv;
-        if (i != pi || j != pj) load(i, j);
+        if (ci == pi && cj == pj && u >= (T)0 && u < (T)1 && v >= (T)0 && v < (T)1) {
+            tx = u;
+            ty = v;
+        } else {
+            // neighbour cell: offsets from comparisons (no conversion instructions,
+            // which are slow on this part); stage points lie within one cell of the
+            // current one when ds <= h, larger offsets take the floor path
+            int i, j;
+            if (u >= (T)-1 && u < (T)2 && v >= (T)-1 && v < (T)2) {
+                const bool ul = u < (T)0, uh = u >= (T)1, vl = v < (T)0, vh = v >= (T)1;
+                tx = ul ? u + (T)1 : (uh ? u - (T)1 : u);
+                ty = vl ? v + (T)1 : (vh ? v - (T)1 : v);
+                i = ci + (ul ? -1 : (uh ? 1 : 0));
+                j = cj + (vl ? -1 : (vh ? 1 : 0));
+            } else {
+                const T fu = floor(u), fv = floor(v);
+                i = ci + (int)fu;
+                j = cj + (int)fv;
+                tx = u - fu;
+                ty = v - fv;
+            }
+            if (i != pi || j != pj) load(i, j);
+        }
         c = ca + tx * cbx + ty * (cby + tx * cbxy);
         gx = xa + tx * xbx + ty * (xby + tx * xbxy);
         gy = ya + tx * ybx + ty * (yby + tx * ybxy);
@@ -267,6 +297,23 @@ __device__ __forceinline__ void abs_pos(const Geom& G, const RayState<T>& S, dou
 
 // ---------------------------------------------------------------- scatter (adjoint / matrix rows)
 
+// Exact float -> double by integer bit operations (normal numbers; zeros and
+// subnormals give +-0), avoiding a conversion instruction.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (ex == 0) return __longlong_as_double((long long)sign);
+    if (ex == 0xffu)   // inf / NaN keep their class
+        return __longlong_as_double((long long)(sign | (0x7ffull << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+    const unsigned long long bits = sign | ((unsigned long long)(ex + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double to_double(float f) { return f2d_bits(f); }
+__device__ __forceinline__ double to_double(double d) { return d; }
+
 // Accumulates the trapezoid-weighted bilinear weights of consecutive points
 // that fall in one cell, as (sum w, sum w tx, sum w ty, sum w tx ty).
 template <typename T>
@@ -309,7 +356,7 @@ struct TraceState {
     int flags;                // bit0 step cap, bit1 left outward at once
     int iL, jL;               // cell and fractions of the last full-step point
     T txL, tyL;
-    long long steps;
+    int steps;                // RK4 steps of this trace (incl. landing)
 };
 
 template <typename T>
@@ -336,7 +383,7 @@ __device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, do
 // cap was reached (flags bit0). On exit ts.S is still the last inside point.
 template <typename T, typename Sink>
 __device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState<T>& ts, Sink& sink) {
-    if (ts.m >= G.max_steps) {
+    if (ts.m >= G.max_steps_i) {
         ts.flags |= 1;
         return true;
     }

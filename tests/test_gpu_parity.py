@@ -44,19 +44,32 @@ def _rel_l2(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+FAN = 256   # the library's default cold start; fan 0 = the paper's straight-line start
+
+
 @pytest.fixture(scope="module")
 def small(orc, P, rt):
     w = P.cfg_small()
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
-    ref = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol)
+    ref = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, fan_rays=FAN)
     return w, prob, ref
 
 
+@pytest.fixture(scope="module")
+def small_straight(orc, small):
+    w, prob, _ = small
+    return orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, fan_rays=0)
+
+
+@pytest.mark.parametrize("fan", [FAN, 0])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-def test_link_matches_oracle_small(small, rt, P, prec):
-    """128^2 grid, 64-ring (4032 pairs, 32 blocks of 128 with a ragged tail)."""
+def test_link_matches_oracle_small(small, small_straight, rt, P, prec, fan):
+    """128^2 grid, 64-ring (4032 pairs, 32 blocks of 128 with a ragged tail),
+    fan-predicted and straight-line cold starts."""
     w, prob, ref = small
-    r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec)
+    if fan == 0:
+        ref = small_straight
+    r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, fan_rays=fan)
     ok, counts = rt.rt_status_counts()
     assert ok and counts[0] == prob.n_pairs
     st = _np(r["status"])
@@ -76,8 +89,11 @@ def test_link_matches_oracle_small(small, rt, P, prec):
     # angles are held to END_TOL in test_tof_at_oracle_angles
     d_or = np.linalg.norm(hit - ref["hit"], axis=1)
     assert d_or.max() <= 2 * w.tol
-    print(f"[{prec}] linked: max ToF rel err {rel.max():.3e}, max |hit - x_r| {d_rx:.3e} mm, "
-          f"max |hit - hit_oracle| {d_or.max():.3e} mm (median {np.median(d_or):.3e})")
+    print(f"[{prec} fan={fan}] linked: max ToF rel err {rel.max():.3e}, max |hit - x_r| {d_rx:.3e} mm, "
+          f"max |hit - hit_oracle| {d_or.max():.3e} mm (median {np.median(d_or):.3e}), "
+          f"traces/pair {_np(r['iters']).mean():.2f} (oracle {ref['iters'].mean():.2f})")
+    if prec == "fp64":
+        np.testing.assert_array_equal(_np(r["iters"]), ref["iters"])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
@@ -186,7 +202,7 @@ def test_closed_forms_on_gpu(rt, P):
 def test_fisheye_against_oracle_and_closed_form(orc, rt, P, prec):
     """Strong refraction (fish-eye lens, 256^2 at 0.4 mm, 32-ring at 45 mm)."""
     w = P.cfg_fisheye(n=256, n_tx=32, h=0.4, ds=0.04)
-    ref = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol)
+    ref = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, fan_rays=FAN)
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
     r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec)
     assert (_np(r["status"]) == 0).all()
@@ -231,7 +247,7 @@ def test_edge_cases(rt, P):
     # max_iter = 2 in a refracting medium leaves unconverged pairs, reported
     w = P.cfg_fisheye(n=256, n_tx=16, h=0.4, ds=0.04)
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
-    r = rt.rt_link(prob, w.ds, tol=1e-6, max_iter=2)
+    r = rt.rt_link(prob, w.ds, tol=1e-6, max_iter=2, fan_rays=0)
     ok, counts = rt.rt_status_counts()
     assert not ok and counts[1] > 0 and (_np(r["iters"]) <= 2).all()
     # warm start from linked angles: one trace per pair

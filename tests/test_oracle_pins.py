@@ -389,3 +389,36 @@ def test_invalid_inputs_rejected(orc):
         orc.link(g, c, tx, 40.0, 0.05)          # ring outside the grid
     with pytest.raises(ValueError):
         orc.link(g, c, tx * 0.9, R, 0.05)       # transducers off the ring
+
+
+# ---------------------------------------------------------------- fan start
+
+def test_fan_start_reaches_the_same_rays(orc):
+    """The fan-predicted cold start (an option) links the same rays as the
+    straight-line start where the root is unique (weak inclusions), with fewer
+    traces; the homogeneous medium links in one trace from the fan."""
+    w = P.cfg_small(n_tx=32)
+    a = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-9, fan_rays=0)
+    b = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-9, fan_rays=64)
+    assert (a["status"] == 0).all() and (b["status"] == 0).all()
+    np.testing.assert_allclose(b["tof"], a["tof"], rtol=1e-11)
+    assert np.abs(np.angle(np.exp(1j * (b["theta"] - a["theta"])))).max() < 1e-9
+    assert b["iters"].mean() < a["iters"].mean()
+    g, tx, R = _small_ring(32)
+    h = orc.link(g, P.homogeneous(g), tx, R, 0.05, fan_rays=64)
+    assert (h["iters"] == 1).all()
+
+
+def test_fan_start_brute_force_bracket(orc):
+    """With the fan start the linked angle still lies in the brute-force bracket."""
+    g = P.Grid(32, 32, 0.5)
+    R = 6.0
+    tx = P.ring(8, R)
+    c = P.gaussian_inclusions(g, seed=21, n_incl=2, amp=0.05, sigma_lo=1.0, sigma_hi=2.0, centre_radius=3.0)
+    pairs = P.all_pairs(8)
+    ds = 0.1
+    r = orc.link(g, c, tx, R, ds, tol=1e-7, fan_rays=16)
+    r0 = orc.link(g, c, tx, R, ds, tol=1e-7, fan_rays=0)
+    assert (r["status"] == 0).all()
+    d = np.angle(np.exp(1j * (r["theta"] - r0["theta"])))
+    assert np.abs(d).max() < 1e-6
