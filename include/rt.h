@@ -184,6 +184,30 @@ int rt_path_matrix(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
  */
 int rt_status_counts(rt_ctx* ctx, int64_t counts[8], void* stream);
 
+/*
+ * rt_tof_forward_noalloc — the same travel times and interceptions as
+ * rt_tof_forward, for callers that cannot allocate device memory when they
+ * need them: a host that routes all device memory through its own pool, a
+ * loop that must not allocate once it runs, or a plugin that only receives
+ * input and output buffers. The paper has no counterpart; this is a service
+ * of the library.
+ * It takes no rt_ctx and calls no allocator (cudaMalloc, cudaFree or any
+ * allocating library routine). The packed field lives in a fixed device array
+ * of 16 MiB inside the library, which every GPU that loads the library keeps
+ * until the process exits: grids of up to 16 MiB / 64 B = 262,144 cells
+ * (e.g. 513 x 513 nodes) in RT_FP32_COMP and 131,072 cells in RT_FP64;
+ * larger grids return RT_ENOMEM without enqueueing anything.
+ * The first call on a device looks up that array's device address with the
+ * device current (make that first call before any stream capture). All calls
+ * share the one array, which keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. Arguments and outputs are as for rt_tof_forward;
+ * opt->fan_rays is ignored. Returns RT_OK, RT_EINVAL (bad argument),
+ * RT_ENOMEM (grid too large) or RT_ECUDA; there is no error message.
+ */
+int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* opt, const double* theta,
+                           double* tof_us, double* hit_xy_mm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

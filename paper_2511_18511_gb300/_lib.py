@@ -20,6 +20,7 @@ RAY_OK, RAY_MAXITER, RAY_STEPCAP, RAY_BADINPUT = 0, 1, 2, 4
 EXPORTED = [
     "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_ctx_reserve",
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
+    "rt_tof_forward_noalloc",
 ]
 
 
@@ -76,6 +77,7 @@ def load():
         L.rt_path_matrix.argtypes = [vp, P(RtProblem), P(RtOptions), vp, vp, vp, vp, C.c_int64,
                                      P(C.c_int64), vp]
         L.rt_status_counts.argtypes = [vp, P(C.c_int64), vp]
+        L.rt_tof_forward_noalloc.argtypes = [P(RtProblem), P(RtOptions), vp, vp, vp, vp]
         _lib = L
         return L
 
