@@ -231,9 +231,20 @@ template <> struct Dir<float> {
 template <typename T>
 struct RayState {
     int ci, cj;
-    T fx, fy;
+    T fx, fy;      // fraction of the cell
+    T lx, ly;      // FP32: rounding residual of the fraction (two-sum), FP64: 0
     Dir<T> d;
 };
+
+// fraction += inc, keeping the rounding error in the residual (FP32 only)
+__device__ __forceinline__ void add_frac(float& f, float& lo, float inc) {
+    const float s = f + inc, bb = s - f;
+    lo += (f - (s - bb)) + (inc - bb);
+    const float s2 = s + lo;
+    lo -= s2 - s;
+    f = s2;
+}
+__device__ __forceinline__ void add_frac(double& f, double&, double inc) { f += inc; }
 
 // (g.e) e - g over c for stage direction e
 template <typename T>
@@ -266,14 +277,22 @@ __device__ __forceinline__ void rk4_step(Cell<T>& C, const RayState<T>& S, T H, 
     T e4x = dx + H * k3x, e4y = dy + H * k3y;
     C.at(S.ci, S.cj, S.fx + H * e3x, S.fy + H * e3y, c, gx, gy, tx, ty);
     ray_rhs(c, gx, gy, e4x, e4y, k4x, k4y);
-    T nfx = S.fx + H6 * ((dx + S.d.lx()) + (T)2 * (e2x + e3x) + e4x);
-    T nfy = S.fy + H6 * ((dy + S.d.ly()) + (T)2 * (e2y + e3y) + e4y);
+    // every stage direction carries the low part of d, so the position
+    // increment gets it in full: H d_lo (zero in FP64); the fraction is
+    // accumulated with its rounding residual in FP32
+    T nfx = S.fx, nfy = S.fy;
+    N.lx = S.lx;
+    N.ly = S.ly;
+    add_frac(nfx, N.lx, H6 * (dx + (T)2 * (e2x + e3x) + e4x) + H * S.d.lx());
+    add_frac(nfy, N.ly, H6 * (dy + (T)2 * (e2y + e3y) + e4y) + H * S.d.ly());
     N.d = S.d;
     N.d.add_normalize(H6 * (k1x + (T)2 * (k2x + k3x) + k4x), H6 * (k1y + (T)2 * (k2y + k3y) + k4y));
     N.ci = S.ci;
     N.cj = S.cj;
-    if (nfx >= (T)1) { N.ci += 1; nfx -= (T)1; } else if (nfx < (T)0) { N.ci -= 1; nfx += (T)1; }
-    if (nfy >= (T)1) { N.cj += 1; nfy -= (T)1; } else if (nfy < (T)0) { N.cj -= 1; nfy += (T)1; }
+    // f - 1 is exact for f in [1, 2); f + 1 for f in [-1, 0) rounds, so it goes
+    // through the residual too
+    if (nfx >= (T)1) { N.ci += 1; nfx -= (T)1; } else if (nfx < (T)0) { N.ci -= 1; add_frac(nfx, N.lx, (T)1); }
+    if (nfy >= (T)1) { N.cj += 1; nfy -= (T)1; } else if (nfy < (T)0) { N.cj -= 1; add_frac(nfy, N.ly, (T)1); }
     N.fx = nfx;
     N.fy = nfy;
 }
@@ -291,8 +310,8 @@ __device__ __forceinline__ T ring_excess(const Geom& G, const RayState<T>& S) {
 
 template <typename T>
 __device__ __forceinline__ void abs_pos(const Geom& G, const RayState<T>& S, double& X, double& Y) {
-    X = G.x0 + G.h * ((double)S.ci + (double)S.fx);
-    Y = G.y0 + G.h * ((double)S.cj + (double)S.fy);
+    X = G.x0 + G.h * ((double)S.ci + ((double)S.fx + (double)S.lx));
+    Y = G.y0 + G.h * ((double)S.cj + ((double)S.fy + (double)S.ly));
 }
 
 // ---------------------------------------------------------------- scatter (adjoint / matrix rows)
@@ -367,6 +386,8 @@ __device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, do
     ts.S.cj = (int)fv;
     ts.S.fx = (T)(u - fu);
     ts.S.fy = (T)(v - fv);
+    ts.S.lx = (T)((u - fu) - (double)ts.S.fx);
+    ts.S.ly = (T)((v - fv) - (double)ts.S.fy);
     ts.S.d.set(theta);
     ts.s_first = ts.s_cur = (T)0;
     ts.Ssum = ts.Scomp = (T)0;

@@ -1,12 +1,12 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances of the ray path: travel time 2e-6 relative per pair, endpoints
-1e-4 mm, adjoint 1e-5 relative (L2 and max-abs over the grid). The FP64 form
-meets them everywhere (measured ~1e-14). The FP32-compensated form meets them
-whenever both sides trace the same rays (same launch angles). End to end, each
-side links to its own iterate within tol of the receiver, so linked rays can
-differ by up to 2 tol at the receiver; there the FP32 form's measured error is
-asserted with a stated margin instead (see each test).
+1e-4 mm, adjoint 1e-5 relative (L2 and max-abs over the grid). Both the FP64
+form (measured ~1e-14) and the FP32-compensated form (~1e-7 travel time,
+~1e-6 adjoint) meet them. Linked endpoints are compared with the receiver
+(tol) and with the oracle's linked endpoint within 2 tol, since each side stops
+at its own iterate within tol of the receiver; rays traced from the same
+angles are compared within 1e-4 mm.
 """
 import numpy as np
 import pytest
@@ -129,10 +129,8 @@ def test_adjoint_at_oracle_angles(small, orc, rt, P, prec):
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_full_pipeline_adjoint(small, orc, rt, P, prec):
     """Link + adjoint end to end (each side with its own linked rays). FP64
-    reaches the same iterates as the oracle (1e-5 bar, measured ~1e-13). FP32:
-    measured 1.07e-5 L2 / 2.5e-5 max on this workload, from rays that stopped at
-    different iterates within tol (at the same angles the FP32 adjoint is
-    2.3e-6, see test_adjoint_at_oracle_angles); bound 3e-5 L2 / 1e-4 max."""
+    reaches the same iterates as the oracle (measured ~1e-13); the FP32 form
+    with compensated position and direction measured 8.5e-7 L2 / 1.2e-6 max."""
     w, prob, ref = small
     g = P.SplitMix64(6).normal(prob.n_pairs)
     want = orc.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, ref["theta"], g)
@@ -141,8 +139,7 @@ def test_full_pipeline_adjoint(small, orc, rt, P, prec):
     e_l2 = _rel_l2(got, want)
     e_max = np.abs(got - want).max() / np.abs(want).max()
     print(f"[{prec}] adjoint end to end: rel L2 {e_l2:.3e}, rel max {e_max:.3e}")
-    b2, bm = (ADJ_RTOL, ADJ_RTOL) if prec == "fp64" else (3e-5, 1e-4)
-    assert e_l2 <= b2 and e_max <= bm, (e_l2, e_max)
+    assert e_l2 <= ADJ_RTOL and e_max <= ADJ_RTOL, (e_l2, e_max)
 
 
 def test_residual_weights_and_autograd(small, orc, rt, P):
@@ -175,8 +172,8 @@ def test_path_matrix_matches_oracle(small, orc, rt, prec):
     B = sp.csr_matrix((oval, ocol, orp), shape=(len(th), n)).toarray()
     err = np.abs(A - B).max() / np.abs(B).max()
     print(f"[{prec}] path matrix at oracle angles: max entry error / max entry {err:.3e}")
-    # FP32: entries move with the trajectory (1e-5 mm at grazing landings ~ 2e-5 of h)
-    assert err <= (1e-11 if prec == "fp64" else 5e-5), err
+    # FP32: entries move with the trajectory (measured 4.9e-6 of the largest entry)
+    assert err <= (1e-11 if prec == "fp64" else 1e-5), err
 
 
 def test_closed_forms_on_gpu(rt, P):
