@@ -81,7 +81,11 @@ typedef struct {
                             a fan of K rays per emitter predicts the first angle
                             and a bracket (256 is the usual); ignored by the calls
                             that take fixed angles */
-    int32_t reserved;    /* must be 0 */
+    int32_t block_threads; /* rt_batch_run only: threads per block of the persistent
+                            kernel, 0 (= 128), 64, 128 or 256 (FP64: 0 or 128) */
+    int32_t step_unroll;   /* rt_batch_run only: RK4 steps per work-queue check,
+                            0 (= 1), 1 or 2 (FP64: 0 or 1) */
+    int32_t reserved;      /* must be 0 */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
@@ -183,6 +187,36 @@ int rt_path_matrix(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
  * when every pair linked, RT_ENOCONV otherwise.
  */
 int rt_status_counts(rt_ctx* ctx, int64_t counts[8], void* stream);
+
+/* One problem of a batch: geometry plus its own outputs (device memory). */
+typedef struct {
+    rt_problem prob;
+    double* theta_io;       /* [n_pairs] in/out, as for rt_link (NaN = cold start) */
+    double* tof_us;         /* [n_pairs] out */
+    double* hit_xy_mm;      /* [2*n_pairs] out or NULL */
+    int32_t* status;        /* [n_pairs] out or NULL */
+    int32_t* iters;         /* [n_pairs] out or NULL */
+    const double* tof_ref;  /* [n_pairs] measured times, or NULL for no adjoint */
+    double* g_c;            /* [ny*nx] out when tof_ref is given: gradient of
+                               0.5*||T - tof_ref||^2 w.r.t. c, us^2/(m/s) */
+} rt_instance;
+
+/*
+ * rt_batch_run — rt_link plus, for instances with tof_ref, the adjoint of the
+ * L2 misfit (rt_tof_adjoint with g_tof = T), for n_inst problems of different
+ * grids and rings in ONE persistent launch over all their pairs (longest rings
+ * first, longest chords first within a ring). Each pair is linked (paper
+ * Sec. 3.4) and then retraced by the same lane with its adjoint weight
+ * T - T_ref (Sec. 3.1.1), so forward and adjoint share one launch.
+ *   inst   HOST array of n_inst descriptors (read during the call).
+ * Every per-instance output is as for rt_link / rt_tof_adjoint; status counts
+ * (summed over instances) are read with rt_status_counts. The call sizes the
+ * context's batch workspace on first use: make one call outside stream
+ * capture, after which the same batch (sizes unchanged) can be captured into
+ * a CUDA graph and replayed (the descriptor copy reads a pinned staging buffer
+ * that the call fills and that later calls overwrite).
+ */
+int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst, const rt_options* opt, void* stream);
 
 /*
  * rt_tof_forward_noalloc — the same travel times and interceptions as

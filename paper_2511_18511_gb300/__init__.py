@@ -19,7 +19,7 @@ from . import _lib as _L
 from .phantoms import Grid
 
 __all__ = ["Context", "Problem", "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix",
-           "rt_status_counts", "ToF", "tof", "PRECISIONS"]
+           "rt_status_counts", "rt_batch_run", "BatchInstance", "ToF", "tof", "PRECISIONS"]
 
 PRECISIONS = {"fp64": _L.RT_FP64, "fp32c": _L.RT_FP32_COMP}
 
@@ -109,10 +109,12 @@ class Problem:
 DEFAULT_FAN = 256
 
 
-def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN) -> _L.RtOptions:
+def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, block_threads=0,
+          step_unroll=0) -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
-    return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays), 0)
+    return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays),
+                        int(block_threads), int(step_unroll), 0)
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
@@ -233,3 +235,49 @@ def tof(c: torch.Tensor, prob: Problem, ds: float, tol: float = 1e-4, max_iter: 
         fan_rays: int = DEFAULT_FAN) -> torch.Tensor:
     """Differentiable travel times of all pairs of ``prob`` for sound speed c."""
     return ToF.apply(c, prob, ds, tol, max_iter, precision, theta0, fan_rays)
+
+
+@dataclasses.dataclass
+class BatchInstance:
+    """One problem of rt_batch_run with its outputs (device tensors)."""
+    prob: Problem
+    theta: torch.Tensor
+    tof: torch.Tensor
+    hit: torch.Tensor
+    status: torch.Tensor
+    iters: torch.Tensor
+    tof_ref: Optional[torch.Tensor] = None
+    g_c: Optional[torch.Tensor] = None
+
+    @staticmethod
+    def create(prob: Problem, tof_ref: Optional[torch.Tensor] = None) -> "BatchInstance":
+        n, dev = prob.n_pairs, prob.c.device
+        return BatchInstance(prob,
+                             torch.full((n,), float("nan"), dtype=torch.float64, device=dev),
+                             torch.empty(n, dtype=torch.float64, device=dev),
+                             torch.empty((n, 2), dtype=torch.float64, device=dev),
+                             torch.empty(n, dtype=torch.int32, device=dev),
+                             torch.empty(n, dtype=torch.int32, device=dev),
+                             None if tof_ref is None else tof_ref.contiguous(),
+                             None if tof_ref is None else torch.empty_like(prob.c))
+
+    def struct(self) -> _L.RtInstance:
+        return _L.RtInstance(self.prob.struct(), self.theta.data_ptr(), self.tof.data_ptr(), self.hit.data_ptr(),
+                             self.status.data_ptr(), self.iters.data_ptr(),
+                             None if self.tof_ref is None else self.tof_ref.data_ptr(),
+                             None if self.g_c is None else self.g_c.data_ptr())
+
+
+def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
+                 fan_rays: int = DEFAULT_FAN, block_threads: int = 0, step_unroll: int = 0,
+                 ctx: Optional[Context] = None, stream=None, reset_angles: bool = True):
+    """Link (and, where tof_ref is set, adjoint-scatter) every pair of every
+    instance in one persistent launch. reset_angles=True starts cold (NaN)."""
+    ctx = ctx or default_context(instances[0].prob.c.device.index)
+    if reset_angles:
+        for b in instances:
+            b.theta.fill_(float("nan"))
+    arr = (_L.RtInstance * len(instances))(*[b.struct() for b in instances])
+    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll)
+    _L.check(ctx.h, ctx.lib.rt_batch_run(ctx.h, len(instances), arr, C.byref(o), _stream(stream)))
+    return instances

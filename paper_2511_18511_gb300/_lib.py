@@ -20,7 +20,7 @@ RAY_OK, RAY_MAXITER, RAY_STEPCAP, RAY_BADINPUT = 0, 1, 2, 4
 EXPORTED = [
     "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_ctx_reserve",
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
-    "rt_tof_forward_noalloc",
+    "rt_tof_forward_noalloc", "rt_batch_run",
 ]
 
 
@@ -31,13 +31,20 @@ class RtGrid(C.Structure):
 
 class RtOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("ds_mm", C.c_double),
-                ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("reserved", C.c_int32)]
+                ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("block_threads", C.c_int32),
+                ("step_unroll", C.c_int32), ("reserved", C.c_int32)]
 
 
 class RtProblem(C.Structure):
     _fields_ = [("grid", RtGrid), ("c_mps", C.c_void_p), ("n_tx", C.c_int32),
                 ("tx_xy_mm", C.c_void_p), ("ring_radius_mm", C.c_double), ("n_pairs", C.c_int32),
                 ("pairs", C.c_void_p)]
+
+
+class RtInstance(C.Structure):
+    _fields_ = [("prob", RtProblem), ("theta_io", C.c_void_p), ("tof_us", C.c_void_p),
+                ("hit_xy_mm", C.c_void_p), ("status", C.c_void_p), ("iters", C.c_void_p),
+                ("tof_ref", C.c_void_p), ("g_c", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -78,6 +85,7 @@ def load():
                                      P(C.c_int64), vp]
         L.rt_status_counts.argtypes = [vp, P(C.c_int64), vp]
         L.rt_tof_forward_noalloc.argtypes = [P(RtProblem), P(RtOptions), vp, vp, vp, vp]
+        L.rt_batch_run.argtypes = [vp, C.c_int32, P(RtInstance), P(RtOptions), vp]
         _lib = L
         return L
 

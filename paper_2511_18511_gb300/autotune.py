@@ -1,0 +1,67 @@
+"""Autotuner for the batched persistent kernel.
+
+Times every supported (threads per block, RK4 steps per queue check) pair on
+the caller's batch with CUDA events and keeps the fastest. Results are cached
+per GPU name and batch signature in a JSON file next to the built library.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import build as _build
+
+CANDIDATES = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1), (256, 2)]
+CACHE = os.path.join(_build.OUT, "autotune.json")
+
+
+def signature(instances, precision: str, fan_rays: int) -> str:
+    parts = [f"{b.prob.grid.nx}x{b.prob.grid.ny}:{b.prob.n_tx}:{int(b.tof_ref is not None)}" for b in instances]
+    return f"{precision}|fan{fan_rays}|" + ",".join(sorted(parts))
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tune_batch(instances, ds: float, tol: float = 1e-4, precision: str = "fp32c", fan_rays: int = 256,
+               reps: int = 2, use_cache: bool = True, verbose: bool = False):
+    """Returns ((block_threads, step_unroll), {candidate: ms}) for this batch."""
+    from . import rt_batch_run
+    key = f"{torch.cuda.get_device_name()}|{signature(instances, precision, fan_rays)}"
+    cache = _load()
+    if use_cache and key in cache:
+        c = cache[key]
+        return tuple(c["best"]), {tuple(map(int, k.split(","))): v for k, v in c["ms"].items()}
+    cands = CANDIDATES if precision == "fp32c" else [(128, 1)]
+    times = {}
+    for blk, unr in cands:
+        rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk, step_unroll=unr)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk,
+                         step_unroll=unr)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        times[(blk, unr)] = best
+        if verbose:
+            print(f"autotune {blk} threads/block, unroll {unr}: {best:.2f} ms")
+    choice = min(times, key=times.get)
+    cache[key] = {"best": list(choice), "ms": {f"{k[0]},{k[1]}": v for k, v in times.items()}}
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, CACHE)
+    return choice, times

@@ -78,6 +78,9 @@ int prepare(rt_ctx* ctx, const rt_problem* p, const rt_options* o, bool need_lin
 
 namespace rt {
 
+int set_error(rt_ctx* ctx, int code, const std::string& msg) { return fail(ctx, code, msg); }
+bool stream_capturing(cudaStream_t s) { return capturing(s); }
+
 int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     if (!p) return fail(ctx, RT_EINVAL, "problem pointer is NULL");
     const rt_grid& g = p->grid;
@@ -149,7 +152,7 @@ int rt_ctx_create(rt_ctx** out, int device) {
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counters, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dflag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->queue, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->dflag, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -170,6 +173,9 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (ctx->scan_tmp) cudaFree(ctx->scan_tmp);
     if (ctx->fan) cudaFree(ctx->fan);
     if (ctx->fan_need) cudaFree(ctx->fan_need);
+    if (ctx->batch_ws) cudaFree(ctx->batch_ws);
+    if (ctx->batch_desc) cudaFree(ctx->batch_desc);
+    if (ctx->batch_desc_host) cudaFreeHost(ctx->batch_desc_host);
     delete ctx;
 }
 
@@ -191,8 +197,8 @@ int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* 
     rt::Geom G;
     int rc = prepare(ctx, prob, opt, true, s, &G);
     if (rc) return rc;
-    if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536 || opt->reserved != 0)
-        return fail(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]; reserved must be 0");
+    if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536)
+        return fail(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
     if (opt->fan_rays >= 2) {
         const size_t fan_bytes = sizeof(double) * (size_t)prob->n_tx * (size_t)opt->fan_rays;
         const size_t need_bytes = sizeof(int) * (size_t)prob->n_tx;

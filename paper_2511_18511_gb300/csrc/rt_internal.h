@@ -19,6 +19,12 @@ struct rt_ctx {
     double* fan = nullptr;          // [n_tx * fan_rays] interception angles of the emitter fans
     int* fan_need = nullptr;        // [n_tx] emitters with at least one cold-start pair
     size_t fan_cap = 0, need_cap = 0;
+    // batch workspace (rt_batch_run): packed fields, fans, flags; descriptors
+    void* batch_ws = nullptr;
+    size_t batch_ws_bytes = 0;
+    void* batch_desc = nullptr;       // device copy of the instance descriptors
+    void* batch_desc_host = nullptr;  // pinned staging of the descriptors
+    size_t batch_desc_bytes = 0;
     void* scan_tmp = nullptr;       // prefix-sum workspace (path matrix)
     size_t scan_bytes = 0;
     cudaStream_t last_stream = nullptr;
@@ -30,6 +36,9 @@ struct Geom;
 
 // Fills a Geom for a validated problem; returns RT_OK or RT_EINVAL (message in ctx).
 int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G);
+// Records an error message on ctx (when not null) and returns code.
+int set_error(rt_ctx* ctx, int code, const std::string& msg);
+bool stream_capturing(cudaStream_t s);
 
 // Kernel launchers (rt_ray.cu). All enqueue on `s` and return a cudaError_t.
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
@@ -38,6 +47,8 @@ cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, 
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
                         unsigned long long* counters, int* queue, int fan_rays, double* fan,
                         int* fan_need, cudaStream_t s);
+cudaError_t launch_fan(const Geom& G, const void* field, int prec, int fan_rays, const double* theta, double* fan,
+                       int* fan_need, unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double* theta, double* tof,
                        double* hit, cudaStream_t s);
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,

@@ -1,0 +1,311 @@
+// rt_link.cuh — device-side shooting-method linking shared by the single-
+// problem and the batched kernels: pair set-up, the linking state machine
+// (paper Sec. 3.4: Secant default with a Regula-Falsi safeguard), the fan
+// start, the persistent work queue, and the adjoint scatter sink.
+#pragma once
+
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include <math_constants.h>
+
+#include "rt_trace.cuh"
+
+namespace rt {
+
+constexpr double kPi = 3.141592653589793;
+
+__device__ __forceinline__ double mod_2pi(double a) { return a - 2.0 * kPi * floor(a / (2.0 * kPi)); }
+
+struct LinkCtx {
+    double xe, ye, xr, yr, phi_e, psi_r, th_lo, th_hi;
+};
+
+__device__ __forceinline__ bool on_ring(double x, double y, double R) {
+    return fabs(sqrt(x * x + y * y) - R) <= 1e-9 * R;
+}
+
+// Resolves pair k; false if the pair or its transducers are invalid.
+__device__ __forceinline__ bool setup_pair(const Geom& G, int k, LinkCtx& L) {
+    int e, r;
+    pair_of(G, k, e, r);
+    if (*G.bad_field || e < 0 || e >= G.n_tx || r < 0 || r >= G.n_tx || e == r) return false;
+    L.xe = G.tx[2 * e]; L.ye = G.tx[2 * e + 1];
+    L.xr = G.tx[2 * r]; L.yr = G.tx[2 * r + 1];
+    if (!on_ring(L.xe, L.ye, G.R) || !on_ring(L.xr, L.yr, G.R)) return false;
+    L.phi_e = atan2(L.ye, L.xe);
+    L.psi_r = mod_2pi(atan2(L.yr, L.xr) - L.phi_e);
+    L.th_lo = L.phi_e + 0.5 * kPi;
+    L.th_hi = L.phi_e + 1.5 * kPi;
+    return true;
+}
+
+// Per-lane linking state of the persistent kernel, kept in shared memory so
+// that only the trace state occupies registers in the marching loop.
+struct LinkState {
+    double xe, ye, xr, yr, phi_e, psi_r, th_lo, th_hi;
+    double a_min, a_max;
+    double th0, m0, mp;              // first angle, its misfit, the probe's misfit
+    double best_th, best_T, best_hx, best_hy, best_dist;
+    double ta, fa, tb, fb;           // bracket
+    double prev_th, prev_m, cur_th, cur_m;
+    double psi_at_lo, next;
+    int k, n_eval, phase, last, e0_flagged;
+    // adjoint retrace of the batched kernel (read on flushes only)
+    double* adj_g;
+    double adj_w;
+    int adj_nx, adj_ny;
+};
+
+__device__ __forceinline__ void br_insert(LinkState& L, double t, double m) {
+    if (!(t > fmin(L.ta, L.tb) && t < fmax(L.ta, L.tb))) return;
+    if (m < 0) {
+        L.ta = t; L.fa = m;
+        if (L.last == -1) L.fb *= 0.5;
+        L.last = -1;
+    } else {
+        L.tb = t; L.fb = m;
+        if (L.last == 1) L.fa *= 0.5;
+        L.last = 1;
+    }
+}
+
+// Misfit of an ended trace (same rule as evaluate()).
+__device__ __forceinline__ void misfit_of(const Geom& G, const LinkState& L, const TraceOut& o, double theta,
+                                          double& m, double& dist) {
+    const double dx = o.hx - L.xr, dy = o.hy - L.yr;
+    dist = sqrt(dx * dx + dy * dy);
+    double psi;
+    if (o.flags & 3) {
+        psi = (theta - L.th_lo < L.th_hi - theta) ? L.psi_at_lo : 2.0 * kPi - L.psi_at_lo;
+        dist = DBL_MAX;
+    } else {
+        psi = mod_2pi(atan2(o.hy, o.hx) - L.phi_e);
+    }
+    m = G.R * (psi - L.psi_r);
+}
+
+// Next angle inside the bracket: the secant of (prev, cur) if it falls inside,
+// else the Regula-Falsi point of the bracket.
+__device__ __forceinline__ double next_angle(const LinkState& L, double cand) {
+    if (!(isfinite(cand) && cand > fmin(L.ta, L.tb) && cand < fmax(L.ta, L.tb)))
+        cand = (L.ta * L.fb - L.tb * L.fa) / (L.fb - L.fa);
+    return cand;
+}
+
+// Linking update after the trace of L.next ended (the same decisions as
+// link_pair). Returns true when the pair is finished.
+__device__ inline bool link_update(const Geom& G, LinkState& L, const TraceOut& o, double tol, int max_iter) {
+    const double theta = L.next;
+    double m, dist;
+    misfit_of(G, L, o, theta, m, dist);
+    ++L.n_eval;
+    if (dist < L.best_dist) {
+        L.best_th = theta; L.best_T = o.T; L.best_hx = o.hx; L.best_hy = o.hy; L.best_dist = dist;
+    }
+    if (dist <= tol) return true;
+    if (L.phase == 0) {
+        L.m0 = m;
+        L.e0_flagged = (o.flags & 3) != 0;
+        if (L.n_eval >= max_iter) return true;
+        L.phase = 1;
+        L.next = L.a_min;   // orientation probe next to the fan's lower end
+        return false;
+    }
+    if (L.phase == 1) {
+        const bool ccw = (m / G.R + L.psi_r) < kPi;
+        L.psi_at_lo = ccw ? 0.0 : 2.0 * kPi;
+        if (L.e0_flagged) {
+            const double psi0 = (L.th0 - L.th_lo < L.th_hi - L.th0) ? L.psi_at_lo : 2.0 * kPi - L.psi_at_lo;
+            L.m0 = G.R * (psi0 - L.psi_r);
+        }
+        const double mp = (o.flags & 3) ? G.R * (L.psi_at_lo - L.psi_r) : m;
+        L.ta = ccw ? L.th_lo : L.th_hi; L.fa = -G.R * L.psi_r;
+        L.tb = ccw ? L.th_hi : L.th_lo; L.fb = G.R * (2.0 * kPi - L.psi_r);
+        L.last = 0;
+        br_insert(L, theta, mp);
+        br_insert(L, L.th0, L.m0);
+        L.last = 0;
+        L.prev_th = L.cur_th = L.th0;
+        L.prev_m = L.cur_m = L.m0;
+        if (L.n_eval >= max_iter) return true;
+        L.phase = 2;
+        L.next = next_angle(L, L.th0 - L.m0 / (ccw ? 2.0 * G.R : -2.0 * G.R));
+        return false;
+    }
+    br_insert(L, theta, m);
+    L.prev_th = L.cur_th; L.prev_m = L.cur_m;
+    L.cur_th = theta; L.cur_m = m;
+    if (L.n_eval >= max_iter) return true;
+    const double den = L.cur_m - L.prev_m;
+    const double cand = (den != 0.0) ? L.cur_th - L.cur_m * (L.cur_th - L.prev_th) / den : nan("");
+    L.next = next_angle(L, cand);
+    return false;
+}
+
+// ---------------------------------------------------------------- fan start
+
+__device__ __forceinline__ double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
+
+// Fan start of a cold pair (the rule of the CPU reference, written so that the
+// per-ray scan issues no FP64 instruction): the interval of the sequence (fan
+// end, rays 0..K-1, fan end) where psi crosses psi_r whose middle lies closest
+// to the straight-line angle in fan-index units; first angle from the inverse
+// cubic of the four rays around it (when monotone and inside), else linear.
+// psi values are non-negative, so "psi < psi_r" is the signed compare of their
+// IEEE bit patterns; NaN (no interception) has the largest patterns.
+__device__ inline void fan_start(const Geom& G, LinkState& L, const double* __restrict__ psi, int K) {
+    const bool ccw = isnan(psi[0]) ? true : (psi[0] < kPi);
+    L.psi_at_lo = ccw ? 0.0 : 2.0 * kPi;
+    const double psi_hi_end = 2.0 * kPi - L.psi_at_lo;
+    const double step = (L.a_max - L.a_min) / (K - 1);
+    double th_s = atan2(L.yr - L.ye, L.xr - L.xe);
+    th_s = L.th_lo + mod_2pi(th_s - L.th_lo);
+    const double u_s = (th_s - L.a_min) / step;
+    const long long* pb = reinterpret_cast<const long long*>(psi);
+    const long long b_r = __double_as_longlong(L.psi_r);
+    const long long b_lo = __double_as_longlong(L.psi_at_lo), b_hi = __double_as_longlong(psi_hi_end);
+    const long long b_nan = 0x7ff0000000000000ll;
+    bool neg_prev = b_lo < b_r;
+    int jsel = K + 1;
+    double best_gap = CUDART_INF;
+    for (int j = 1; j <= K + 1; ++j) {
+        long long b;
+        if (j <= K) {
+            const int k = j - 1;
+            b = pb[k];
+            if (b > b_nan) b = (k < K / 2) ? b_lo : b_hi;
+        } else {
+            b = b_hi;
+        }
+        const bool neg = b < b_r;
+        if (neg != neg_prev) {
+            const double gap = fabs((j - 1.5) - u_s);
+            if (gap < best_gap) { best_gap = gap; jsel = j; }
+        }
+        neg_prev = neg;
+    }
+    const double R = G.R;
+    double t0, t1, p0, p1;
+    {
+        const int ja = jsel - 1, jb = jsel;
+        if (ja == 0) { t0 = L.th_lo; p0 = L.psi_at_lo; }
+        else { const int k = ja - 1; t0 = fan_theta(L.a_min, step, k); p0 = psi[k]; if (isnan(p0)) p0 = (k < K / 2) ? L.psi_at_lo : psi_hi_end; }
+        if (jb == K + 1) { t1 = L.th_hi; p1 = psi_hi_end; }
+        else { const int k = jb - 1; t1 = fan_theta(L.a_min, step, k); p1 = psi[k]; if (isnan(p1)) p1 = (k < K / 2) ? L.psi_at_lo : psi_hi_end; }
+    }
+    const double m0 = R * (p0 - L.psi_r), m1 = R * (p1 - L.psi_r);
+    if (m0 < 0) { L.ta = t0; L.fa = m0; L.tb = t1; L.fb = m1; }
+    else { L.ta = t1; L.fa = m1; L.tb = t0; L.fb = m0; }
+    L.last = 0;
+    double th0 = t0 - m0 * (t1 - t0) / (m1 - m0);
+    const int k0 = jsel - 2;
+    if (k0 >= 1 && k0 + 2 <= K - 1) {
+        double tt[4], mm[4];
+        bool ok = true;
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 - 1 + q;
+            const double pk = psi[k];
+            if (isnan(pk)) ok = false;
+            tt[q] = fan_theta(L.a_min, step, k);
+            mm[q] = R * (pk - L.psi_r);
+        }
+        for (int q = 0; q < 3 && ok; ++q)
+            if (!((mm[q + 1] - mm[q]) * (mm[2] - mm[1]) > 0)) ok = false;
+        if (ok) {
+            double v = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                double l = 1.0;
+                for (int b = 0; b < 4; ++b)
+                    if (b != a) l *= (0.0 - mm[b]) / (mm[a] - mm[b]);
+                v += l * tt[a];
+            }
+            if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
+        }
+    }
+    if (!(th0 > fmin(L.ta, L.tb) && th0 < fmax(L.ta, L.tb))) th0 = 0.5 * (L.ta + L.tb);
+    const bool first = fabs(m0) <= fabs(m1);
+    L.cur_th = L.prev_th = first ? t0 : t1;
+    L.cur_m = L.prev_m = first ? m0 : m1;
+    L.th0 = th0;
+    L.next = th0;
+    L.phase = 2;
+}
+
+// Work order of the persistent kernel. For the all-pairs list, queue slot q
+// serves ring offsets o = r - e (mod N) from the longest chord (o = N/2) down to
+// the shortest (o = 1, N-1), N emitters per offset, so the launch's tail is
+// made of the shortest rays; the pair's own index k is returned. Explicit pair
+// lists are served in their order.
+__device__ __forceinline__ int queue_pair(const Geom& G, int q) {
+    if (G.pairs) return q;
+    const int N = G.n_tx;
+    const int t = q / N, e = q - t * N;
+    const int h = (N + 1) / 2;
+    const int o = (t & 1) ? h - (t + 1) / 2 : h + t / 2;
+    const int r = (e + o) % N;
+    return e * (N - 1) + r - (r > e);
+}
+
+// Warp-aggregated fetch of the next pair index from the work queue.
+__device__ __forceinline__ int fetch_pair(int* queue) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(queue, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+constexpr int kLinkBlock = 128;
+// Resident blocks per SM asked of the compiler: FP32 at <= 85 registers
+// (6 blocks, 24 warps), FP64 unconstrained.
+template <typename T> struct LinkOcc { static constexpr int blocks = 1; };
+template <> struct LinkOcc<float> { static constexpr int blocks = 6; };
+
+// Scatters w * alpha_m * phi_j(x_m) into g (FP64 atomics), one flush of the
+// four nodes per run of consecutive points in one cell. The node weights are
+// formed in the marching precision and widened exactly to FP64 for the atomic.
+template <typename T>
+struct AdjSink {
+    double* g;
+    T w;
+    int nx, ny;
+    CellAcc<T> acc;
+    __device__ __forceinline__ void flush() {
+        if (acc.ai == INT_MIN) return;
+        const T w11 = acc.Wxy, w10 = acc.Wx - acc.Wxy, w01 = acc.Wy - acc.Wxy;
+        const T w00 = (acc.W - acc.Wx) - w01;
+        const int i = min(max(acc.ai, 0), nx - 2), j = min(max(acc.aj, 0), ny - 2);
+        double* p = g + (size_t)j * nx + i;
+        atomicAdd(p, to_double(w * w00));
+        atomicAdd(p + 1, to_double(w * w10));
+        atomicAdd(p + nx, to_double(w * w01));
+        atomicAdd(p + nx + 1, to_double(w * w11));
+    }
+    __device__ __forceinline__ void add(int ci, int cj, T tx, T ty, T a) {
+        if (ci != acc.ai || cj != acc.aj) {
+            flush();
+            acc.reset();
+            acc.ai = ci;
+            acc.aj = cj;
+        }
+        acc.W += a;
+        acc.Wx += a * tx;
+        acc.Wy += a * ty;
+        acc.Wxy += a * tx * ty;
+    }
+    __device__ __forceinline__ void finish() {
+        flush();
+        acc.reset();
+    }
+};
+
+struct PairEnds {
+    double xe, ye, xr, yr;
+};
+
+
+}  // namespace rt
