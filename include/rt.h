@@ -81,11 +81,15 @@ typedef struct {
                             a fan of K rays per emitter predicts the first angle
                             and a bracket (256 is the usual); ignored by the calls
                             that take fixed angles */
-    int32_t block_threads; /* rt_batch_run only: threads per block of the persistent
-                            kernel, 0 (= 128), 64, 128 or 256 (FP64: 0 or 128) */
+    int32_t block_threads; /* rt_batch_run only: rays (threads) per block of the
+                            persistent kernel, 0 (= 128), 64, 128 or 256 */
     int32_t step_unroll;   /* rt_batch_run only: RK4 steps per work-queue check,
-                            0 (= 1), 1 or 2 (FP64: 0 or 1) */
-    int32_t reserved;      /* must be 0 */
+                            0 (= 1), 1 or 2 */
+    int32_t blocks_per_sm; /* rt_batch_run only: resident blocks per SM the kernel
+                            variant is compiled for (fewer registers, more warps),
+                            0 = 512 / block_threads. FP32 variants (threads, unroll,
+                            blocks): (64,1,8) (64,1,12) (128,1,4) (128,1,5) (128,1,6)
+                            (128,2,4) (256,1,2) (256,1,3); FP64: (128,1,1) */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system

@@ -110,11 +110,11 @@ DEFAULT_FAN = 256
 
 
 def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, block_threads=0,
-          step_unroll=0) -> _L.RtOptions:
+          step_unroll=0, blocks_per_sm=0) -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
     return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays),
-                        int(block_threads), int(step_unroll), 0)
+                        int(block_threads), int(step_unroll), int(blocks_per_sm))
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
@@ -270,7 +270,8 @@ class BatchInstance:
 
 def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
                  fan_rays: int = DEFAULT_FAN, block_threads: int = 0, step_unroll: int = 0,
-                 ctx: Optional[Context] = None, stream=None, reset_angles: bool = True):
+                 blocks_per_sm: int = 0, ctx: Optional[Context] = None, stream=None,
+                 reset_angles: bool = True):
     """Link (and, where tof_ref is set, adjoint-scatter) every pair of every
     instance in one persistent launch. reset_angles=True starts cold (NaN)."""
     ctx = ctx or default_context(instances[0].prob.c.device.index)
@@ -278,6 +279,6 @@ def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, pr
         for b in instances:
             b.theta.fill_(float("nan"))
     arr = (_L.RtInstance * len(instances))(*[b.struct() for b in instances])
-    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll, blocks_per_sm)
     _L.check(ctx.h, ctx.lib.rt_batch_run(ctx.h, len(instances), arr, C.byref(o), _stream(stream)))
     return instances

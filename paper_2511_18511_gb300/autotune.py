@@ -1,7 +1,8 @@
 """Autotuner for the batched persistent kernel.
 
-Times every supported (threads per block, RK4 steps per queue check) pair on
-the caller's batch with CUDA events and keeps the fastest. Results are cached
+Times every supported (rays per block, RK4 steps per queue check, resident
+blocks per SM) variant on the caller's batch with CUDA events and keeps the
+fastest. Results are cached
 per GPU name and batch signature in a JSON file next to the built library.
 """
 from __future__ import annotations
@@ -13,7 +14,9 @@ import torch
 
 from . import build as _build
 
-CANDIDATES = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1), (256, 2)]
+# (rays per block, RK4 steps per queue check, resident blocks per SM)
+CANDIDATES = [(64, 1, 8), (64, 1, 12), (128, 1, 4), (128, 1, 5), (128, 1, 6), (128, 2, 4), (256, 1, 2),
+              (256, 1, 3)]
 CACHE = os.path.join(_build.OUT, "autotune.json")
 
 
@@ -32,33 +35,34 @@ def _load():
 
 def tune_batch(instances, ds: float, tol: float = 1e-4, precision: str = "fp32c", fan_rays: int = 256,
                reps: int = 2, use_cache: bool = True, verbose: bool = False):
-    """Returns ((block_threads, step_unroll), {candidate: ms}) for this batch."""
+    """Returns ((block_threads, step_unroll, blocks_per_sm), {candidate: ms}) for this batch."""
     from . import rt_batch_run
     key = f"{torch.cuda.get_device_name()}|{signature(instances, precision, fan_rays)}"
     cache = _load()
     if use_cache and key in cache:
         c = cache[key]
         return tuple(c["best"]), {tuple(map(int, k.split(","))): v for k, v in c["ms"].items()}
-    cands = CANDIDATES if precision == "fp32c" else [(128, 1)]
+    cands = CANDIDATES if precision == "fp32c" else [(128, 1, 1)]
     times = {}
-    for blk, unr in cands:
-        rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk, step_unroll=unr)
+    for blk, unr, occ in cands:
+        rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk, step_unroll=unr,
+                     blocks_per_sm=occ)
         torch.cuda.synchronize()
         best = None
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk,
-                         step_unroll=unr)
+                         step_unroll=unr, blocks_per_sm=occ)
             b.record()
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
             best = ms if best is None else min(best, ms)
-        times[(blk, unr)] = best
+        times[(blk, unr, occ)] = best
         if verbose:
-            print(f"autotune {blk} threads/block, unroll {unr}: {best:.2f} ms")
+            print(f"autotune {blk} rays/block, unroll {unr}, {occ} blocks/SM: {best:.2f} ms")
     choice = min(times, key=times.get)
-    cache[key] = {"best": list(choice), "ms": {f"{k[0]},{k[1]}": v for k, v in times.items()}}
+    cache[key] = {"best": list(choice), "ms": {",".join(map(str, k)): v for k, v in times.items()}}
     os.makedirs(os.path.dirname(CACHE), exist_ok=True)
     tmp = CACHE + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:

@@ -89,11 +89,10 @@ __device__ __forceinline__ int find_inst(const BatchParams& P, long long q) {
     return lo;
 }
 
-template <typename T, int BLOCK> struct BatchOcc { static constexpr int blocks = 1; };
-template <int BLOCK> struct BatchOcc<float, BLOCK> { static constexpr int blocks = 512 / BLOCK; };   // <= 128 registers, no spills
-
-template <typename T, int BLOCK, int UNROLL>
-__global__ void __launch_bounds__(BLOCK, (BatchOcc<T, BLOCK>::blocks))
+// MINB: resident blocks per SM the kernel is compiled for (it caps the
+// registers per thread at 64K / (BLOCK * MINB); fewer registers, more warps).
+template <typename T, int BLOCK, int UNROLL, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
     k_batch(const __grid_constant__ BatchParams P, long long total, double tol, int max_iter, int fan_rays,
             unsigned long long* counters, unsigned long long* queue) {
     extern __shared__ unsigned char smem[];
@@ -243,42 +242,42 @@ using rt::InstDesc;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <typename T, int BLOCK, int UNROLL>
+template <typename T, int BLOCK, int UNROLL, int MINB>
 cudaError_t launch_batch_kernel(const rt::BatchParams& D, long long total, double tol, int max_iter,
                                 int fan_rays, unsigned long long* counters, unsigned long long* queue,
                                 cudaStream_t s) {
     static int blocks = 0;
     const size_t smem = sizeof(rt::LinkState) * BLOCK;
     if (!blocks) {
-        cudaError_t e = cudaFuncSetAttribute(rt::k_batch<T, BLOCK, UNROLL>,
+        cudaError_t e = cudaFuncSetAttribute(rt::k_batch<T, BLOCK, UNROLL, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt::k_batch<T, BLOCK, UNROLL>, BLOCK, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt::k_batch<T, BLOCK, UNROLL, MINB>, BLOCK, smem);
         blocks = sms * (per_sm > 0 ? per_sm : 1);
     }
     const long long need = (total + BLOCK - 1) / BLOCK;
     const int nb = (int)(need < blocks ? need : blocks);
     if (nb <= 0) return cudaSuccess;
-    rt::k_batch<T, BLOCK, UNROLL><<<nb, BLOCK, smem, s>>>(D, total, tol, max_iter, fan_rays, counters, queue);
+    rt::k_batch<T, BLOCK, UNROLL, MINB><<<nb, BLOCK, smem, s>>>(D, total, tol, max_iter, fan_rays, counters, queue);
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_batch(int prec, int block, int unroll, const rt::BatchParams& D, long long total,
+cudaError_t dispatch_batch(int prec, int block, int unroll, int bpsm, const rt::BatchParams& D, long long total,
                            double tol, int max_iter, int fan_rays, unsigned long long* counters,
                            unsigned long long* queue, cudaStream_t s, bool* ok) {
     *ok = true;
     if (prec == RT_FP64) {
-        if (block == 128 && unroll == 1)
-            return launch_batch_kernel<double, 128, 1>(D, total, tol, max_iter, fan_rays, counters, queue, s);
+        if (block == 128 && unroll == 1 && bpsm == 1)
+            return launch_batch_kernel<double, 128, 1, 1>(D, total, tol, max_iter, fan_rays, counters, queue, s);
     } else {
-#define RT_BATCH_CASE(B, U)                                                                                     \
-    if (block == B && unroll == U)                                                                              \
-        return launch_batch_kernel<float, B, U>(D, total, tol, max_iter, fan_rays, counters, queue, s);
-        RT_BATCH_CASE(64, 1) RT_BATCH_CASE(64, 2) RT_BATCH_CASE(128, 1) RT_BATCH_CASE(128, 2)
-        RT_BATCH_CASE(256, 1) RT_BATCH_CASE(256, 2)
+#define RT_BATCH_CASE(B, U, M)                                                                                      \
+    if (block == B && unroll == U && bpsm == M)                                                                     \
+        return launch_batch_kernel<float, B, U, M>(D, total, tol, max_iter, fan_rays, counters, queue, s);
+        RT_BATCH_CASE(64, 1, 8) RT_BATCH_CASE(64, 1, 12) RT_BATCH_CASE(128, 1, 4) RT_BATCH_CASE(128, 1, 5)
+        RT_BATCH_CASE(128, 1, 6) RT_BATCH_CASE(128, 2, 4) RT_BATCH_CASE(256, 1, 2) RT_BATCH_CASE(256, 1, 3)
 #undef RT_BATCH_CASE
     }
     *ok = false;
@@ -302,6 +301,8 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
         return rt::set_error(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
     const int block = opt->block_threads ? opt->block_threads : 128;
     const int unroll = opt->step_unroll ? opt->step_unroll : 1;
+    const int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm
+                                        : (opt->precision == RT_FP64 ? 1 : 512 / block);
     const size_t nb = rt::node_bytes(opt->precision);
     // per-instance geometry and workspace offsets; longest rings first
     std::vector<InstDesc> D((size_t)n_inst);
@@ -382,9 +383,10 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
     e = cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return rt::set_error(ctx, RT_ECUDA, std::string("queue reset: ") + cudaGetErrorString(e));
     bool ok = true;
-    e = dispatch_batch(opt->precision, block, unroll, params, total, opt->tol_mm, opt->max_iter, opt->fan_rays,
+    e = dispatch_batch(opt->precision, block, unroll, bpsm, params, total, opt->tol_mm, opt->max_iter, opt->fan_rays,
                        ctx->counters, reinterpret_cast<unsigned long long*>(ctx->queue), s, &ok);
-    if (!ok) return rt::set_error(ctx, RT_EINVAL, "unsupported block_threads / step_unroll for this precision");
+    if (!ok)
+        return rt::set_error(ctx, RT_EINVAL, "unsupported block_threads / step_unroll / blocks_per_sm combination");
     if (e != cudaSuccess) return rt::set_error(ctx, RT_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(e));
     rt::k_batch_finish<<<dim3(64, (unsigned)n_inst), 256, 0, s>>>(params);
     e = cudaGetLastError();

@@ -113,6 +113,8 @@ def test_autotuner_and_bad_options(rt, P, tmp_path, monkeypatch):
         rt.rt_batch_run(insts, 0.05, block_threads=96)
     with pytest.raises(rt._L.RtError):
         rt.rt_batch_run(insts, 0.05, precision="fp64", block_threads=256)
+    with pytest.raises(rt._L.RtError):
+        rt.rt_batch_run(insts, 0.05, block_threads=128, blocks_per_sm=7)
     L = rt._L.load()
     ctx = rt.default_context()
     o = rt._opts(0.05)
