@@ -1,8 +1,9 @@
-"""FP64 CPU oracle for two-point ray tracing: ctypes wrapper around oracle.c.
+"""FP64 CPU oracle for two-point ray tracing and ray-Born: ctypes wrapper
+around oracle.c and born.c.
 
 TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` use it; the library never does. It shares no code
-with the CUDA path. The C source is compiled on first use (gcc, OpenMP,
+with the CUDA path. The C sources are compiled on first use (gcc, OpenMP,
 ``-ffp-contract=off`` so that x86 and Arm hosts round identically).
 
 Every function takes plain numpy arrays in the library's units: lengths in mm,
@@ -18,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "oracle.c")]
+_SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "born.c")]
 _HDR = os.path.join(_HERE, "oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
@@ -29,7 +30,7 @@ RAY_OK, RAY_MAXITER, RAY_STEPCAP, RAY_BADINPUT = 0, 1, 2, 4
 
 
 def compile_to(out_path: str, sources=None) -> str:
-    """gcc-compile the oracle sources (default: oracle.c) into a shared library."""
+    """gcc-compile the oracle sources (default: oracle.c and born.c) into a shared library."""
     sources = list(sources or _SRC)
     tmp = out_path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
@@ -80,6 +81,15 @@ def load(path: str):
     L.orc_adjoint.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
                               C.c_double, _dp, _dp, _dp, C.c_int32]
     L.orc_num_threads.argtypes = []
+    L.orc_fan_angles.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, _dp, _dp]
+    L.orc_fan_ray.argtypes = [G, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                              C.c_int64, _dp, _lp]
+    L.orc_fan_maps.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_double, C.c_int32, _dp, _dp,
+                               C.c_int32]
+    L.orc_born_apply.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, C.c_int32, _dp, _dp, C.c_int32,
+                                 _ip, _dp, C.c_int32]
+    L.orc_born_adjoint.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, C.c_int32, _dp, _dp, _dp,
+                                   C.c_int32]
     return L
 
 
@@ -263,4 +273,69 @@ def adjoint(grid, c_mps, tx, R, ds, theta, g_tof, pairs=None, nthreads=0):
     rc = lib().orc_adjoint(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds,
                            _d(th), _d(gt), _d(out), nthreads)
     _check(rc, "adjoint")
+    return out
+
+
+# ---- ray-Born (born.c) ------------------------------------------------------
+
+def fan_angles(xe, R, ds, K):
+    """(a_min, step) of the fan of transducer xe: theta_k = a_min + k * step."""
+    a, st = C.c_double(0), C.c_double(0)
+    _check(lib().orc_fan_angles(float(xe[0]), float(xe[1]), R, ds, K, C.byref(a), C.byref(st)), "fan_angles")
+    return a.value, st.value
+
+
+def fan_ray(grid, c_mps, R, xe, theta, ds):
+    """One fan ray with its paraxial ray -> dict of per-sample arrays
+    x, y, dx, dy, T, Q, P, c, s (sample points strictly inside the ring)."""
+    c = _f64(c_mps)
+    cap = int(np.ceil(8.0 * R / ds)) + 2
+    rec = np.empty((cap, 9))
+    n = C.c_int64(0)
+    g = _grid(grid)
+    _check(lib().orc_fan_ray(C.byref(g), _d(c), R, float(xe[0]), float(xe[1]), theta, ds, cap, _d(rec),
+                             C.byref(n)), "fan_ray")
+    rec = rec[: min(n.value, cap)]
+    return {k: rec[:, q].copy() for q, k in enumerate(("x", "y", "dx", "dy", "T", "Q", "P", "c", "s"))}
+
+
+def fan_maps(grid, c_mps, tx, R, ds, K, nthreads=0):
+    """First-arrival maps (T us, A) of every transducer -> two [n_tx, ny, nx]
+    arrays (T = inf, A = 0 where no fan ray reaches)."""
+    c = _f64(c_mps)
+    tx = _f64(tx).reshape(-1, 2)
+    n_tx = tx.shape[0]
+    T = np.empty((n_tx, grid.ny, grid.nx))
+    A = np.empty((n_tx, grid.ny, grid.nx))
+    g = _grid(grid)
+    _check(lib().orc_fan_maps(C.byref(g), _d(c), n_tx, _d(tx), R, ds, K, _d(T), _d(A), nthreads), "fan_maps")
+    return T, A
+
+
+def born_apply(grid, R, T, A, f_mhz, dc, pairs=None, nthreads=0):
+    """Born data, complex: [n_freq, n_tx, n_tx] (pairs None) or [n_freq, n_pairs]."""
+    T, A = _f64(T), _f64(A)
+    n_tx = T.shape[0]
+    f = _f64(f_mhz).ravel()
+    dc = _f64(dc)
+    p = None if pairs is None else np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    n_out = n_tx * n_tx if p is None else p.shape[0]
+    out = np.empty((len(f), n_out, 2))
+    g = _grid(grid)
+    _check(lib().orc_born_apply(C.byref(g), R, n_tx, _d(T), _d(A), len(f), _d(f), _d(dc),
+                                0 if p is None else p.shape[0], _i(p), _d(out), nthreads), "born_apply")
+    d = out[..., 0] + 1j * out[..., 1]
+    return d.reshape(len(f), n_tx, n_tx) if p is None else d
+
+
+def born_adjoint(grid, R, T, A, f_mhz, d, nthreads=0):
+    """Adjoint of born_apply for complex d [n_freq, n_tx, n_tx] -> [ny, nx]."""
+    T, A = _f64(T), _f64(A)
+    n_tx = T.shape[0]
+    f = _f64(f_mhz).ravel()
+    dd = np.ascontiguousarray(np.stack([np.real(d), np.imag(d)], axis=-1), dtype=np.float64)
+    out = np.empty((grid.ny, grid.nx))
+    g = _grid(grid)
+    _check(lib().orc_born_adjoint(C.byref(g), R, n_tx, _d(T), _d(A), len(f), _d(f), _d(dd), _d(out),
+                                  nthreads), "born_adjoint")
     return out

@@ -90,6 +90,33 @@ int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const doub
 
 int orc_num_threads(void);
 
+/* ---- ray-Born (born.c) ------------------------------------------------ */
+
+/* Fan angles of transducer (xe, ye): theta_k = a_min + k * step, k < K. */
+int orc_fan_angles(double xe, double ye, double R, double ds, int32_t K, double* a_min, double* step);
+
+/* One fan ray with its paraxial ray; per sample point 9 values
+ * (x, y, dx, dy, T, Q, P, c, s) into rec9 (capacity cap points);
+ * *n_out = the number of points (may exceed cap). */
+int orc_fan_ray(const orc_grid* g, const double* c_mps, double R, double xe, double ye, double theta,
+                double ds, int64_t cap, double* rec9, int64_t* n_out);
+
+/* First-arrival travel-time and amplitude maps of every transducer from a
+ * fan of K rays each: T, A [n_tx][ny*nx] (T = +inf, A = 0 where unreached). */
+int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx, double R,
+                 double ds, int32_t K, double* T, double* A, int32_t nthreads);
+
+/* Born map: d[f][q] = omega^2 h^2 sum_{|x| < R} E_e E_r dc (complex, interleaved)
+ * for the listed pairs q = (e, r), or all n_tx x n_tx with pairs == NULL. */
+int orc_born_apply(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
+                   int32_t n_freq, const double* f_mhz, const double* dc, int32_t n_pairs,
+                   const int32_t* pairs, double* d_out, int32_t nthreads);
+
+/* Its adjoint: dc[x] from d[n_freq][n_tx][n_tx] (complex, interleaved). */
+int orc_born_adjoint(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
+                     int32_t n_freq, const double* f_mhz, const double* d_in, double* dc_out,
+                     int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -252,3 +252,55 @@ def born_perturbation(grid: Grid, ring_radius: float, seed: int = 5, sigma: floa
     dc = rng.normal(grid.nx * grid.ny, sigma).reshape(grid.ny, grid.nx)
     dc[x * x + y * y >= ring_radius**2] = 0.0
     return dc
+
+
+@dataclasses.dataclass
+class BornWorkload:
+    """One ray-Born problem: background medium and ring (for the fan maps),
+    the fan size, the frequencies and a sound-speed perturbation."""
+    name: str
+    grid: Grid
+    c: np.ndarray              # background sound speed [ny, nx] m/s
+    tx: np.ndarray             # transducer positions [N, 2] mm
+    ring_radius: float
+    ds: float
+    fan_rays: int              # rays per transducer fan
+    f_mhz: np.ndarray          # frequencies, MHz
+    dc: np.ndarray             # perturbation [ny, nx] m/s, 0 outside the ring
+
+    @property
+    def n_tx(self) -> int:
+        return int(self.tx.shape[0])
+
+
+def born_fan_rays(ring_radius: float, h: float, multiple: int = 64) -> int:
+    """Fan size K >= 2 pi * 2R / h (far-side ray spacing below one grid step),
+    rounded up to a multiple of `multiple`."""
+    k = math.ceil(2.0 * math.pi * 2.0 * ring_radius / h)
+    return int(multiple * math.ceil(k / multiple))
+
+
+def born_frequencies(n: int = 8, lo: float = 0.5, hi: float = 1.5) -> np.ndarray:
+    return np.linspace(lo, hi, n)
+
+
+def cfg_born(seed: int = 3, n: int = 1024, n_tx: int = 512, h: float = 0.2,
+             ring_radius: float = 95.0, ds: float = 0.02) -> BornWorkload:
+    """Ray-Born at full size: the breast model medium (1024^2 at 0.2 mm, 512-ring
+    at 95 mm), 8 frequencies 0.5-1.5 MHz, dc ~ N(0, 5 m/s) inside the ring."""
+    w = cfg_breast(seed, n, n_tx, h, ring_radius, ds)
+    return BornWorkload("born_breast_1024_ring512", w.grid, w.c, w.tx, ring_radius, ds,
+                        born_fan_rays(ring_radius, h), born_frequencies(),
+                        born_perturbation(w.grid, ring_radius, seed=5))
+
+
+def cfg_born_small(seed: int = 6, n: int = 128, n_tx: int = 64, h: float = 0.5,
+                   ring_radius: float = 30.0, ds: float = 0.05) -> BornWorkload:
+    """Scaled-down ray-Born: 128^2 at 0.5 mm, 64-ring at 30 mm, 3 broad Gaussian
+    inclusions (+-3%, sigma 4-8 mm), 8 frequencies 0.5-1.5 MHz."""
+    g = Grid(n, n, h)
+    c = gaussian_inclusions(g, seed, amp=0.03, sigma_lo=4.0, sigma_hi=8.0,
+                            centre_radius=0.6 * ring_radius)
+    return BornWorkload("born_gauss3_128_ring64", g, c, ring(n_tx, ring_radius), ring_radius, ds,
+                        born_fan_rays(ring_radius, h), born_frequencies(),
+                        born_perturbation(g, ring_radius, seed=seed + 1))

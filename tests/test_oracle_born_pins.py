@@ -1,0 +1,193 @@
+"""Pins of the FP64 ray-Born oracle (fan maps with paraxial rays, Born map and
+its adjoint) against closed forms and invariants, none of which reuses the
+oracle's own formulas: straight rays and circular arcs solve the ray and
+paraxial equations exactly, finite differences of neighbouring fan rays give
+the ray Jacobian independently of the paraxial system (the paper's auxiliary
+rays, Sec. 3.5), Fermat's principle ties the maps to the separately pinned
+two-point linking, and a point scatterer in a homogeneous medium has a closed
+Born response. The mutation tests show that plausible slips fail one of them.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_18511_gb300 import phantoms as P
+
+C0 = 1.5  # mm/us
+
+
+def _homog(n=64, h=0.5, R=14.0, n_tx=8):
+    g = P.Grid(n, n, h)
+    return g, P.homogeneous(g), P.ring(n_tx, R), R
+
+
+# ------------------------------------------------------------ single fan rays
+
+def test_fan_ray_homogeneous_straight(orc):
+    """c = const: the ray is straight, Q is the distance travelled, P = 1/c,
+    T = distance / c."""
+    g, c, tx, R = _homog()
+    r = orc.fan_ray(g, c, R, tx[0], np.pi + 0.3, 0.05)
+    dist = np.hypot(r["x"] - tx[0, 0], r["y"] - tx[0, 1])
+    assert len(dist) > 100
+    np.testing.assert_allclose(r["Q"], dist, atol=1e-11)
+    np.testing.assert_allclose(r["P"], 1.0 / C0, rtol=1e-14)
+    np.testing.assert_allclose(r["T"], dist / C0, atol=1e-12)
+    np.testing.assert_allclose(r["dx"], np.cos(np.pi + 0.3), atol=1e-14)
+
+
+@pytest.mark.parametrize("theta_off", [0.2, -0.5, 0.8])
+def test_fan_ray_linear_gradient_closed_form_Q(orc, theta_off):
+    """c = c_m + g y: the Hessian vanishes, so P = 1/c_t stays constant and
+    Q = int c ds / c_t. Along the circular ray, c ds = g rho^2 sin(phi) dphi
+    integrates to g rho |dx|, and rho = c_t / (g |cos a|) (Snell), so
+    Q = |x - x_e| / |cos a| with a the launch angle to the x axis."""
+    g = P.Grid(128, 128, 0.5)
+    c = P.linear_gradient(g)
+    tx = P.ring(16, 30.0)
+    th = np.pi + theta_off
+    r = orc.fan_ray(g, c, 30.0, tx[0], th, 0.05)
+    q = np.abs(r["x"] - tx[0, 0]) / abs(np.cos(th))
+    np.testing.assert_allclose(r["Q"][1:], q[1:], rtol=1e-10)
+    c_t = 1e-3 * (1500.0 + tx[0, 1])
+    np.testing.assert_allclose(r["P"], 1.0 / c_t, rtol=1e-12)
+
+
+@pytest.mark.parametrize("k,off", [(0, 0.1), (9, -0.6), (18, 0.9), (40, -0.25)])
+def test_paraxial_Q_matches_auxiliary_rays(orc, k, off):
+    """The paper's auxiliary-ray Jacobian (Sec. 3.5): two rays launched at
+    theta +- delta; their separation along the normal n of the reference ray,
+    divided by 2 delta, is dq/dtheta, which the paraxial Q (Q(0) = 0,
+    P(0) = 1/c_t) equals to first order. Broad Gaussian inclusions; the
+    remaining gap is the bilinear Hessian against the derivative of the
+    bilinear gradient, O(h^2)."""
+    w = P.cfg_born_small()
+    e = w.tx[k]
+    th = np.arctan2(e[1], e[0]) + np.pi + off
+    d = 1e-6
+    a = orc.fan_ray(w.grid, w.c, w.ring_radius, e, th, w.ds)
+    p = orc.fan_ray(w.grid, w.c, w.ring_radius, e, th + d, w.ds)
+    m = orc.fan_ray(w.grid, w.c, w.ring_radius, e, th - d, w.ds)
+    n = min(len(a["x"]), len(p["x"]), len(m["x"]))
+    q = (-a["dy"][:n] * (p["x"][:n] - m["x"][:n]) + a["dx"][:n] * (p["y"][:n] - m["y"][:n])) / (2 * d)
+    assert n > 200
+    err = np.abs(a["Q"][1:n] - q[1:n]).max() / np.abs(q[1:n]).max()
+    assert err < 2e-3, err
+
+
+# ------------------------------------------------------------------- the maps
+
+def test_maps_homogeneous_match_distance(orc):
+    """Homogeneous medium: every node inside the ring is reached, T = r/c up to
+    the third-order remainder of the second-order extrapolation
+    (|T - r/c| <= 0.2 s h^3 / r^2 for r >= 2h) and A = 1/sqrt(r) to
+    O(h/r) (the sample that wins lies within a cell of the node)."""
+    g, c, tx, R = _homog()
+    K = P.born_fan_rays(R, g.h)
+    T, A = orc.fan_maps(g, c, tx, R, 0.05, K)
+    x, y = g.node_xy()
+    inside = x * x + y * y < R * R
+    for t in range(len(tx)):
+        r = np.hypot(x - tx[t, 0], y - tx[t, 1])
+        assert np.isfinite(T[t][inside]).all() and (A[t][inside] > 0).all()
+        m = inside & (r >= 2 * g.h)
+        assert (np.abs(T[t][m] - r[m] / C0) <= 0.2 * g.h ** 3 / (C0 * r[m] ** 2)).all()
+        assert (np.abs(A[t][m] * np.sqrt(r[m]) - 1.0) <= 0.1 * g.h / r[m]).all()
+        assert np.isinf(T[t][x * x + y * y > (R + 2 * g.h) ** 2]).all()
+
+
+def test_maps_fermat_against_linking(orc):
+    """Fermat: for first-arrival maps, min_x T_e(x) + T_r(x) is the two-point
+    travel time, which the separately pinned linking oracle computes. Pairs at
+    least 8 elements apart (the node lattice misses the ray by < h, a
+    second-order excess that is relatively small on long rays)."""
+    w = P.cfg_born_small()
+    T, _ = orc.fan_maps(w.grid, w.c, w.tx, w.ring_radius, w.ds, w.fan_rays)
+    x, y = w.grid.node_xy()
+    inside = x * x + y * y < w.ring_radius ** 2
+    assert np.isfinite(T[:, inside]).all()
+    pairs = P.all_pairs(w.n_tx)
+    sep = np.abs(pairs[:, 0] - pairs[:, 1])
+    sep = np.minimum(sep, w.n_tx - sep)
+    sel = np.flatnonzero(sep >= 8)[::23]
+    L = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, pairs=pairs[sel], fan_rays=256)
+    rel = np.array([(T[e] + T[r])[inside].min() / L["tof"][k] - 1 for k, (e, r) in enumerate(pairs[sel])])
+    assert rel.min() >= -2e-4 and rel.max() <= 5e-4, (rel.min(), rel.max())
+
+
+# --------------------------------------------------------- Born map and adjoint
+
+def _synthetic_maps(g, tx, seed):
+    """Seeded smooth maps: straight-ray times plus a random ripple, 1/sqrt(r)."""
+    x, y = g.node_xy()
+    rng = P.SplitMix64(seed)
+    T = np.empty((len(tx), g.ny, g.nx))
+    A = np.empty_like(T)
+    for t in range(len(tx)):
+        r = np.hypot(x - tx[t, 0], y - tx[t, 1]) + 0.1
+        T[t] = r / C0 + 0.05 * rng.normal(x.size).reshape(x.shape)
+        A[t] = 1.0 / np.sqrt(r)
+    T[1, 3, 4] = np.inf            # an unreached node
+    A[1, 3, 4] = 0.0
+    return T, A
+
+
+def test_born_dot_product_identity(orc):
+    """Re<F dc, d> = <dc, F* d> for seeded random dc and complex d."""
+    g = P.Grid(24, 24, 0.5)
+    R = 5.5
+    tx = P.ring(6, R)
+    T, A = _synthetic_maps(g, tx, 3)
+    f = P.born_frequencies(3)
+    rng = P.SplitMix64(4)
+    dc = rng.normal(g.nx * g.ny).reshape(g.ny, g.nx)
+    d = (rng.normal(3 * 36) + 1j * rng.normal(3 * 36)).reshape(3, 6, 6)
+    lhs = np.sum(np.real(np.conj(orc.born_apply(g, R, T, A, f, dc)) * d))
+    rhs = np.sum(dc * orc.born_adjoint(g, R, T, A, f, d))
+    assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(dc)) * np.abs(d).sum() * 100, (lhs, rhs)
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+def test_born_point_scatterer_homogeneous(orc):
+    """One node x0 perturbed by dc in a homogeneous medium: the Born data are
+    omega^2 h^2 dc exp(i omega (r_e + r_r)/c) / sqrt(r_e r_r) (2D ray Green's
+    functions A = 1/sqrt(r), phase omega r / c), zero on the diagonal."""
+    g, c, tx, R = _homog()
+    T, A = orc.fan_maps(g, c, tx, R, 0.05, P.born_fan_rays(R, g.h))
+    x, y = g.node_xy()
+    j0, i0 = 30, 37
+    dc = np.zeros_like(c)
+    dc[j0, i0] = 3.0
+    f = P.born_frequencies(4)
+    d = orc.born_apply(g, R, T, A, f, dc)
+    rx = np.hypot(x[j0, i0] - tx[:, 0], y[j0, i0] - tx[:, 1])
+    for k, fm in enumerate(f):
+        om = 2 * np.pi * fm
+        want = om ** 2 * g.h ** 2 * 3.0 * np.exp(1j * om * (rx[:, None] + rx[None, :]) / C0) / np.sqrt(
+            rx[:, None] * rx[None, :])
+        np.fill_diagonal(want, 0.0)
+        assert np.all(np.diag(d[k]) == 0)
+        err = np.abs(d[k] - want)
+        bound = np.abs(want) * (0.1 * g.h / np.minimum(rx[:, None], rx[None, :]) + 1e-6)
+        assert (err <= bound).all(), (err / np.maximum(np.abs(want), 1e-300)).max()
+
+
+def test_born_adjoint_single_datum_homogeneous(orc):
+    """Adjoint of one datum d[f][e][r] = 1 in a homogeneous medium:
+    omega^2 h^2 cos(omega (r_e + r_r)/c) / sqrt(r_e r_r) at every node inside
+    the ring, 0 outside."""
+    g, c, tx, R = _homog()
+    T, A = orc.fan_maps(g, c, tx, R, 0.05, P.born_fan_rays(R, g.h))
+    f = P.born_frequencies(2)
+    d = np.zeros((2, len(tx), len(tx)), complex)
+    d[1, 2, 5] = 1.0
+    out = orc.born_adjoint(g, R, T, A, f, d)
+    x, y = g.node_xy()
+    inside = x * x + y * y < R * R
+    re = np.hypot(x - tx[2, 0], y - tx[2, 1])
+    rr = np.hypot(x - tx[5, 0], y - tx[5, 1])
+    om = 2 * np.pi * f[1]
+    want = om ** 2 * g.h ** 2 * np.cos(om * (re + rr) / C0) / np.sqrt(re * rr)
+    m = inside & (re >= 2 * g.h) & (rr >= 2 * g.h)
+    amp = om ** 2 * g.h ** 2 / np.sqrt(re * rr)
+    assert (np.abs(out[m] - want[m]) <= amp[m] * (0.1 * g.h / np.minimum(re, rr)[m] + 1e-6)).all()
+    assert (out[~inside] == 0).all()

@@ -1,10 +1,11 @@
 """Plant plausible mistakes in a temporary copy of the oracle and check that
 the pins catch every one of them.
 
-Each mutant is compiled from a copy of oracle.c with one textual change (a
-dropped term, a flipped sign, a wrong index, a transposed operand, a missing
-factor); the committed oracle is never touched. A mutant survives only if all
-pins in ``PINS`` still pass, which fails the test.
+Each mutant is compiled from a copy of the oracle sources with one textual
+change in oracle.c or born.c (a dropped term, a flipped sign, a wrong index, a
+transposed operand, a missing factor); the committed oracle is never touched.
+A mutant survives only if all pins of its file (``PINS`` or ``BORN_PINS``)
+still pass, which fails the test.
 """
 import os
 import shutil
@@ -12,6 +13,7 @@ import shutil
 import pytest
 
 import oracle
+from tests import test_oracle_born_pins as bpins
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -55,19 +57,84 @@ PINS = [
 ]
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_mutant_is_caught(name, tmp_path):
-    old, new = MUTANTS[name]
-    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+BORN_MUTANTS = {
+    "born_drop_cnn": ("k[5] = -cnn / (f[F_C] * f[F_C]) * st[4];", "k[5] = 0.0 * cnn;"),
+    "born_cnn_sign": ("k[5] = -cnn / (f[F_C] * f[F_C]) * st[4];", "k[5] = cnn / (f[F_C] * f[F_C]) * st[4];"),
+    "born_drop_hxy": ("- 2.0 * dx * dy * f[F_HXY]", "- 0.0 * dx * dy * f[F_HXY]"),
+    "born_hxx_hyy_swapped": ("(dy * dy * f[F_HXX] - 2.0 * dx * dy * f[F_HXY] + dx * dx * f[F_HYY])",
+                             "(dx * dx * f[F_HXX] - 2.0 * dx * dy * f[F_HXY] + dy * dy * f[F_HYY])"),
+    "born_hessian_scale": ("F->v[F_HXY][k] = (c[k + nx + 1] - c[k + nx - 1] - c[k - nx + 1] + c[k - nx - 1]) / (4 * h * h);",
+                           "F->v[F_HXY][k] = (c[k + nx + 1] - c[k + nx - 1] - c[k - nx + 1] + c[k - nx - 1]) / (2 * h * h);"),
+    "born_P0_is_c": ("double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, 1.0 / c_t}",
+                     "double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, c_t}"),
+    "born_Q_missing_c": ("k[4] = f[F_C] * st[5];", "k[4] = st[5];"),
+    "born_amplitude_no_sqrt": ("const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(p->Q, h))));",
+                               "const double A = p->c / (M->c_t * fabs(clamp_q(p->Q, h)));"),
+    "born_first_order_only": ("const double cand = p->T + p->s * along + 0.5 * curv * across * across;",
+                              "const double cand = p->T + p->s * along;"),
+    "born_nearest_node_only": ("for (int i = ic - 1; i <= ic + 1; ++i) {", "for (int i = ic; i <= ic; ++i) {"),
+    "born_latest_arrival": ("if (cand < M->T[k] || (cand == M->T[k] && A < M->A[k])) {",
+                            "if (!(cand <= M->T[k]) || M->T[k] == INFINITY) {"),
+    "born_T_uses_c": ("const double T = p.T + ds * 0.5 * (p.s + f[F_S]);",
+                      "const double T = p.T + ds * 0.5 * (p.c + f[F_C]);"),
+    "born_apply_conj": ("sim += (ar * bi + ai * br) * dc[k];", "sim += (ar * bi - ai * br) * dc[k];"),
+    "born_apply_omega_not_squared": ("const double scale = omega * omega * g->h * g->h;\n#pragma omp parallel for schedule(dynamic, 16)",
+                                     "const double scale = omega * g->h * g->h;\n#pragma omp parallel for schedule(dynamic, 16)"),
+    "born_apply_keeps_diagonal": ("if (e != r && e >= 0", "if (e >= 0"),
+    "born_adjoint_conj_one_factor": ("acc += scale * (pr * dd[0] + pi * dd[1]);",
+                                     "acc += scale * (pr * dd[0] - pi * dd[1]);"),
+    "born_adjoint_uses_diagonal": ("if (r == e) continue;\n                        const double br", "const double br"),
+    "born_phase_units": ("const double omega = 2.0 * M_PI * f_mhz[f];\n        const double scale = omega * omega * g->h * g->h;\n#pragma",
+                         "const double omega = M_PI * f_mhz[f];\n        const double scale = omega * omega * g->h * g->h;\n#pragma"),
+}
+
+BORN_PINS = [
+    bpins.test_fan_ray_homogeneous_straight,
+    lambda orc: bpins.test_fan_ray_linear_gradient_closed_form_Q(orc, 0.2),
+    lambda orc: bpins.test_paraxial_Q_matches_auxiliary_rays(orc, 0, 0.1),
+    lambda orc: bpins.test_paraxial_Q_matches_auxiliary_rays(orc, 9, -0.6),
+    bpins.test_maps_homogeneous_match_distance,
+    bpins.test_born_dot_product_identity,
+    bpins.test_born_point_scatterer_homogeneous,
+    bpins.test_born_adjoint_single_datum_homogeneous,
+    bpins.test_maps_fermat_against_linking,
+]
+
+
+def _compile_mutant(tmp_path, name, target, old, new):
+    here = os.path.dirname(oracle.__file__)
+    src = open(os.path.join(here, target)).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
-    shutil.copy(os.path.join(os.path.dirname(oracle.__file__), "oracle.h"), tmp_path / "oracle.h")
-    (tmp_path / "oracle.c").write_text(src.replace(old, new))
-    so = oracle.compile_to(str(tmp_path / f"liboracle_{name}.so"), [str(tmp_path / "oracle.c")])
-    L = oracle.load(so)
+    shutil.copy(os.path.join(here, "oracle.h"), tmp_path / "oracle.h")
+    for f in ("oracle.c", "born.c"):
+        text = open(os.path.join(here, f)).read()
+        (tmp_path / f).write_text(src.replace(old, new) if f == target else text)
+    so = oracle.compile_to(str(tmp_path / f"liboracle_{name}.so"),
+                           [str(tmp_path / "oracle.c"), str(tmp_path / "born.c")])
+    return oracle.load(so)
+
+
+def _survives(L, pin_list):
     with oracle.using(L):
-        for pin in PINS:
+        for pin in pin_list:
             try:
                 pin(oracle)
             except (AssertionError, ValueError, FloatingPointError):
-                return
-    pytest.fail(f"mutant {name} survived every pin")
+                return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    L = _compile_mutant(tmp_path, name, "oracle.c", old, new)
+    if _survives(L, PINS):
+        pytest.fail(f"mutant {name} survived every pin")
+
+
+@pytest.mark.parametrize("name", sorted(BORN_MUTANTS))
+def test_born_mutant_is_caught(name, tmp_path):
+    old, new = BORN_MUTANTS[name]
+    L = _compile_mutant(tmp_path, name, "born.c", old, new)
+    if _survives(L, BORN_PINS):
+        pytest.fail(f"mutant {name} survived every pin")
