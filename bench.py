@@ -53,9 +53,10 @@ def parse():
                          "the first N_EMIT emitters of the workload, then exit")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"],
                     help="precision of the --profile case")
-    ap.add_argument("--workload", default="breast", choices=["breast", "batch"],
+    ap.add_argument("--workload", default="breast", choices=["breast", "batch", "born"],
                     help="breast: the headline single problem; batch: 32 uneven instances in one persistent "
-                         "launch replayed from a CUDA graph")
+                         "launch replayed from a CUDA graph; born: ray-Born maps + apply + adjoint "
+                         "(1024^2, 512-ring, 8 frequencies)")
     return ap.parse_args()
 
 
@@ -132,6 +133,181 @@ def run_batch(args):
                          "rk4_steps_per_launch": counts[7]},
             "link": {"all_linked": ok, "status_counts": counts[:7]},
             "gpu_launches": args.steps * (3 * len(insts) + 2), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+# FLOPs of one RK4 step of the fan-map kernel (4 samples of c, grad c and the
+# Hessian, ray and paraxial right-hand sides, stage updates, compensated
+# position and direction updates, slowness and Kahan time, the 3 x 3 foot
+# test and the candidates that pass); the derivation is in the design notes.
+FLOP_PER_BORN_STEP = 403
+
+
+def _born_cpu_baseline(w, n_fans: int, n_pairs: int, n_nodes: int):
+    """The FP64 oracle on bounded samples of the ray-Born step, each part
+    extrapolated linearly to the full step: n_fans fans (maps), n_pairs
+    emitter-receiver pairs x all frequencies (apply), n_nodes nodes
+    (adjoint)."""
+    import oracle
+    from paper_2511_18511_gb300 import phantoms as P
+    oracle.build()
+    cores = oracle.num_threads()
+    sel = np.linspace(0, w.n_tx - 1, n_fans).astype(int)
+    t0 = time.perf_counter()
+    T, A = oracle.fan_maps(w.grid, w.c, w.tx[sel], w.ring_radius, w.ds, w.fan_rays)
+    t_maps = (time.perf_counter() - t0) * w.n_tx / n_fans
+    pairs = np.array([(a, b) for a in range(n_fans) for b in range(n_fans) if a != b][:n_pairs], np.int32)
+    t0 = time.perf_counter()
+    oracle.born_apply(w.grid, w.ring_radius, T, A, w.f_mhz, w.dc, pairs=pairs)
+    t_apply = (time.perf_counter() - t0) * (w.n_tx * (w.n_tx - 1)) / len(pairs)
+    # adjoint cost per node is that of all n_tx^2 pairs; time it on a sub-grid
+    # of n_nodes nodes around the centre with the full ring of maps replaced by
+    # the sampled fans repeated (cost depends on n_tx only)
+    gs = P.Grid(int(np.sqrt(n_nodes)), int(np.sqrt(n_nodes)), w.grid.h)
+    rng = P.SplitMix64(7)
+    j0, i0 = (w.grid.ny - gs.ny) // 2, (w.grid.nx - gs.nx) // 2
+    Ts = np.tile(T[:1, j0:j0 + gs.ny, i0:i0 + gs.nx], (w.n_tx, 1, 1))
+    As = np.tile(A[:1, j0:j0 + gs.ny, i0:i0 + gs.nx], (w.n_tx, 1, 1))
+    n = len(w.f_mhz) * w.n_tx * w.n_tx
+    d = (rng.normal(n) + 1j * rng.normal(n)).reshape(len(w.f_mhz), w.n_tx, w.n_tx)
+    t0 = time.perf_counter()
+    oracle.born_adjoint(gs, 1e9, Ts, As, w.f_mhz, d)
+    n_in = int(np.sum(np.hypot(*w.grid.node_xy()) < w.ring_radius))
+    t_adj = (time.perf_counter() - t0) * n_in / (gs.nx * gs.ny)
+    total = t_maps + t_apply + t_adj
+    data = len(w.f_mhz) * w.n_tx * (w.n_tx - 1)
+    return {"value": data / total, "unit": "Born data/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_fans} fan maps ({w.fan_rays} rays each, two passes), {len(pairs)} pairs x "
+                      f"{len(w.f_mhz)} frequencies of the Born map, {gs.nx * gs.ny} nodes of the adjoint; "
+                      f"each extrapolated linearly to the full step: maps {t_maps:.0f} s, apply {t_apply:.0f} s, "
+                      f"adjoint {t_adj:.0f} s"}
+
+
+def run_born(args):
+    """Ray-Born step on the breast model medium: first-arrival maps of all 512
+    transducers (rtborn_maps), the Born data of a seeded perturbation at 8
+    frequencies (rtborn_apply) and the adjoint of those data (rtborn_adjoint)."""
+    import torch
+    import paper_2511_18511_gb300 as rt
+    from paper_2511_18511_gb300 import phantoms as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = P.cfg_born()
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, device=dev)
+    dc = torch.as_tensor(w.dc, dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    nf = len(w.f_mhz)
+    maps = rt.rtborn_maps(prob, w.ds, w.fan_rays)
+    d = rt.rtborn_apply(maps, w.f_mhz, dc)
+    g = rt.rtborn_adjoint(maps, w.f_mhz, d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(gemm, ev=None):
+        if ev:
+            ev[0].record(s)
+        rt.rtborn_maps(prob, w.ds, w.fan_rays, out=maps)
+        if ev:
+            ev[1].record(s)
+        rt.rtborn_apply(maps, w.f_mhz, dc, gemm=gemm, out=d)
+        if ev:
+            ev[2].record(s)
+        rt.rtborn_adjoint(maps, w.f_mhz, d, gemm=gemm, out=g)
+        if ev:
+            ev[3].record(s)
+
+    def timed(gemm, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            step(gemm)
+        torch.cuda.synchronize()
+        evs = []
+        if clocks:
+            clocks.start()
+        for _ in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            step(gemm, ev)
+            evs.append(ev)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        part = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(3)] for e in evs]).mean(0)
+        return part, clk
+
+    clocks = Clocks(0)
+    part, clk = timed("bf16x9", args.steps, args.warmup, clocks)
+    _, counts = rt.rt_status_counts()
+    steps_per_call = counts[7]
+    part32, _ = timed("fp32", 1, 1)
+    ms = float(part.sum())
+    data = nf * w.n_tx * (w.n_tx - 1)
+    n_in = int(np.sum(np.hypot(*w.grid.node_xy()) < w.ring_radius))
+    gemm_flop = nf * 8.0 * w.n_tx * w.n_tx * n_in        # one complex GEMM per frequency
+    maps_tflops = steps_per_call * FLOP_PER_BORN_STEP / (part[0] / 1e3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16 = float(peaks["bf16_tflops"])
+    gemm_peak = bf16 / 9.0                                 # FP32 emulated by 9 BF16 products
+    apply_tflops = gemm_flop / (part[1] / 1e3) / 1e12
+    adj_tflops = gemm_flop / (part[2] / 1e3) / 1e12
+    dominant = int(np.argmax(part))
+    if dominant == 0:
+        roof = {"bound": "alu", "achieved": maps_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": maps_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_born_fan (two passes) + pack + unpack",
+                "flop_per_rk4_step": FLOP_PER_BORN_STEP, "rk4_steps_per_launch": steps_per_call,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"}
+    else:
+        a = apply_tflops if dominant == 1 else adj_tflops
+        roof = {"bound": "tensor", "achieved": a, "peak": gemm_peak, "unit": "TFLOP/s", "frac": a / gemm_peak,
+                "traffic": None, "kernel": "cuBLAS CGEMM (BF16x9-emulated FP32) + E-field kernels",
+                "peak_basis": f"measured bf16 burst {bf16} TFLOP/s / 9"}
+    # e2e: host c and dc in, host data and gradient out
+    c_host = torch.as_tensor(w.c).pin_memory()
+    dc_host = torch.as_tensor(w.dc, dtype=torch.float32).pin_memory()
+    d_host = torch.empty(d.shape, dtype=torch.complex64).pin_memory()
+    g_host = torch.empty(g.shape, dtype=torch.float32).pin_memory()
+    c_dev = torch.empty_like(prob.c)
+
+    def e2e_step():
+        c_dev.copy_(c_host, non_blocking=True)
+        dc.copy_(dc_host, non_blocking=True)
+        rt.rtborn_maps(prob, w.ds, w.fan_rays, c=c_dev, out=maps)
+        rt.rtborn_apply(maps, w.f_mhz, dc, out=d)
+        rt.rtborn_adjoint(maps, w.f_mhz, d, out=g)
+        d_host.copy_(d, non_blocking=True)
+        g_host.copy_(g, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = 2
+    for _ in range(n_e2e):
+        e2e_step()
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    line = {"metric": "ray-Born data/s (fan maps + Born apply + adjoint, 8 frequencies, 512-ring, 1024^2 grid)",
+            "value": data / (ms / 1e3), "unit": "Born data/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": f"{w.grid.nx}x{w.grid.ny}", "h_mm": w.grid.h, "ring": w.n_tx,
+                       "ring_radius_mm": w.ring_radius, "fan_rays": w.fan_rays, "ds_mm": w.ds,
+                       "f_mhz": [float(f) for f in w.f_mhz], "inside_nodes": n_in, "gemm": "bf16x9",
+                       "step": "rtborn_maps + rtborn_apply + rtborn_adjoint",
+                       "l2": "flushed between timed steps (256 MB write); maps 4.3 GB, E 2.9 GB per frequency"},
+            "parts_ms": {"maps": float(part[0]), "apply": float(part[1]), "adjoint": float(part[2])},
+            "parts_ms_fp32_gemm": {"maps": float(part32[0]), "apply": float(part32[1]), "adjoint": float(part32[2])},
+            "gemm_tflops": {"apply_bf16x9": apply_tflops, "adjoint_bf16x9": adj_tflops,
+                            "apply_fp32": gemm_flop / (part32[1] / 1e3) / 1e12,
+                            "adjoint_fp32": gemm_flop / (part32[2] / 1e3) / 1e12},
+            "maps": {"rays": w.n_tx * w.fan_rays, "rk4_steps_both_passes": steps_per_call,
+                     "tflops": maps_tflops, "rays_per_s": w.n_tx * w.fan_rays / (part[0] / 1e3)},
+            "roofline": roof,
+            "e2e": {"value": data / e2e_s, "unit": "Born data/s",
+                    "h2d_bytes_per_step": c_host.numel() * 8 + dc_host.numel() * 4,
+                    "d2h_bytes_per_step": d_host.numel() * 8 + g_host.numel() * 4},
+            "gpu_launches": args.steps * (4 + (nf + 1) + (3 * nf + 1)),
+            "library_launches": {"cublas_gemm": 2 * nf * args.steps},
+            "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _born_cpu_baseline(w, n_fans=16, n_pairs=64, n_nodes=1024)
     print(json.dumps(line), flush=True)
 
 
@@ -268,6 +444,8 @@ def main():
         return run_profile_case(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "born":
+        return run_born(args)
     import torch
     import paper_2511_18511_gb300 as rt
 

@@ -246,6 +246,94 @@ int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst, const rt_
 int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* opt, const double* theta,
                            double* tof_us, double* hit_xy_mm, void* stream);
 
+
+/* ------------------------------------------------------------------ ray-Born
+ * The ray-Born operator of arXiv:2511.18511 (Sec. 3.5 and the Appendix): the
+ * Green's function from transducer t to a point x is g = A_t(x) exp(i omega
+ * T_t(x)), with the phase from the eikonal (travel time along rays) and the
+ * geometric amplitude from the transport equation through the ray Jacobian,
+ * which a paraxial ray traced with each ray supplies (Sec. 3.5, default). The
+ * backward Green's functions of the receivers are the same per-transducer maps
+ * (reciprocity). Absorption is not modelled (A_abs = 1).
+ */
+
+/* Window of near-simultaneous arrivals for the amplitude choice of rtborn_maps. */
+#define RTBORN_EPS_REL 1e-5f
+#define RTBORN_EPS_ABS_US 1e-5f
+
+/* GEMM arithmetic of rtborn_apply / rtborn_adjoint (complex64 in and out). */
+enum rtborn_gemm {
+    RTBORN_GEMM_FP32 = 0,    /* FP32 multiply-add (SIMT) */
+    RTBORN_GEMM_BF16X9 = 1   /* FP32 emulated on the BF16 tensor cores (each
+                                operand split into three BF16 parts) */
+};
+
+/*
+ * rtborn_maps — first-arrival travel-time and amplitude maps of every
+ * transducer, from a fan of fan_rays rays per transducer at evenly spaced
+ * angles over the inward half-plane (tangents excluded by a margin ds/R).
+ * Each ray is marched with RK4 at the fixed step opt->ds_mm (<= h) together
+ * with its paraxial ray (Q, P): dQ/ds = c P, dP/ds = -(c_nn/c^2) Q, Q(0) = 0,
+ * P(0) = 1/c_t, c_nn the second derivative of c across the ray (central
+ * second differences interpolated bilinearly); the travel time by the
+ * trapezoid rule over the interpolated slowness; A = sqrt(c/(c_t max(|Q|, h))).
+ * Every sample point offers each node of the 3 x 3 block around its nearest
+ * node whose foot on the ray lies within half a step (a = d.D in [-ds/2, ds/2),
+ * D = node - point, b = n.D) the second-order ray-centred extrapolation from
+ * that foot, T + s a + (P/Q_f)/2 b^2 with Q_f = Q + a c P (|Q_f| clamped to
+ * >= h where P/Q_f < 0), and A from Q_f. A node's time is its earliest
+ * candidate (first arrival); its amplitude is that of the candidate from the
+ * ray passing closest to the node (smallest |b|, then the smaller A) among
+ * those within RTBORN_EPS_REL * T + RTBORN_EPS_ABS_US of the first arrival.
+ * The fan is traced twice (once per choice).
+ *   prob      grid, c_mps, n_tx, tx_xy_mm, ring_radius_mm (pairs ignored).
+ *   opt       precision must be RT_FP32_COMP; ds_mm in (0, h]; others ignored.
+ *   fan_rays  rays per fan in [2, 2^20]; about 4 pi R / h covers the far side
+ *             of the ring at one ray per half grid step.
+ *   T_out     [n_tx][ny*nx] float out, us; +inf where no ray arrives.
+ *   A_out     [n_tx][ny*nx] float out, amplitude (mm^-1/2); 0 where none.
+ * Workspace: 12 bytes per map entry (n_tx * nx * ny) plus 32 bytes per node.
+ * rt_status_counts afterwards reports counts[7] = RK4 steps of both passes
+ * (counts[0..6] = 0).
+ * A sound speed <= 0 or NaN anywhere leaves every entry unreached.
+ */
+int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int32_t fan_rays,
+                float* T_out, float* A_out, void* stream);
+
+/*
+ * rtborn_apply — the linearised Born map (Appendix: Helmholtz model with the
+ * ray Green's functions; scattered data from a sound-speed perturbation):
+ *   d[f][e][r] = omega_f^2 h^2 sum_{|x_n| < R} E_e(x_n) E_r(x_n) dc(x_n), e != r,
+ *   d[f][e][e] = 0,  E_t = A_t exp(i omega_f T_t) (0 where T_t = inf),
+ * omega_f = 2 pi f_mhz[f] rad/us, over the grid nodes strictly inside the ring
+ * of radius ring_radius_mm. The physical prefactors of the scattering
+ * potential (-2/c^3 and the source spectrum) are left to the caller.
+ *   T, A      [n_tx][ny*nx] maps as written by rtborn_maps.
+ *   f_mhz     HOST [n_freq] frequencies (MHz).
+ *   dc_mps    [ny*nx] float perturbation (m/s).
+ *   gemm_mode enum rtborn_gemm.
+ *   d_out     [n_freq][n_tx][n_tx] complex64 out, interleaved (re, im) floats.
+ * The first call for a grid and ring builds the list of inside nodes on the
+ * host and synchronises the stream once. Workspace: 2 x 8 bytes x n_tx x
+ * (inside nodes), reused over frequencies and calls.
+ */
+int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                 const float* A, int32_t n_freq, const double* f_mhz, const float* dc_mps,
+                 int32_t gemm_mode, float* d_out, void* stream);
+
+/*
+ * rtborn_adjoint — the adjoint of rtborn_apply under Re<a, b> = Re sum
+ * conj(a) b on the data and the plain dot product on dc:
+ *   dc_out[x] = Re sum_f omega_f^2 h^2 sum_{e != r} conj(E_e(x) E_r(x)) d[f][e][r]
+ * for nodes inside the ring, 0 elsewhere (the diagonal of d is ignored).
+ *   d_in      [n_freq][n_tx][n_tx] complex64, interleaved.
+ *   dc_out    [ny*nx] float out.
+ * Other arguments as for rtborn_apply.
+ */
+int rtborn_adjoint(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                   const float* A, int32_t n_freq, const double* f_mhz, const float* d_in,
+                   int32_t gemm_mode, float* dc_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

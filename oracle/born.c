@@ -31,14 +31,19 @@
  *      the clamp at the grid spacing h bounds it at the source and at caustics;
  *   B5 maps: every sample point after the transducer offers each node of the
  *      3 x 3 block around its nearest node whose foot on the ray lies within
- *      half a step of it (-ds/2 <= d_m.D < ds/2, D = node - sample) the travel
- *      time extrapolated to second order in the ray-centred frame,
- *      T_m + s_m d_m.D + (M_m / 2) (n_m.D)^2, where M = P/Q is the wavefront
- *      curvature of the paraxial ray (for M < 0, a converging front, |Q| is
- *      clamped to >= h so that a focus cannot send the time to -inf), paired
- *      with A_m; each node keeps the earliest candidate (first arrival), ties
- *      to the smaller A. Unreached nodes keep T = +inf, A = 0;
- *   B6 Born map, per frequency f (MHz; omega = 2 pi f rad/us):
+ *      half a step of it (a = d_m.D in [-ds/2, ds/2), D = node - sample,
+ *      b = n_m.D) the travel time extrapolated to second order in the
+ *      ray-centred frame, T_m + s_m a + (M / 2) b^2, with M = P/Q_f the
+ *      curvature of the paraxial wavefront at the foot, Q_f = Q_m + a c_m P_m
+ *      (for M < 0, a converging front, |Q_f| is clamped to >= h so that a focus
+ *      cannot send the time to -inf), with the amplitude A from Q_f. A node's
+ *      travel time is its earliest candidate (first arrival). Its amplitude is
+ *      that of the candidate, among those within eps_rel T + eps_abs of the
+ *      first arrival, from the ray passing closest to the node (smallest |b|,
+ *      ties to the smaller A): rays near a node arrive within far less than
+ *      any rounding of T of one another, so the earliest alone would pick
+ *      among them by rounding, while their amplitudes differ by the spreading
+ *      across the fan. Unreached nodes keep T = +inf, A = 0; *   B6 Born map, per frequency f (MHz; omega = 2 pi f rad/us):
  *      d[f][e][r] = omega^2 h^2 sum_x E_e(x) E_r(x) dc(x) for e != r, 0 for
  *      e == r, E_t = A_t exp(i omega T_t) (0 where unreached), x over the nodes
  *      strictly inside the ring (dc in m/s as given);
@@ -185,6 +190,8 @@ typedef struct {
     double *T, *A;    /* map mode: [ny*nx] of one transducer */
     double* rec;      /* record mode: 9 values per sample */
     int64_t cap, n;
+    double* B;                  /* map mode: |b| of the kept candidate */
+    double eps_rel, eps_abs;    /* map mode: near-simultaneous window */
 } MapCtx;
 
 static double clamp_q(double q, double h) {
@@ -192,15 +199,13 @@ static double clamp_q(double q, double h) {
     return q < 0 ? -h : h;
 }
 
-/* B4 + B5 */
-static void deposit(void* vctx, const BSample* p) {
-    MapCtx* M = (MapCtx*)vctx;
+typedef void (*offer_fn)(MapCtx* M, size_t k, double cand, double b, double A);
+
+/* B4 + B5: every candidate (node k, time, amplitude) of sample p */
+static void candidates(MapCtx* M, const BSample* p, offer_fn offer) {
     const BField* F = M->F;
     const double h = F->h;
     if (p->T == 0.0) return; /* the transducer itself */
-    const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(p->Q, h))));
-    double curv = p->P / p->Q;
-    if (curv < 0) curv = p->P / clamp_q(p->Q, h);
     const int ic = (int)floor((p->x - F->x0) / h + 0.5), jc = (int)floor((p->y - F->y0) / h + 0.5);
     for (int j = jc - 1; j <= jc + 1; ++j) {
         if (j < 0 || j >= F->ny) continue;
@@ -209,15 +214,36 @@ static void deposit(void* vctx, const BSample* p) {
             const double Dx = F->x0 + i * h - p->x, Dy = F->y0 + j * h - p->y;
             const double along = p->dx * Dx + p->dy * Dy, across = -p->dy * Dx + p->dx * Dy;
             if (!(along >= -0.5 * M->ds && along < 0.5 * M->ds)) continue;
-            const double cand = p->T + p->s * along + 0.5 * curv * across * across;
-            const size_t k = (size_t)j * F->nx + i;
-            if (cand < M->T[k] || (cand == M->T[k] && A < M->A[k])) {
-                M->T[k] = cand;
-                M->A[k] = A;
-            }
+            /* paraxial Q carried to the foot of the node: dQ/ds = c P */
+            const double Qf = p->Q + along * p->c * p->P;
+            double curv = p->P / Qf;
+            if (!(curv >= 0)) curv = p->P / clamp_q(Qf, h);
+            const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(Qf, h))));
+            offer(M, (size_t)j * F->nx + i, p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A);
         }
     }
 }
+
+/* pass 1: the first arrival, the earliest candidate */
+static void keep_first(MapCtx* M, size_t k, double cand, double b, double A) {
+    (void)b;
+    (void)A;
+    if (cand < M->T[k]) M->T[k] = cand;
+}
+
+/* pass 2: among the candidates within eps of the first arrival, the one from
+ * the ray passing closest to the node (ties to the smaller amplitude) */
+static void keep_nearest(MapCtx* M, size_t k, double cand, double b, double A) {
+    const double Tf = M->T[k];
+    if (!(cand <= Tf + M->eps_rel * Tf + M->eps_abs)) return;
+    if (b < M->B[k] || (b == M->B[k] && A < M->A[k])) {
+        M->B[k] = b;
+        M->A[k] = A;
+    }
+}
+
+static void deposit_first(void* vctx, const BSample* p) { candidates((MapCtx*)vctx, p, keep_first); }
+static void deposit_nearest(void* vctx, const BSample* p) { candidates((MapCtx*)vctx, p, keep_nearest); }
 
 static void record(void* vctx, const BSample* p) {
     MapCtx* M = (MapCtx*)vctx;
@@ -276,28 +302,36 @@ int orc_fan_angles(double xe, double ye, double R, double ds, int32_t K, double*
 }
 
 int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx, double R,
-                 double ds, int32_t K, double* T, double* A, int32_t nthreads) {
-    if (!g || !tx || n_tx < 1 || K < 2 || !T || !A || !(ds > 0) || !(R > 0)) return ORC_EINVAL;
+                 double ds, int32_t K, double eps_rel, double eps_abs, double* T, double* A, int32_t nthreads) {
+    if (!g || !tx || n_tx < 1 || K < 2 || !T || !A || !(ds > 0) || !(R > 0) || !(eps_rel >= 0) || !(eps_abs >= 0))
+        return ORC_EINVAL;
     BField F;
     int rc = bfield_make(&F, g, c_mps);
     if (rc) return rc;
     const size_t nn = (size_t)F.nx * F.ny;
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads))
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads)) reduction(| : bad)
     for (int32_t t = 0; t < n_tx; ++t) {
         MapCtx M = {0};
         M.F = &F;
         M.T = T + (size_t)t * nn;
         M.A = A + (size_t)t * nn;
-        for (size_t k = 0; k < nn; ++k) { M.T[k] = INFINITY; M.A[k] = 0.0; }
+        M.B = malloc(nn * sizeof(double));
+        if (!M.B) { bad = 1; continue; }
+        M.eps_rel = eps_rel;
+        M.eps_abs = eps_abs;
+        for (size_t k = 0; k < nn; ++k) { M.T[k] = INFINITY; M.A[k] = 0.0; M.B[k] = INFINITY; }
         const double xe = tx[2 * t], ye = tx[2 * t + 1];
         M.c_t = c_at(&F, xe, ye);
         M.ds = ds;
         double a_min, step;
         fan_angles(xe, ye, R, ds, K, &a_min, &step);
-        for (int k = 0; k < K; ++k) fan_ray(&F, R, xe, ye, a_min + k * step, ds, M.c_t, &M, deposit);
+        for (int k = 0; k < K; ++k) fan_ray(&F, R, xe, ye, a_min + k * step, ds, M.c_t, &M, deposit_first);
+        for (int k = 0; k < K; ++k) fan_ray(&F, R, xe, ye, a_min + k * step, ds, M.c_t, &M, deposit_nearest);
+        free(M.B);
     }
     bfield_free(&F);
-    return ORC_OK;
+    return bad ? ORC_ENOMEM : ORC_OK;
 }
 
 /* E_t(x) = A exp(i omega T), 0 where unreached; the phase is reduced mod 2 pi */

@@ -19,7 +19,8 @@ from . import _lib as _L
 from .phantoms import Grid
 
 __all__ = ["Context", "Problem", "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix",
-           "rt_status_counts", "rt_batch_run", "BatchInstance", "ToF", "tof", "PRECISIONS"]
+           "rt_status_counts", "rt_batch_run", "BatchInstance", "ToF", "tof", "PRECISIONS",
+           "BornMaps", "rtborn_maps", "rtborn_apply", "rtborn_adjoint", "Born", "born", "GEMM_MODES"]
 
 PRECISIONS = {"fp64": _L.RT_FP64, "fp32c": _L.RT_FP32_COMP}
 
@@ -282,3 +283,111 @@ def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, pr
     o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll, blocks_per_sm)
     _L.check(ctx.h, ctx.lib.rt_batch_run(ctx.h, len(instances), arr, C.byref(o), _stream(stream)))
     return instances
+
+
+# ---------------------------------------------------------------- ray-Born
+
+GEMM_MODES = {"fp32": _L.RTBORN_GEMM_FP32, "bf16x9": _L.RTBORN_GEMM_BF16X9}
+
+
+@dataclasses.dataclass
+class BornMaps:
+    """Per-transducer first-arrival maps (device float32 [n_tx, ny, nx]):
+    travel time T (us, +inf where no ray arrives) and amplitude A."""
+    grid: Grid
+    ring_radius: float
+    T: torch.Tensor
+    A: torch.Tensor
+
+    @property
+    def n_tx(self) -> int:
+        return int(self.T.shape[0])
+
+    def _grid_struct(self) -> _L.RtGrid:
+        return _L.RtGrid(self.grid.nx, self.grid.ny, self.grid.h, self.grid.x0, self.grid.y0)
+
+
+def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tensor] = None,
+                ctx: Optional[Context] = None, stream=None, out: Optional[BornMaps] = None) -> BornMaps:
+    """Travel-time and amplitude maps of every transducer from fans of
+    fan_rays rays traced with their paraxial rays (paper Sec. 3.5)."""
+    ctx = ctx or default_context(prob.c.device.index)
+    g = prob.grid
+    if out is None:
+        shape = (prob.n_tx, g.ny, g.nx)
+        out = BornMaps(g, prob.ring_radius, torch.empty(shape, dtype=torch.float32, device=prob.c.device),
+                       torch.empty(shape, dtype=torch.float32, device=prob.c.device))
+    o = _opts(ds, precision="fp32c")
+    ps = prob.struct(c)
+    _L.check(ctx.h, ctx.lib.rtborn_maps(ctx.h, C.byref(ps), C.byref(o), int(fan_rays), _ptr(out.T), _ptr(out.A),
+                                        _stream(stream)))
+    return out
+
+
+def _freqs(f_mhz):
+    f = [float(v) for v in f_mhz]
+    return len(f), (C.c_double * max(len(f), 1))(*f)
+
+
+def _check_maps(maps: BornMaps):
+    for t in (maps.T, maps.A):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("maps must be contiguous float32 CUDA tensors")
+        if t.shape != (maps.n_tx, maps.grid.ny, maps.grid.nx):
+            raise ValueError("maps have the wrong shape")
+
+
+def rtborn_apply(maps: BornMaps, f_mhz, dc: torch.Tensor, gemm: str = "bf16x9", ctx: Optional[Context] = None,
+                 stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Born data d[f, e, r] (complex64) of the perturbation dc (m/s, float32
+    [ny, nx]) at frequencies f_mhz."""
+    _check_maps(maps)
+    ctx = ctx or default_context(maps.T.device.index)
+    nf, fa = _freqs(f_mhz)
+    dc = dc.to(torch.float32).contiguous()
+    if dc.numel() != maps.grid.nx * maps.grid.ny or not dc.is_cuda:
+        raise ValueError("dc must be a CUDA tensor with one value per node")
+    if out is None:
+        out = torch.empty((nf, maps.n_tx, maps.n_tx), dtype=torch.complex64, device=maps.T.device)
+    g = maps._grid_struct()
+    _L.check(ctx.h, ctx.lib.rtborn_apply(ctx.h, C.byref(g), maps.ring_radius, maps.n_tx, _ptr(maps.T), _ptr(maps.A),
+                                         nf, fa, _ptr(dc), GEMM_MODES[gemm], _ptr(out), _stream(stream)))
+    return out
+
+
+def rtborn_adjoint(maps: BornMaps, f_mhz, d: torch.Tensor, gemm: str = "bf16x9", ctx: Optional[Context] = None,
+                   stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Adjoint of rtborn_apply: float32 [ny, nx] from complex64 d[f, e, r]."""
+    _check_maps(maps)
+    ctx = ctx or default_context(maps.T.device.index)
+    nf, fa = _freqs(f_mhz)
+    d = d.to(torch.complex64).contiguous()
+    if d.shape != (nf, maps.n_tx, maps.n_tx) or not d.is_cuda:
+        raise ValueError("d must be a CUDA complex tensor [n_freq, n_tx, n_tx]")
+    if out is None:
+        out = torch.empty((maps.grid.ny, maps.grid.nx), dtype=torch.float32, device=maps.T.device)
+    g = maps._grid_struct()
+    _L.check(ctx.h, ctx.lib.rtborn_adjoint(ctx.h, C.byref(g), maps.ring_radius, maps.n_tx, _ptr(maps.T),
+                                           _ptr(maps.A), nf, fa, _ptr(d), GEMM_MODES[gemm], _ptr(out),
+                                           _stream(stream)))
+    return out
+
+
+class Born(torch.autograd.Function):
+    """d = Born(dc): the linearised ray-Born map; backward = rtborn_adjoint
+    (for a real input and complex output, the vector-Jacobian product is
+    Re(F^H g))."""
+
+    @staticmethod
+    def forward(fctx, dc, maps: BornMaps, f_mhz, gemm: str):
+        fctx.maps, fctx.f, fctx.gemm = maps, list(f_mhz), gemm
+        return rtborn_apply(maps, f_mhz, dc.detach(), gemm=gemm)
+
+    @staticmethod
+    def backward(fctx, g):
+        return rtborn_adjoint(fctx.maps, fctx.f, g, gemm=fctx.gemm), None, None, None
+
+
+def born(dc: torch.Tensor, maps: BornMaps, f_mhz, gemm: str = "bf16x9") -> torch.Tensor:
+    """Differentiable Born data of dc (float32 [ny, nx])."""
+    return Born.apply(dc, maps, f_mhz, gemm)

@@ -26,7 +26,7 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        glob.glob(os.path.join(ROOT, "include", "*.h"))
+        glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:
@@ -34,6 +34,16 @@ def up_to_date() -> bool:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
+
+
+def _rpath():
+    """Run path to the toolkit's lib64 (cuBLAS), found from nvcc's location."""
+    import shutil
+    nv = shutil.which(NVCC)
+    if not nv:
+        return []
+    lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nv))), "lib64")
+    return ["-Xlinker", "-rpath", "-Xlinker", lib] if os.path.isdir(lib) else []
 
 
 def _compile(src: str) -> str:
@@ -55,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", *_rpath()]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

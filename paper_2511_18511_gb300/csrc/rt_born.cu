@@ -1,0 +1,693 @@
+// rt_born.cu — the ray-Born operator: first-arrival travel-time and amplitude
+// maps of every transducer from ray fans traced with their paraxial rays, and
+// the linearised Born map and its adjoint (arXiv:2511.18511 Sec. 3.5 and the
+// Appendix: Green's functions g = A exp(i omega T) whose phase follows the
+// eikonal and whose geometric amplitude follows the transport equation through
+// the ray Jacobian, obtained from a paraxial ray traced with each ray).
+//
+// Fan maps (rtborn_maps). One thread per fan ray, K rays per transducer at
+// evenly spaced angles over the inward half-plane (the two tangents excluded
+// by a margin ds/R). The march is the FP32-compensated one of the ToF path
+// (cell-local position with a two-sum residual, double-float direction, RK4 in
+// cell units) extended by the paraxial pair in cell units Q~ = Q/h:
+//     dQ~/ds~ = c P,   dP/ds~ = -(h^2 c_nn / c^2) Q~,   Q~(0) = 0, P(0) = 1/c_t,
+// with c_nn = n^T H n, H the Hessian of c from central second differences
+// interpolated bilinearly. The travel time is the trapezoid rule over the
+// interpolated slowness (Kahan-summed). Every sample point after the
+// transducer offers each node of the 3 x 3 block around its nearest node whose
+// foot on the ray lies within half a step (-ds/2 <= d.D < ds/2, D = node -
+// sample, a = d.D, b = n.D) the time extrapolated to second order in the
+// ray-centred frame from the foot of the node on the ray,
+//     T + s a + (M/2) b^2,   M = P/Q_f,   Q_f = Q + a c P   (|Q_f| >= h where M < 0),
+// paired with A = sqrt(c / (c_t max(|Q_f|, h))). Two passes over the fan: the
+// first keeps each node's earliest candidate (first arrival; a 32-bit
+// atomicMin on order-preserving bits of T), the second, among the candidates
+// within RTBORN_EPS_REL T + RTBORN_EPS_ABS_US of it, the one from the ray
+// passing closest to the node (a 64-bit atomicMin on |b| << 32 | bits of A):
+// rays next to a node arrive within far less than the rounding of T of one
+// another, so the earliest alone would choose among them by rounding.
+//
+// Born map (rtborn_apply), per frequency f (omega = 2 pi f rad/us):
+//     d[f][e][r] = omega^2 h^2 sum_{|x| < R} E_e(x) E_r(x) dc(x),  e != r,
+// E_t = A_t exp(i omega T_t) over the nodes inside the ring (a compact list).
+// E and W = omega^2 h^2 dc E are formed per frequency by one kernel (the phase
+// reduced as 2 pi frac(f T) with a compensated product, then sincospi), and
+// d = W^T E is a dense complex GEMM (cuBLAS, complex64, FP32 or the
+// BF16x9-emulated FP32 tensor-core mode). The adjoint (rtborn_adjoint) is
+//     dc~(x) = Re sum_f omega^2 h^2 sum_{e != r} conj(E_e E_r) d[f][e][r]
+//            = Re sum_f omega^2 h^2 sum_e E_e(x) V(x, e),  V = E conj(D_f)
+// (diagonal of D zeroed): one GEMM and one column reduction per frequency.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include "rt_internal.h"
+#include "rt_trace.cuh"
+
+namespace rt {
+namespace {
+
+constexpr double kPiB = 3.14159265358979323846;
+
+// Nodal fields for the Born march: (c, h dc/dx, h dc/dy, s) and
+// (h^2 d2c/dx2, h^2 d2c/dxdy, h^2 d2c/dy2, 0), mm/us units.
+struct __align__(32) BNode {
+    float4 a, b;
+};
+
+__global__ void k_born_pack(rt_grid g, const double* __restrict__ c_mps, BNode* __restrict__ out, int* bad) {
+    const int nx = g.nx, ny = g.ny;
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
+        const double v = c_mps[k];
+        if (!(v > 0.0) || !(v < 1e300)) atomicExch(bad, 1);
+        auto C = [&](int ii, int jj) { return 1e-3 * c_mps[(size_t)jj * nx + ii]; };
+        const double c = 1e-3 * v;
+        const double gx = (i == 0) ? C(1, j) - c : (i == nx - 1) ? c - C(nx - 2, j) : 0.5 * (C(i + 1, j) - C(i - 1, j));
+        const double gy = (j == 0) ? C(i, 1) - c : (j == ny - 1) ? c - C(i, ny - 2) : 0.5 * (C(i, j + 1) - C(i, j - 1));
+        double hxx = 0.0, hxy = 0.0, hyy = 0.0;
+        if (i > 0 && i < nx - 1 && j > 0 && j < ny - 1) {
+            hxx = C(i + 1, j) - 2.0 * c + C(i - 1, j);
+            hyy = C(i, j + 1) - 2.0 * c + C(i, j - 1);
+            hxy = 0.25 * (C(i + 1, j + 1) - C(i - 1, j + 1) - C(i + 1, j - 1) + C(i - 1, j - 1));
+        }
+        BNode o;
+        o.a = make_float4((float)c, (float)gx, (float)gy, (float)(1.0 / c));
+        o.b = make_float4((float)hxx, (float)hxy, (float)hyy, 0.0f);
+        out[k] = o;
+    }
+}
+
+// Register cache of one cell: the seven fields in bilinear coefficient form
+// f = a + tx bx + ty (by + tx bxy), built from the cell's four nodes.
+struct BornCell {
+    const BNode* __restrict__ F;
+    int nx, ny, pi, pj;
+    float c0, c1, c2, c3, x0, x1, x2, x3, y0, y1, y2, y3, s0, s1, s2, s3;
+    float p0, p1, p2, p3, q0, q1, q2, q3, r0, r1, r2, r3;   // hxx, hxy, hyy
+
+    __device__ __forceinline__ void load(int i, int j) {
+        pi = i;
+        pj = j;
+        i = min(max(i, 0), nx - 2);
+        j = min(max(j, 0), ny - 2);
+        const BNode* p = F + (size_t)j * nx + i;
+        const float4 a00 = p[0].a, b00 = p[0].b, a10 = p[1].a, b10 = p[1].b;
+        const float4 a01 = p[nx].a, b01 = p[nx].b, a11 = p[nx + 1].a, b11 = p[nx + 1].b;
+#define BC_(v0, v1, v2, v3, A00, A10, A01, A11) \
+    v0 = A00; v1 = A10 - A00; v2 = A01 - A00; v3 = (A11 - A10) - (A01 - A00);
+        BC_(c0, c1, c2, c3, a00.x, a10.x, a01.x, a11.x)
+        BC_(x0, x1, x2, x3, a00.y, a10.y, a01.y, a11.y)
+        BC_(y0, y1, y2, y3, a00.z, a10.z, a01.z, a11.z)
+        BC_(s0, s1, s2, s3, a00.w, a10.w, a01.w, a11.w)
+        BC_(p0, p1, p2, p3, b00.x, b10.x, b01.x, b11.x)
+        BC_(q0, q1, q2, q3, b00.y, b10.y, b01.y, b11.y)
+        BC_(r0, r1, r2, r3, b00.z, b10.z, b01.z, b11.z)
+#undef BC_
+    }
+
+    // Fields at fractions (u, v) of cell (ci, cj), as Cell::at of the ToF path.
+    __device__ __forceinline__ void at(int ci, int cj, float u, float v, float& c, float& gx, float& gy, float& hxx,
+                                       float& hxy, float& hyy, float& tx, float& ty) {
+        if (ci == pi && cj == pj && u >= 0.f && u < 1.f && v >= 0.f && v < 1.f) {
+            tx = u;
+            ty = v;
+        } else {
+            int i, j;
+            if (u >= -1.f && u < 2.f && v >= -1.f && v < 2.f) {
+                const bool ul = u < 0.f, uh = u >= 1.f, vl = v < 0.f, vh = v >= 1.f;
+                tx = ul ? u + 1.f : (uh ? u - 1.f : u);
+                ty = vl ? v + 1.f : (vh ? v - 1.f : v);
+                i = ci + (ul ? -1 : (uh ? 1 : 0));
+                j = cj + (vl ? -1 : (vh ? 1 : 0));
+            } else {
+                const float fu = floorf(u), fv = floorf(v);
+                i = ci + (int)fu;
+                j = cj + (int)fv;
+                tx = u - fu;
+                ty = v - fv;
+            }
+            if (i != pi || j != pj) load(i, j);
+        }
+        c = c0 + tx * c1 + ty * (c2 + tx * c3);
+        gx = x0 + tx * x1 + ty * (x2 + tx * x3);
+        gy = y0 + tx * y1 + ty * (y2 + tx * y3);
+        hxx = p0 + tx * p1 + ty * (p2 + tx * p3);
+        hxy = q0 + tx * q1 + ty * (q2 + tx * q3);
+        hyy = r0 + tx * r1 + ty * (r2 + tx * r3);
+    }
+    __device__ __forceinline__ float slow(float tx, float ty) const { return s0 + tx * s1 + ty * (s2 + tx * s3); }
+};
+
+// ray and paraxial right-hand sides at stage direction (ex, ey)
+__device__ __forceinline__ void born_rhs(float c, float gx, float gy, float hxx, float hxy, float hyy, float ex,
+                                         float ey, float Q, float P, float& kx, float& ky, float& kQ, float& kP) {
+    const float ic = rcp_approx(c);
+    const float gd = gx * ex + gy * ey;
+    kx = (gd * ex - gx) * ic;
+    ky = (gd * ey - gy) * ic;
+    const float cnn = ey * ey * hxx - 2.f * ex * ey * hxy + ex * ex * hyy;
+    kQ = c * P;
+    kP = -cnn * ic * ic * Q;
+}
+
+struct BornRay {
+    RayState<float> S;
+    float Q, P;
+};
+
+// One RK4 step of length H (cells). Stage 1 has already been evaluated at S
+// (c1.., passed in), since the deposit of S needs it.
+__device__ __forceinline__ void born_rk4(BornCell& C, const BornRay& B, float H, float c, float gx, float gy,
+                                         float hxx, float hxy, float hyy, BornRay& N) {
+    const float Hh = 0.5f * H, H6 = H / 6.f;
+    const float dx = B.S.d.hx(), dy = B.S.d.hy();
+    float tx, ty, k1x, k1y, k1Q, k1P, k2x, k2y, k2Q, k2P, k3x, k3y, k3Q, k3P, k4x, k4y, k4Q, k4P;
+    born_rhs(c, gx, gy, hxx, hxy, hyy, dx, dy, B.Q, B.P, k1x, k1y, k1Q, k1P);
+    float e2x = dx + Hh * k1x, e2y = dy + Hh * k1y, Q2 = B.Q + Hh * k1Q, P2 = B.P + Hh * k1P;
+    C.at(B.S.ci, B.S.cj, B.S.fx + Hh * dx, B.S.fy + Hh * dy, c, gx, gy, hxx, hxy, hyy, tx, ty);
+    born_rhs(c, gx, gy, hxx, hxy, hyy, e2x, e2y, Q2, P2, k2x, k2y, k2Q, k2P);
+    float e3x = dx + Hh * k2x, e3y = dy + Hh * k2y, Q3 = B.Q + Hh * k2Q, P3 = B.P + Hh * k2P;
+    C.at(B.S.ci, B.S.cj, B.S.fx + Hh * e2x, B.S.fy + Hh * e2y, c, gx, gy, hxx, hxy, hyy, tx, ty);
+    born_rhs(c, gx, gy, hxx, hxy, hyy, e3x, e3y, Q3, P3, k3x, k3y, k3Q, k3P);
+    float e4x = dx + H * k3x, e4y = dy + H * k3y, Q4 = B.Q + H * k3Q, P4 = B.P + H * k3P;
+    C.at(B.S.ci, B.S.cj, B.S.fx + H * e3x, B.S.fy + H * e3y, c, gx, gy, hxx, hxy, hyy, tx, ty);
+    born_rhs(c, gx, gy, hxx, hxy, hyy, e4x, e4y, Q4, P4, k4x, k4y, k4Q, k4P);
+    N.Q = B.Q + H6 * (k1Q + 2.f * (k2Q + k3Q) + k4Q);
+    N.P = B.P + H6 * (k1P + 2.f * (k2P + k3P) + k4P);
+    float nfx = B.S.fx, nfy = B.S.fy;
+    N.S.lx = B.S.lx;
+    N.S.ly = B.S.ly;
+    add_frac(nfx, N.S.lx, H6 * (dx + 2.f * (e2x + e3x) + e4x) + H * B.S.d.lx());
+    add_frac(nfy, N.S.ly, H6 * (dy + 2.f * (e2y + e3y) + e4y) + H * B.S.d.ly());
+    N.S.d = B.S.d;
+    N.S.d.add_normalize(H6 * (k1x + 2.f * (k2x + k3x) + k4x), H6 * (k1y + 2.f * (k2y + k3y) + k4y));
+    N.S.ci = B.S.ci;
+    N.S.cj = B.S.cj;
+    if (nfx >= 1.f) { N.S.ci += 1; nfx -= 1.f; } else if (nfx < 0.f) { N.S.ci -= 1; add_frac(nfx, N.S.lx, 1.f); }
+    if (nfy >= 1.f) { N.S.cj += 1; nfy -= 1.f; } else if (nfy < 0.f) { N.S.cj -= 1; add_frac(nfy, N.S.ly, 1.f); }
+    N.S.fx = nfx;
+    N.S.fy = nfy;
+}
+
+// order-preserving map of float bits to unsigned (negative values included)
+__device__ __forceinline__ unsigned f2ord(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+struct FanArgs {
+    int K;
+    float hf;                     // h, mm
+    float Hhalf;                  // ds / (2h), cells
+    float eps_rel, eps_abs;       // near-simultaneous window of the amplitude choice
+    unsigned* tfirst;             // [n_tx][ny*nx] order-preserving bits of the first arrival
+    unsigned long long* near;     // [n_tx][ny*nx] (|b| bits << 32) | A bits of the kept candidate
+    long long nn;
+    unsigned long long* steps;    // RK4 steps taken (summed over rays)
+};
+
+// Offer the nodes around sample B (time T, stage-1 c and s) their candidates.
+// PASS 0: first arrival (32-bit atomicMin on the ordered time). PASS 1: among
+// the candidates within eps of it, the ray passing closest (64-bit atomicMin on
+// |b|, then A).
+template <int PASS>
+__device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, unsigned* __restrict__ tfirst,
+                                             unsigned long long* __restrict__ near, const BornRay& B, float T,
+                                             float c, float s, float inv_ct_h) {
+    const float fx = B.S.fx, fy = B.S.fy;
+    const bool oi = fx >= 0.5f, oj = fy >= 0.5f;
+    const float D0x = oi ? 1.f - fx : -fx, D0y = oj ? 1.f - fy : -fy;
+    const float dx = B.S.d.hx(), dy = B.S.d.hy();
+    const float al0 = dx * D0x + dy * D0y;
+    const float ac0 = dx * D0y - dy * D0x;
+    const int ic = B.S.ci + (oi ? 1 : 0), jc = B.S.cj + (oj ? 1 : 0);
+    const float cP = c * B.P;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+            const float al = al0 + (float)a * dx + (float)b * dy;
+            if (al >= -A.Hhalf && al < A.Hhalf) {
+                const int ni = ic + a, nj = jc + b;
+                if (ni >= 0 && ni < G.nx && nj >= 0 && nj < G.ny) {
+                    const float ac = ac0 + (float)b * dx - (float)a * dy;
+                    // paraxial Q carried to the foot of the node (dQ~/ds~ = c P)
+                    const float Qf = B.Q + al * cP;
+                    const float aQ = fabsf(Qf);
+                    const float Qc = aQ >= 1.f ? aQ : 1.f;
+                    float M = B.P / Qf;
+                    if (!(M >= 0.f)) M = B.P / copysignf(Qc, Qf);
+                    const float cand = T + A.hf * (s * al + 0.5f * M * ac * ac);
+                    const size_t node = (size_t)nj * G.nx + ni;
+                    if (PASS == 0) {
+                        atomicMin(tfirst + node, f2ord(cand));
+                    } else {
+                        const float Tf = ord2f(__ldg(tfirst + node));
+                        if (cand <= Tf + (A.eps_rel * Tf + A.eps_abs)) {
+                            const float amp = sqrtf(c * inv_ct_h / Qc);
+                            const unsigned long long key =
+                                ((unsigned long long)__float_as_uint(fabsf(ac)) << 32) | __float_as_uint(amp);
+                            atomicMin(near + node, key);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int BLOCK, int PASS>
+__global__ void __launch_bounds__(BLOCK) k_born_fan(const Geom G, const FanArgs A, const BNode* __restrict__ field) {
+    const long long id = blockIdx.x * (long long)BLOCK + threadIdx.x;
+    if (id >= (long long)G.n_tx * A.K) return;
+    if (*G.bad_field) return;   // c <= 0 or NaN somewhere: every node stays unreached
+    const int t = (int)(id / A.K), k = (int)(id - (long long)t * A.K);
+    const double xe = G.tx[2 * t], ye = G.tx[2 * t + 1];
+    const double phi = atan2(ye, xe);
+    double margin = G.ds / G.R;
+    if (margin < 1e-9) margin = 1e-9;
+    const double a_min = phi + 0.5 * kPiB + margin;
+    const double step = ((phi + 1.5 * kPiB - margin) - a_min) / (A.K - 1);
+    const double theta = a_min + k * step;
+    unsigned* __restrict__ tfirst = A.tfirst + (size_t)t * A.nn;
+    unsigned long long* __restrict__ near = A.near + (size_t)t * A.nn;
+
+    BornRay B;
+    {
+        const double u = (xe - G.x0) / G.h, v = (ye - G.y0) / G.h;
+        const double fu = floor(u), fv = floor(v);
+        B.S.ci = (int)fu;
+        B.S.cj = (int)fv;
+        B.S.fx = (float)(u - fu);
+        B.S.fy = (float)(v - fv);
+        B.S.lx = (float)((u - fu) - (double)B.S.fx);
+        B.S.ly = (float)((v - fv) - (double)B.S.fy);
+        B.S.d.set(theta);
+    }
+    BornCell C;
+    C.F = field;
+    C.nx = G.nx;
+    C.ny = G.ny;
+    C.load(B.S.ci, B.S.cj);
+    const float H = G.Hf;
+    const float half_ds = 0.5f * G.dsf;
+    float c, gx, gy, hxx, hxy, hyy, tx, ty;
+    C.at(B.S.ci, B.S.cj, B.S.fx, B.S.fy, c, gx, gy, hxx, hxy, hyy, tx, ty);
+    const float c_t = c;
+    const float inv_ct_h = 1.f / (c_t * A.hf);
+    B.Q = 0.f;
+    B.P = 1.f / c_t;
+    float s_prev = C.slow(tx, ty);
+    float T = 0.f, Tc = 0.f;       // Kahan sum of the trapezoid increments
+    int safe = 0, nsteps = 0;
+    for (int m = 1; m <= G.max_steps_i; ++m) {
+        BornRay N;
+        born_rk4(C, B, H, c, gx, gy, hxx, hxy, hyy, N);
+        ++nsteps;
+        if (--safe < 0) {
+            const float ex = ring_excess(G, N.S);
+            if (ex >= 0.f) break;
+            const float Rc = G.Rcf;
+            const float r = sqrtf(Rc * Rc + ex);
+            safe = (int)((-ex / (Rc + r)) * 0.98f / H) - 1;
+        }
+        B = N;
+        C.at(B.S.ci, B.S.cj, B.S.fx, B.S.fy, c, gx, gy, hxx, hxy, hyy, tx, ty);
+        const float s = C.slow(tx, ty);
+        const float y = half_ds * (s_prev + s) - Tc;
+        const float tt = T + y;
+        Tc = (tt - T) - y;
+        T = tt;
+        s_prev = s;
+        born_deposit<PASS>(G, A, tfirst, near, B, T, c, s, inv_ct_h);
+    }
+    const unsigned mask = __activemask();
+    const unsigned tot = __reduce_add_sync(mask, (unsigned)nsteps);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(A.steps, (unsigned long long)tot);
+}
+
+__global__ void k_born_unpack(const unsigned* __restrict__ tfirst, const unsigned long long* __restrict__ near,
+                              long long n, float* __restrict__ T, float* __restrict__ A) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const unsigned tf = tfirst[k];
+        const unsigned long long key = near[k];
+        T[k] = tf == 0xffffffffu ? __uint_as_float(0x7f800000u) : ord2f(tf);
+        A[k] = (tf == 0xffffffffu || key == ~0ull) ? 0.f : __uint_as_float((unsigned)key);
+    }
+}
+
+// E[t][p] = A exp(i 2 pi frac(f T)) at inside node idx[p]; W = scale dc E.
+__global__ void k_born_efield(int n_in, const int* __restrict__ idx, long long nn, const float* __restrict__ Tm,
+                              const float* __restrict__ Am, float f_hi, float f_lo, float scale,
+                              const float* __restrict__ dc, float2* __restrict__ E, float2* __restrict__ W) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_in) return;
+    const int t = blockIdx.y;
+    const int k = idx[p];
+    const float Tv = Tm[(size_t)t * nn + k], Av = Am[(size_t)t * nn + k];
+    float2 e = make_float2(0.f, 0.f);
+    if (Tv < __uint_as_float(0x7f800000u)) {
+        // frac(f T) with f = f_hi + f_lo: the product's rounding error by FMA
+        const float pr = f_hi * Tv;
+        const float er = fmaf(f_hi, Tv, -pr);
+        const float fr = (pr - rintf(pr)) + (er + f_lo * Tv);
+        float sn, cs;
+        sincospif(2.f * fr, &sn, &cs);
+        e = make_float2(Av * cs, Av * sn);
+    }
+    const size_t o = (size_t)t * n_in + p;
+    E[o] = e;
+    if (W) {
+        const float w = scale * dc[k];
+        W[o] = make_float2(w * e.x, w * e.y);
+    }
+}
+
+__global__ void k_zero_diag(float2* d, int n_tx, int n_freq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tx * n_freq) return;
+    const int f = i / n_tx, e = i - f * n_tx;
+    d[((size_t)f * n_tx + e) * n_tx + e] = make_float2(0.f, 0.f);
+}
+
+// Dc[r + e n] = conj(d[e][r]), 0 on the diagonal
+__global__ void k_conj_nodiag(const float2* __restrict__ d, float2* __restrict__ Dc, int n_tx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tx * n_tx) return;
+    const int e = i / n_tx, r = i - e * n_tx;
+    const float2 v = d[i];
+    Dc[i] = (e == r) ? make_float2(0.f, 0.f) : make_float2(v.x, -v.y);
+}
+
+// acc[p] (+)= scale * Re sum_e E[e][p] V[e][p]
+__global__ void k_born_reduce(int n_in, int n_tx, const float2* __restrict__ E, const float2* __restrict__ V,
+                              float scale, double* __restrict__ acc, int first) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_in) return;
+    float s0 = 0.f, s1 = 0.f;
+    int e = 0;
+    for (; e + 1 < n_tx; e += 2) {
+        const float2 a = E[(size_t)e * n_in + p], b = V[(size_t)e * n_in + p];
+        const float2 a2 = E[(size_t)(e + 1) * n_in + p], b2 = V[(size_t)(e + 1) * n_in + p];
+        s0 = fmaf(a.x, b.x, fmaf(-a.y, b.y, s0));
+        s1 = fmaf(a2.x, b2.x, fmaf(-a2.y, b2.y, s1));
+    }
+    if (e < n_tx) {
+        const float2 a = E[(size_t)e * n_in + p], b = V[(size_t)e * n_in + p];
+        s0 = fmaf(a.x, b.x, fmaf(-a.y, b.y, s0));
+    }
+    const double v = (double)(scale * (s0 + s1));
+    acc[p] = first ? v : acc[p] + v;
+}
+
+__global__ void k_born_scatter(int n_in, const int* __restrict__ idx, const double* __restrict__ acc,
+                               float* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_in) out[idx[p]] = (float)acc[p];
+}
+
+}  // namespace
+
+void destroy_blas(void* handle) { cublasDestroy((cublasHandle_t)handle); }
+
+}  // namespace rt
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+int bfail(rt_ctx* ctx, int code, const std::string& msg) { return rt::set_error(ctx, code, msg); }
+
+int bcuda(rt_ctx* ctx, cudaError_t e, const char* where) {
+    return bfail(ctx, RT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Grows one workspace buffer (never during stream capture).
+int grow(rt_ctx* ctx, void** p, size_t* have, size_t need, cudaStream_t s, const char* what) {
+    if (*have >= need) return RT_OK;
+    if (rt::stream_capturing(s)) return bfail(ctx, RT_EINVAL, std::string(what) + " workspace too small during capture");
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e != cudaSuccess) return bfail(ctx, RT_ENOMEM, std::string(what) + " workspace: " + cudaGetErrorString(e));
+    *have = need;
+    return RT_OK;
+}
+
+int check_grid(rt_ctx* ctx, const rt_grid* g, double R) {
+    if (!g) return bfail(ctx, RT_EINVAL, "grid pointer is NULL");
+    if (g->nx < 3 || g->ny < 3 || (int64_t)g->nx * g->ny > (int64_t)INT32_MAX / 2)
+        return bfail(ctx, RT_EINVAL, "grid size invalid");
+    if (!(g->h_mm > 0) || !std::isfinite(g->h_mm) || !std::isfinite(g->x0_mm) || !std::isfinite(g->y0_mm))
+        return bfail(ctx, RT_EINVAL, "grid spacing/origin invalid");
+    if (!(R > 0) || !std::isfinite(R)) return bfail(ctx, RT_EINVAL, "ring radius must be > 0");
+    return RT_OK;
+}
+
+// Compact list of the nodes strictly inside the ring (row-major order),
+// cached on the context per (grid, radius).
+int inside_list(rt_ctx* ctx, const rt_grid& g, double R, cudaStream_t s, int* n_in) {
+    const bool same = ctx->born_idx && ctx->born_idx_key[0] == g.nx && ctx->born_idx_key[1] == g.ny &&
+                      ctx->born_idx_geo[0] == g.h_mm && ctx->born_idx_geo[1] == g.x0_mm &&
+                      ctx->born_idx_geo[2] == g.y0_mm && ctx->born_idx_geo[3] == R;
+    if (same) {
+        *n_in = ctx->born_n_in;
+        return RT_OK;
+    }
+    if (rt::stream_capturing(s)) return bfail(ctx, RT_EINVAL, "inside-node list must be built outside capture");
+    std::vector<int> idx;
+    for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+            const double x = g.x0_mm + i * g.h_mm, y = g.y0_mm + j * g.h_mm;
+            if (x * x + y * y < R * R) idx.push_back(j * g.nx + i);
+        }
+    if (idx.empty()) return bfail(ctx, RT_EINVAL, "no grid node inside the ring");
+    size_t have = ctx->born_idx_bytes;
+    int rc = grow(ctx, (void**)&ctx->born_idx, &have, idx.size() * sizeof(int), s, "inside-node");
+    if (rc) return rc;
+    ctx->born_idx_bytes = have;
+    cudaError_t e = cudaMemcpyAsync(ctx->born_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "inside-node upload");
+    ctx->born_idx_key[0] = g.nx;
+    ctx->born_idx_key[1] = g.ny;
+    ctx->born_idx_geo[0] = g.h_mm;
+    ctx->born_idx_geo[1] = g.x0_mm;
+    ctx->born_idx_geo[2] = g.y0_mm;
+    ctx->born_idx_geo[3] = R;
+    ctx->born_n_in = (int)idx.size();
+    *n_in = ctx->born_n_in;
+    return RT_OK;
+}
+
+int blas(rt_ctx* ctx, cudaStream_t s, cublasHandle_t* h) {
+    if (!ctx->cublas) {
+        cublasHandle_t hh = nullptr;
+        if (cublasCreate(&hh) != CUBLAS_STATUS_SUCCESS) return bfail(ctx, RT_ECUDA, "cublasCreate failed");
+        ctx->cublas = hh;
+    }
+    *h = (cublasHandle_t)ctx->cublas;
+    if (cublasSetStream(*h, s) != CUBLAS_STATUS_SUCCESS) return bfail(ctx, RT_ECUDA, "cublasSetStream failed");
+    return RT_OK;
+}
+
+int gemm(rt_ctx* ctx, cublasHandle_t h, int mode, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+         const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc) {
+    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+    cublasComputeType_t ct = CUBLAS_COMPUTE_32F_PEDANTIC;
+    if (mode == RTBORN_GEMM_BF16X9) {
+        ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+        cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER);
+    }
+    const cublasStatus_t st = cublasGemmEx(h, ta, tb, m, n, k, &one, A, CUDA_C_32F, lda, B, CUDA_C_32F, ldb, &zero, C,
+                                           CUDA_C_32F, ldc, ct, CUBLAS_GEMM_DEFAULT);
+    if (st != CUBLAS_STATUS_SUCCESS) return bfail(ctx, RT_ECUDA, "cublasGemmEx failed (status " + std::to_string((int)st) + ")");
+    return RT_OK;
+}
+
+int check_born_args(rt_ctx* ctx, const rt_grid* grid, double R, int32_t n_tx, const float* T, const float* A,
+                    int32_t n_freq, const double* f_mhz, int32_t mode) {
+    int rc = check_grid(ctx, grid, R);
+    if (rc) return rc;
+    if (n_tx < 2 || n_tx > 65535) return bfail(ctx, RT_EINVAL, "n_tx must be in [2, 65535]");
+    if (!T || !A) return bfail(ctx, RT_EINVAL, "T and A maps are required");
+    if (n_freq < 0 || (n_freq > 0 && !f_mhz)) return bfail(ctx, RT_EINVAL, "frequencies invalid");
+    for (int f = 0; f < n_freq; ++f)
+        if (!std::isfinite(f_mhz[f])) return bfail(ctx, RT_EINVAL, "frequency not finite");
+    if (mode != RTBORN_GEMM_FP32 && mode != RTBORN_GEMM_BF16X9) return bfail(ctx, RT_EINVAL, "unknown GEMM mode");
+    return RT_OK;
+}
+
+// per-frequency workspace: E and W (or V) [n_tx][n_in] complex64
+int born_ws(rt_ctx* ctx, int n_tx, int n_in, cudaStream_t s) {
+    const size_t eb = sizeof(float2) * (size_t)n_tx * (size_t)n_in;
+    int rc = grow(ctx, &ctx->born_E, &ctx->born_E_bytes, eb, s, "Born E");
+    if (!rc) rc = grow(ctx, &ctx->born_W, &ctx->born_W_bytes, eb, s, "Born W");
+    if (!rc) rc = grow(ctx, &ctx->born_aux, &ctx->born_aux_bytes,
+                       std::max(sizeof(float2) * (size_t)n_tx * n_tx, sizeof(double) * (size_t)n_in), s, "Born aux");
+    if (!rc) rc = grow(ctx, &ctx->born_acc, &ctx->born_acc_bytes, sizeof(double) * (size_t)n_in, s, "Born acc");
+    return rc;
+}
+
+void split_freq(double f, float* hi, float* lo) {
+    *hi = (float)f;
+    *lo = (float)(f - (double)*hi);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int32_t fan_rays, float* T_out,
+                float* A_out, void* stream) {
+    if (!ctx) return RT_EINVAL;
+    ctx->err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!opt) return bfail(ctx, RT_EINVAL, "options pointer is NULL");
+    if (opt->precision != RT_FP32_COMP) return bfail(ctx, RT_EINVAL, "fan maps are computed in RT_FP32_COMP only");
+    if (!(opt->ds_mm > 0) || !std::isfinite(opt->ds_mm)) return bfail(ctx, RT_EINVAL, "ds_mm must be > 0");
+    if (fan_rays < 2 || fan_rays > (1 << 20)) return bfail(ctx, RT_EINVAL, "fan_rays must be in [2, 2^20]");
+    if (!T_out || !A_out) return bfail(ctx, RT_EINVAL, "T and A outputs are required");
+    if (opt->ds_mm > (prob ? prob->grid.h_mm : 0.0)) return bfail(ctx, RT_EINVAL, "ds_mm must not exceed the grid spacing");
+    rt::Geom G;
+    int rc = rt::make_geom(ctx, prob, opt, &G);
+    if (rc) return rc;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return bcuda(ctx, e, "cudaSetDevice");
+    const long long nn = (long long)G.nx * G.ny;
+    rc = grow(ctx, &ctx->born_field, &ctx->born_field_bytes, sizeof(rt::BNode) * (size_t)nn, s, "Born field");
+    if (rc) return rc;
+    const size_t n_ent = (size_t)nn * prob->n_tx;
+    rc = grow(ctx, &ctx->born_keys, &ctx->born_keys_bytes, (sizeof(unsigned long long) + sizeof(unsigned)) * n_ent, s,
+              "fan-map keys");
+    if (rc) return rc;
+    unsigned long long* near = (unsigned long long*)ctx->born_keys;
+    unsigned* tfirst = (unsigned*)(near + n_ent);
+    e = cudaMemsetAsync(ctx->dflag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "flag reset");
+    G.bad_field = ctx->dflag;
+    rt::k_born_pack<<<std::min<long long>((nn + 255) / 256, 152 * 32), 256, 0, s>>>(
+        prob->grid, prob->c_mps, (rt::BNode*)ctx->born_field, ctx->dflag);
+    e = cudaMemsetAsync(ctx->born_keys, 0xff, (sizeof(unsigned long long) + sizeof(unsigned)) * n_ent, s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "key reset");
+    rt::FanArgs A;
+    A.K = fan_rays;
+    A.hf = (float)G.h;
+    A.Hhalf = (float)(0.5 * G.ds / G.h);
+    A.eps_rel = RTBORN_EPS_REL;
+    A.eps_abs = RTBORN_EPS_ABS_US;
+    A.tfirst = tfirst;
+    A.near = near;
+    A.nn = nn;
+    A.steps = ctx->counters + 7;
+    e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "counter reset");
+    const long long rays = (long long)prob->n_tx * fan_rays;
+    constexpr int B = 128;
+    const unsigned blocks = (unsigned)((rays + B - 1) / B);
+    rt::k_born_fan<B, 0><<<blocks, B, 0, s>>>(G, A, (const rt::BNode*)ctx->born_field);
+    rt::k_born_fan<B, 1><<<blocks, B, 0, s>>>(G, A, (const rt::BNode*)ctx->born_field);
+    rt::k_born_unpack<<<(unsigned)std::min<long long>(((long long)n_ent + 255) / 256, 152 * 64), 256, 0, s>>>(
+        tfirst, near, (long long)n_ent, T_out, A_out);
+    e = cudaGetLastError();
+    ctx->last_stream = s;
+    return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "fan-map kernels");
+}
+
+int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                 const float* A, int32_t n_freq, const double* f_mhz, const float* dc_mps, int32_t gemm_mode,
+                 float* d_out, void* stream) {
+    if (!ctx) return RT_EINVAL;
+    ctx->err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = check_born_args(ctx, grid, ring_radius_mm, n_tx, T, A, n_freq, f_mhz, gemm_mode);
+    if (rc) return rc;
+    if (!dc_mps || (!d_out && n_freq > 0)) return bfail(ctx, RT_EINVAL, "dc_mps and d_out are required");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return bcuda(ctx, e, "cudaSetDevice");
+    if (n_freq == 0) return RT_OK;
+    int n_in = 0;
+    rc = inside_list(ctx, *grid, ring_radius_mm, s, &n_in);
+    if (!rc) rc = born_ws(ctx, n_tx, n_in, s);
+    cublasHandle_t h = nullptr;
+    if (!rc) rc = blas(ctx, s, &h);
+    if (rc) return rc;
+    const long long nn = (long long)grid->nx * grid->ny;
+    float2* E = (float2*)ctx->born_E;
+    float2* W = (float2*)ctx->born_W;
+    float2* d = (float2*)d_out;
+    const dim3 eg((n_in + 255) / 256, n_tx);
+    for (int f = 0; f < n_freq; ++f) {
+        float fh, fl;
+        split_freq(f_mhz[f], &fh, &fl);
+        const double om = 2.0 * rt::kPiB * f_mhz[f];
+        const float scale = (float)(om * om * grid->h_mm * grid->h_mm);
+        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, fh, fl, scale, dc_mps, E, W);
+        // d(r, e) = sum_p W(p, r) E(p, e): column-major D = W^T E, stored at r + e n = d[e][r]
+        rc = gemm(ctx, h, gemm_mode, CUBLAS_OP_T, CUBLAS_OP_N, n_tx, n_tx, n_in, W, n_in, E, n_in,
+                  d + (size_t)f * n_tx * n_tx, n_tx);
+        if (rc) return rc;
+    }
+    rt::k_zero_diag<<<(n_tx * n_freq + 255) / 256, 256, 0, s>>>(d, n_tx, n_freq);
+    e = cudaGetLastError();
+    ctx->last_stream = s;
+    return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "Born apply kernels");
+}
+
+int rtborn_adjoint(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                   const float* A, int32_t n_freq, const double* f_mhz, const float* d_in, int32_t gemm_mode,
+                   float* dc_out, void* stream) {
+    if (!ctx) return RT_EINVAL;
+    ctx->err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = check_born_args(ctx, grid, ring_radius_mm, n_tx, T, A, n_freq, f_mhz, gemm_mode);
+    if (rc) return rc;
+    if (!dc_out || (!d_in && n_freq > 0)) return bfail(ctx, RT_EINVAL, "d_in and dc_out are required");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return bcuda(ctx, e, "cudaSetDevice");
+    const long long nn = (long long)grid->nx * grid->ny;
+    e = cudaMemsetAsync(dc_out, 0, sizeof(float) * (size_t)nn, s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "dc reset");
+    if (n_freq == 0) return RT_OK;
+    int n_in = 0;
+    rc = inside_list(ctx, *grid, ring_radius_mm, s, &n_in);
+    if (!rc) rc = born_ws(ctx, n_tx, n_in, s);
+    cublasHandle_t h = nullptr;
+    if (!rc) rc = blas(ctx, s, &h);
+    if (rc) return rc;
+    float2* E = (float2*)ctx->born_E;
+    float2* V = (float2*)ctx->born_W;
+    float2* Dc = (float2*)ctx->born_aux;
+    double* acc = (double*)ctx->born_acc;
+    const float2* d = (const float2*)d_in;
+    const dim3 eg((n_in + 255) / 256, n_tx);
+    for (int f = 0; f < n_freq; ++f) {
+        float fh, fl;
+        split_freq(f_mhz[f], &fh, &fl);
+        const double om = 2.0 * rt::kPiB * f_mhz[f];
+        const float scale = (float)(om * om * grid->h_mm * grid->h_mm);
+        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, fh, fl, 0.f, nullptr, E, nullptr);
+        rt::k_conj_nodiag<<<(n_tx * n_tx + 255) / 256, 256, 0, s>>>(d + (size_t)f * n_tx * n_tx, Dc, n_tx);
+        // V(p, e) = sum_r E(p, r) Dc(r, e)
+        rc = gemm(ctx, h, gemm_mode, CUBLAS_OP_N, CUBLAS_OP_N, n_in, n_tx, n_tx, E, n_in, Dc, n_tx, V, n_in);
+        if (rc) return rc;
+        rt::k_born_reduce<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, n_tx, E, V, scale, acc, f == 0);
+    }
+    rt::k_born_scatter<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, ctx->born_idx, acc, dc_out);
+    e = cudaGetLastError();
+    ctx->last_stream = s;
+    return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "Born adjoint kernels");
+}
+
+}  // extern "C"

@@ -28,6 +28,26 @@ struct rt_ctx {
     void* scan_tmp = nullptr;       // prefix-sum workspace (path matrix)
     size_t scan_bytes = 0;
     cudaStream_t last_stream = nullptr;
+    // ray-Born workspace (rtborn_*): packed field with Hessian, fan-map keys,
+    // inside-ring node list, per-frequency E / W(V) and small buffers, cuBLAS
+    void* born_field = nullptr;
+    size_t born_field_bytes = 0;
+    void* born_keys = nullptr;
+    size_t born_keys_bytes = 0;
+    int* born_idx = nullptr;
+    size_t born_idx_bytes = 0;
+    int born_idx_key[2] = {0, 0};
+    double born_idx_geo[4] = {0, 0, 0, 0};
+    int born_n_in = 0;
+    void* born_E = nullptr;
+    size_t born_E_bytes = 0;
+    void* born_W = nullptr;
+    size_t born_W_bytes = 0;
+    void* born_aux = nullptr;
+    size_t born_aux_bytes = 0;
+    void* born_acc = nullptr;
+    size_t born_acc_bytes = 0;
+    void* cublas = nullptr;         // cublasHandle_t, created on first Born call
 };
 
 namespace rt {
@@ -59,5 +79,8 @@ cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double
 cudaError_t launch_scan(int64_t* row_ptr, int n, void* tmp, size_t* tmp_bytes, cudaStream_t s);
 
 size_t node_bytes(int prec);
+
+// Releases the context's cuBLAS handle (rt_born.cu).
+void destroy_blas(void* handle);
 
 }  // namespace rt

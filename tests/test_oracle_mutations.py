@@ -68,13 +68,16 @@ BORN_MUTANTS = {
     "born_P0_is_c": ("double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, 1.0 / c_t}",
                      "double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, c_t}"),
     "born_Q_missing_c": ("k[4] = f[F_C] * st[5];", "k[4] = st[5];"),
-    "born_amplitude_no_sqrt": ("const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(p->Q, h))));",
-                               "const double A = p->c / (M->c_t * fabs(clamp_q(p->Q, h)));"),
-    "born_first_order_only": ("const double cand = p->T + p->s * along + 0.5 * curv * across * across;",
-                              "const double cand = p->T + p->s * along;"),
+    "born_amplitude_no_sqrt": ("const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(Qf, h))));",
+                               "const double A = p->c / (M->c_t * fabs(clamp_q(Qf, h)));"),
+    "born_first_order_only": ("p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A);",
+                              "p->T + p->s * along, fabs(across), A);"),
+    "born_curvature_at_sample": ("const double Qf = p->Q + along * p->c * p->P;", "const double Qf = p->Q;"),
+    "born_amplitude_farthest_ray": ("if (b < M->B[k] || (b == M->B[k] && A < M->A[k])) {",
+                                    "if (b > M->B[k] || M->B[k] == INFINITY) {"),
     "born_nearest_node_only": ("for (int i = ic - 1; i <= ic + 1; ++i) {", "for (int i = ic; i <= ic; ++i) {"),
-    "born_latest_arrival": ("if (cand < M->T[k] || (cand == M->T[k] && A < M->A[k])) {",
-                            "if (!(cand <= M->T[k]) || M->T[k] == INFINITY) {"),
+    "born_latest_arrival": ("if (cand < M->T[k]) M->T[k] = cand;",
+                            "if (!(cand <= M->T[k]) || M->T[k] == INFINITY) M->T[k] = cand;"),
     "born_T_uses_c": ("const double T = p.T + ds * 0.5 * (p.s + f[F_S]);",
                       "const double T = p.T + ds * 0.5 * (p.c + f[F_C]);"),
     "born_apply_conj": ("sim += (ar * bi + ai * br) * dc[k];", "sim += (ar * bi - ai * br) * dc[k];"),
