@@ -312,8 +312,23 @@ def run_born(args):
 
 
 def run_profile_case(args):
-    """One rt_link on a subset of pairs of the full-size workload (ncu captures)."""
+    """One rt_link on a subset of pairs of the full-size workload (ncu captures);
+    with --workload born, rtborn_maps on the first N_EMIT transducers."""
     import torch
+    if args.workload == "born":
+        import paper_2511_18511_gb300 as rt
+        from paper_2511_18511_gb300 import phantoms as P
+        w = P.cfg_born()
+        n = args.profile
+        prob = rt.Problem.create(w.grid, w.c, w.tx[:n], w.ring_radius)
+        maps = None
+        for _ in range(2):
+            maps = rt.rtborn_maps(prob, w.ds, w.fan_rays, out=maps)
+        torch.cuda.synchronize()
+        _, counts = rt.rt_status_counts()
+        print(json.dumps({"profile_case": w.name, "transducers": n, "fan_rays": w.fan_rays,
+                          "rk4_steps_both_passes": counts[7]}))
+        return
     import paper_2511_18511_gb300 as rt
     from paper_2511_18511_gb300 import phantoms as P
     w = workload(0)

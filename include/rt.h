@@ -257,9 +257,9 @@ int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* opt, const 
  * (reciprocity). Absorption is not modelled (A_abs = 1).
  */
 
-/* Window of near-simultaneous arrivals for the amplitude choice of rtborn_maps. */
-#define RTBORN_EPS_REL 1e-5f
-#define RTBORN_EPS_ABS_US 1e-5f
+/* Penalty (us) of the squared distance to the ray, in grid steps, in the
+ * amplitude choice of rtborn_maps. */
+#define RTBORN_ETA_US 1e-2f
 
 /* GEMM arithmetic of rtborn_apply / rtborn_adjoint (complex64 in and out). */
 enum rtborn_gemm {
@@ -282,18 +282,21 @@ enum rtborn_gemm {
  * D = node - point, b = n.D) the second-order ray-centred extrapolation from
  * that foot, T + s a + (P/Q_f)/2 b^2 with Q_f = Q + a c P (|Q_f| clamped to
  * >= h where P/Q_f < 0), and A from Q_f. A node's time is its earliest
- * candidate (first arrival); its amplitude is that of the candidate from the
- * ray passing closest to the node (smallest |b|, then the smaller A) among
- * those within RTBORN_EPS_REL * T + RTBORN_EPS_ABS_US of the first arrival.
- * The fan is traced twice (once per choice).
+ * candidate (first arrival); its amplitude is that of the candidate of least
+ * T + RTBORN_ETA_US (b/h)^2 (then the smaller A), i.e. of the ray passing
+ * closest to the node; as the first-arrival branch passes within h/2 of every
+ * node it reaches, another branch supplies A only if it arrives within
+ * RTBORN_ETA_US / 4 of the first.
  *   prob      grid, c_mps, n_tx, tx_xy_mm, ring_radius_mm (pairs ignored).
- *   opt       precision must be RT_FP32_COMP; ds_mm in (0, h]; others ignored.
+ *   opt       precision must be RT_FP32_COMP; ds_mm in (0, h]; blocks_per_sm
+ *             picks the fan kernel variant (resident 128-thread blocks per SM
+ *             it is compiled for): 0 (= 6), 4, 5, 6 or 8; others ignored.
  *   fan_rays  rays per fan in [2, 2^20]; about 4 pi R / h covers the far side
  *             of the ring at one ray per half grid step.
  *   T_out     [n_tx][ny*nx] float out, us; +inf where no ray arrives.
  *   A_out     [n_tx][ny*nx] float out, amplitude (mm^-1/2); 0 where none.
  * Workspace: 12 bytes per map entry (n_tx * nx * ny) plus 32 bytes per node.
- * rt_status_counts afterwards reports counts[7] = RK4 steps of both passes
+ * rt_status_counts afterwards reports counts[7] = RK4 steps of the fans
  * (counts[0..6] = 0).
  * A sound speed <= 0 or NaN anywhere leaves every entry unreached.
  */

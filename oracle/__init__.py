@@ -85,7 +85,7 @@ def load(path: str):
     L.orc_fan_ray.argtypes = [G, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                               C.c_int64, _dp, _lp]
     L.orc_fan_maps.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_double, C.c_int32, C.c_double,
-                               C.c_double, _dp, _dp, C.c_int32]
+                               _dp, _dp, C.c_int32]
     L.orc_born_apply.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, C.c_int32, _dp, _dp, C.c_int32,
                                  _ip, _dp, C.c_int32]
     L.orc_born_adjoint.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, C.c_int32, _dp, _dp, _dp,
@@ -299,21 +299,20 @@ def fan_ray(grid, c_mps, R, xe, theta, ds):
     return {k: rec[:, q].copy() for q, k in enumerate(("x", "y", "dx", "dy", "T", "Q", "P", "c", "s"))}
 
 
-EPS_REL, EPS_ABS = 1e-5, 1e-5   # near-simultaneous window of the amplitude choice (relative, us)
+ETA = 1e-2   # us: penalty of the squared distance (in cells) to the ray in the amplitude choice
 
 
-def fan_maps(grid, c_mps, tx, R, ds, K, eps_rel=EPS_REL, eps_abs=EPS_ABS, nthreads=0):
+def fan_maps(grid, c_mps, tx, R, ds, K, eta=ETA, nthreads=0):
     """First-arrival maps (T us, A) of every transducer -> two [n_tx, ny, nx]
-    arrays (T = inf, A = 0 where no fan ray reaches); A from the closest ray
-    among the candidates within eps_rel T + eps_abs of the first arrival."""
+    arrays (T = inf, A = 0 where no fan ray reaches); A from the candidate of
+    least T + eta (b/h)^2, b its distance to the ray."""
     c = _f64(c_mps)
     tx = _f64(tx).reshape(-1, 2)
     n_tx = tx.shape[0]
     T = np.empty((n_tx, grid.ny, grid.nx))
     A = np.empty((n_tx, grid.ny, grid.nx))
     g = _grid(grid)
-    _check(lib().orc_fan_maps(C.byref(g), _d(c), n_tx, _d(tx), R, ds, K, eps_rel, eps_abs, _d(T), _d(A), nthreads),
-           "fan_maps")
+    _check(lib().orc_fan_maps(C.byref(g), _d(c), n_tx, _d(tx), R, ds, K, eta, _d(T), _d(A), nthreads), "fan_maps")
     return T, A
 
 

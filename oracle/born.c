@@ -38,12 +38,16 @@
  *      (for M < 0, a converging front, |Q_f| is clamped to >= h so that a focus
  *      cannot send the time to -inf), with the amplitude A from Q_f. A node's
  *      travel time is its earliest candidate (first arrival). Its amplitude is
- *      that of the candidate, among those within eps_rel T + eps_abs of the
- *      first arrival, from the ray passing closest to the node (smallest |b|,
- *      ties to the smaller A): rays near a node arrive within far less than
- *      any rounding of T of one another, so the earliest alone would pick
- *      among them by rounding, while their amplitudes differ by the spreading
- *      across the fan. Unreached nodes keep T = +inf, A = 0; *   B6 Born map, per frequency f (MHz; omega = 2 pi f rad/us):
+ *      that of the candidate of least T + eta (b/h)^2 (ties to the smaller A):
+ *      rays next to a node arrive within far less than any rounding of T of
+ *      one another, so the earliest alone would pick among them by rounding,
+ *      while their amplitudes differ by the spreading across the fan; the
+ *      penalty eta (b/h)^2 (eta = 1e-2 us) takes the ray passing closest to
+ *      the node; since the first-arrival branch passes within half a ray
+ *      spacing (< h/2) of every node it reaches, another branch can supply A
+ *      only if it arrives less than eta/4 after the first (a phase of 0.02 rad
+ *      at 1.5 MHz). Unreached nodes keep T = +inf, A = 0;
+ *   B6 Born map, per frequency f (MHz; omega = 2 pi f rad/us):
  *      d[f][e][r] = omega^2 h^2 sum_x E_e(x) E_r(x) dc(x) for e != r, 0 for
  *      e == r, E_t = A_t exp(i omega T_t) (0 where unreached), x over the nodes
  *      strictly inside the ring (dc in m/s as given);
@@ -190,8 +194,8 @@ typedef struct {
     double *T, *A;    /* map mode: [ny*nx] of one transducer */
     double* rec;      /* record mode: 9 values per sample */
     int64_t cap, n;
-    double* B;                  /* map mode: |b| of the kept candidate */
-    double eps_rel, eps_abs;    /* map mode: near-simultaneous window */
+    double* S;                  /* map mode: score of the candidate whose A is kept */
+    double eta;                 /* map mode: penalty of the distance to the ray */
 } MapCtx;
 
 static double clamp_q(double q, double h) {
@@ -224,26 +228,19 @@ static void candidates(MapCtx* M, const BSample* p, offer_fn offer) {
     }
 }
 
-/* pass 1: the first arrival, the earliest candidate */
-static void keep_first(MapCtx* M, size_t k, double cand, double b, double A) {
-    (void)b;
-    (void)A;
+/* the first arrival (earliest candidate) for T; for A the candidate of least
+ * T + eta (b/h)^2, ties to the smaller amplitude */
+static void keep(MapCtx* M, size_t k, double cand, double b, double A) {
     if (cand < M->T[k]) M->T[k] = cand;
-}
-
-/* pass 2: among the candidates within eps of the first arrival, the one from
- * the ray passing closest to the node (ties to the smaller amplitude) */
-static void keep_nearest(MapCtx* M, size_t k, double cand, double b, double A) {
-    const double Tf = M->T[k];
-    if (!(cand <= Tf + M->eps_rel * Tf + M->eps_abs)) return;
-    if (b < M->B[k] || (b == M->B[k] && A < M->A[k])) {
-        M->B[k] = b;
+    const double q = b / M->F->h;
+    const double score = cand + M->eta * q * q;
+    if (score < M->S[k] || (score == M->S[k] && A < M->A[k])) {
+        M->S[k] = score;
         M->A[k] = A;
     }
 }
 
-static void deposit_first(void* vctx, const BSample* p) { candidates((MapCtx*)vctx, p, keep_first); }
-static void deposit_nearest(void* vctx, const BSample* p) { candidates((MapCtx*)vctx, p, keep_nearest); }
+static void deposit(void* vctx, const BSample* p) { candidates((MapCtx*)vctx, p, keep); }
 
 static void record(void* vctx, const BSample* p) {
     MapCtx* M = (MapCtx*)vctx;
@@ -302,9 +299,8 @@ int orc_fan_angles(double xe, double ye, double R, double ds, int32_t K, double*
 }
 
 int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx, double R,
-                 double ds, int32_t K, double eps_rel, double eps_abs, double* T, double* A, int32_t nthreads) {
-    if (!g || !tx || n_tx < 1 || K < 2 || !T || !A || !(ds > 0) || !(R > 0) || !(eps_rel >= 0) || !(eps_abs >= 0))
-        return ORC_EINVAL;
+                 double ds, int32_t K, double eta, double* T, double* A, int32_t nthreads) {
+    if (!g || !tx || n_tx < 1 || K < 2 || !T || !A || !(ds > 0) || !(R > 0) || !(eta >= 0)) return ORC_EINVAL;
     BField F;
     int rc = bfield_make(&F, g, c_mps);
     if (rc) return rc;
@@ -316,19 +312,17 @@ int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const dou
         M.F = &F;
         M.T = T + (size_t)t * nn;
         M.A = A + (size_t)t * nn;
-        M.B = malloc(nn * sizeof(double));
-        if (!M.B) { bad = 1; continue; }
-        M.eps_rel = eps_rel;
-        M.eps_abs = eps_abs;
-        for (size_t k = 0; k < nn; ++k) { M.T[k] = INFINITY; M.A[k] = 0.0; M.B[k] = INFINITY; }
+        M.S = malloc(nn * sizeof(double));
+        if (!M.S) { bad = 1; continue; }
+        M.eta = eta;
+        for (size_t k = 0; k < nn; ++k) { M.T[k] = INFINITY; M.A[k] = 0.0; M.S[k] = INFINITY; }
         const double xe = tx[2 * t], ye = tx[2 * t + 1];
         M.c_t = c_at(&F, xe, ye);
         M.ds = ds;
         double a_min, step;
         fan_angles(xe, ye, R, ds, K, &a_min, &step);
-        for (int k = 0; k < K; ++k) fan_ray(&F, R, xe, ye, a_min + k * step, ds, M.c_t, &M, deposit_first);
-        for (int k = 0; k < K; ++k) fan_ray(&F, R, xe, ye, a_min + k * step, ds, M.c_t, &M, deposit_nearest);
-        free(M.B);
+        for (int k = 0; k < K; ++k) fan_ray(&F, R, xe, ye, a_min + k * step, ds, M.c_t, &M, deposit);
+        free(M.S);
     }
     bfield_free(&F);
     return bad ? ORC_ENOMEM : ORC_OK;

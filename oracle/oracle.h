@@ -103,10 +103,9 @@ int orc_fan_ray(const orc_grid* g, const double* c_mps, double R, double xe, dou
 
 /* First-arrival travel-time and amplitude maps of every transducer from a
  * fan of K rays each: T, A [n_tx][ny*nx] (T = +inf, A = 0 where unreached);
- * A from the closest ray among the candidates within eps_rel T + eps_abs of
- * the first arrival. */
+ * A from the candidate of least T + eta (b/h)^2, b its distance to the ray. */
 int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx, double R,
-                 double ds, int32_t K, double eps_rel, double eps_abs, double* T, double* A, int32_t nthreads);
+                 double ds, int32_t K, double eta, double* T, double* A, int32_t nthreads);
 
 /* Born map: d[f][q] = omega^2 h^2 sum_{|x| < R} E_e E_r dc (complex, interleaved)
  * for the listed pairs q = (e, r), or all n_tx x n_tx with pairs == NULL. */

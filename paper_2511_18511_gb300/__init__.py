@@ -308,16 +308,18 @@ class BornMaps:
 
 
 def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tensor] = None,
-                ctx: Optional[Context] = None, stream=None, out: Optional[BornMaps] = None) -> BornMaps:
+                ctx: Optional[Context] = None, stream=None, out: Optional[BornMaps] = None,
+                blocks_per_sm: int = 0) -> BornMaps:
     """Travel-time and amplitude maps of every transducer from fans of
-    fan_rays rays traced with their paraxial rays (paper Sec. 3.5)."""
+    fan_rays rays traced with their paraxial rays (paper Sec. 3.5).
+    blocks_per_sm selects the fan kernel variant (0 = default)."""
     ctx = ctx or default_context(prob.c.device.index)
     g = prob.grid
     if out is None:
         shape = (prob.n_tx, g.ny, g.nx)
         out = BornMaps(g, prob.ring_radius, torch.empty(shape, dtype=torch.float32, device=prob.c.device),
                        torch.empty(shape, dtype=torch.float32, device=prob.c.device))
-    o = _opts(ds, precision="fp32c")
+    o = _opts(ds, precision="fp32c", blocks_per_sm=blocks_per_sm)
     ps = prob.struct(c)
     _L.check(ctx.h, ctx.lib.rtborn_maps(ctx.h, C.byref(ps), C.byref(o), int(fan_rays), _ptr(out.T), _ptr(out.A),
                                         _stream(stream)))

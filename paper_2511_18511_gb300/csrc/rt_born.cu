@@ -19,13 +19,13 @@
 // sample, a = d.D, b = n.D) the time extrapolated to second order in the
 // ray-centred frame from the foot of the node on the ray,
 //     T + s a + (M/2) b^2,   M = P/Q_f,   Q_f = Q + a c P   (|Q_f| >= h where M < 0),
-// paired with A = sqrt(c / (c_t max(|Q_f|, h))). Two passes over the fan: the
-// first keeps each node's earliest candidate (first arrival; a 32-bit
-// atomicMin on order-preserving bits of T), the second, among the candidates
-// within RTBORN_EPS_REL T + RTBORN_EPS_ABS_US of it, the one from the ray
-// passing closest to the node (a 64-bit atomicMin on |b| << 32 | bits of A):
-// rays next to a node arrive within far less than the rounding of T of one
-// another, so the earliest alone would choose among them by rounding.
+// paired with A = sqrt(c / (c_t max(|Q_f|, h))). A node's travel time is its
+// earliest candidate (first arrival; a 32-bit atomicMin on order-preserving
+// bits of T). Its amplitude is that of the candidate of least
+// T + RTBORN_ETA_US (b/h)^2 (a 64-bit atomicMin on the ordered score << 32 |
+// bits of A): rays next to a node arrive within far less than the rounding of
+// T of one another, so the earliest alone would choose among them by
+// rounding; the penalty takes the ray passing closest to the node.
 //
 // Born map (rtborn_apply), per frequency f (omega = 2 pi f rad/us):
 //     d[f][e][r] = omega^2 h^2 sum_{|x| < R} E_e(x) E_r(x) dc(x),  e != r,
@@ -209,21 +209,30 @@ struct FanArgs {
     int K;
     float hf;                     // h, mm
     float Hhalf;                  // ds / (2h), cells
-    float eps_rel, eps_abs;       // near-simultaneous window of the amplitude choice
+    float eta;                    // us: penalty of the squared distance (cells) to the ray, amplitude choice
     unsigned* tfirst;             // [n_tx][ny*nx] order-preserving bits of the first arrival
-    unsigned long long* near;     // [n_tx][ny*nx] (|b| bits << 32) | A bits of the kept candidate
+    unsigned long long* near;     // [n_tx][ny*nx] (ordered bits of T + eta b^2) << 32 | A bits
     long long nn;
     unsigned long long* steps;    // RK4 steps taken (summed over rays)
 };
 
-// Offer the nodes around sample B (time T, stage-1 c and s) their candidates.
-// PASS 0: first arrival (32-bit atomicMin on the ordered time). PASS 1: among
-// the candidates within eps of it, the ray passing closest (64-bit atomicMin on
-// |b|, then A).
-template <int PASS>
-__device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, unsigned* __restrict__ tfirst,
-                                             unsigned long long* __restrict__ near, const BornRay& B, float T,
-                                             float c, float s, float inv_ct_h) {
+// Per-ray constants of the deposit: the transducer in cell coordinates and
+// h / c_t, for the reference time T_ref = h |node - x_t| / c_t of a node,
+// which is the same for every ray of the fan.
+struct FanRef {
+    float xt, yt, h_ct;
+};
+
+// Offer the nodes around sample B (Kahan pair T - Tc, stage-1 c and s) their
+// candidates: the first arrival by a 32-bit atomicMin on the ordered time; the
+// amplitude by a 64-bit atomicMin on (ordered score) << 32 | bits of A, with
+// score = T_cand - T_ref + eta b^2. T and T_ref lie within a factor of two of
+// each other, so their difference is exact and the score resolves ~1e-6 us
+// where T itself rounds at ~1e-5 us.
+__device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, const FanRef& F,
+                                             unsigned* __restrict__ tfirst, unsigned long long* __restrict__ near,
+                                             const BornRay& B, float T, float Tc, float c, float s,
+                                             float inv_ct_h) {
     const float fx = B.S.fx, fy = B.S.fy;
     const bool oi = fx >= 0.5f, oj = fy >= 0.5f;
     const float D0x = oi ? 1.f - fx : -fx, D0y = oj ? 1.f - fy : -fy;
@@ -247,27 +256,22 @@ __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, un
                     const float Qc = aQ >= 1.f ? aQ : 1.f;
                     float M = B.P / Qf;
                     if (!(M >= 0.f)) M = B.P / copysignf(Qc, Qf);
-                    const float cand = T + A.hf * (s * al + 0.5f * M * ac * ac);
+                    const float ext = A.hf * (s * al + 0.5f * M * ac * ac) - Tc;
                     const size_t node = (size_t)nj * G.nx + ni;
-                    if (PASS == 0) {
-                        atomicMin(tfirst + node, f2ord(cand));
-                    } else {
-                        const float Tf = ord2f(__ldg(tfirst + node));
-                        if (cand <= Tf + (A.eps_rel * Tf + A.eps_abs)) {
-                            const float amp = sqrtf(c * inv_ct_h / Qc);
-                            const unsigned long long key =
-                                ((unsigned long long)__float_as_uint(fabsf(ac)) << 32) | __float_as_uint(amp);
-                            atomicMin(near + node, key);
-                        }
-                    }
+                    atomicMin(tfirst + node, f2ord(T + ext));
+                    const float ux = (float)ni - F.xt, uy = (float)nj - F.yt;
+                    const float Tref = F.h_ct * sqrtf(ux * ux + uy * uy);
+                    const float score = ((T - Tref) + ext) + A.eta * ac * ac;
+                    const float amp = sqrtf(c * inv_ct_h / Qc);
+                    atomicMin(near + node, ((unsigned long long)f2ord(score) << 32) | __float_as_uint(amp));
                 }
             }
         }
     }
 }
 
-template <int BLOCK, int PASS>
-__global__ void __launch_bounds__(BLOCK) k_born_fan(const Geom G, const FanArgs A, const BNode* __restrict__ field) {
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const FanArgs A, const BNode* __restrict__ field) {
     const long long id = blockIdx.x * (long long)BLOCK + threadIdx.x;
     if (id >= (long long)G.n_tx * A.K) return;
     if (*G.bad_field) return;   // c <= 0 or NaN somewhere: every node stays unreached
@@ -305,6 +309,10 @@ __global__ void __launch_bounds__(BLOCK) k_born_fan(const Geom G, const FanArgs 
     C.at(B.S.ci, B.S.cj, B.S.fx, B.S.fy, c, gx, gy, hxx, hxy, hyy, tx, ty);
     const float c_t = c;
     const float inv_ct_h = 1.f / (c_t * A.hf);
+    FanRef F;
+    F.xt = (float)((xe - G.x0) / G.h);
+    F.yt = (float)((ye - G.y0) / G.h);
+    F.h_ct = A.hf / c_t;
     B.Q = 0.f;
     B.P = 1.f / c_t;
     float s_prev = C.slow(tx, ty);
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(BLOCK) k_born_fan(const Geom G, const FanArgs 
         Tc = (tt - T) - y;
         T = tt;
         s_prev = s;
-        born_deposit<PASS>(G, A, tfirst, near, B, T, c, s, inv_ct_h);
+        born_deposit(G, A, F, tfirst, near, B, T, Tc, c, s, inv_ct_h);
     }
     const unsigned mask = __activemask();
     const unsigned tot = __reduce_add_sync(mask, (unsigned)nsteps);
@@ -585,8 +593,7 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     A.K = fan_rays;
     A.hf = (float)G.h;
     A.Hhalf = (float)(0.5 * G.ds / G.h);
-    A.eps_rel = RTBORN_EPS_REL;
-    A.eps_abs = RTBORN_EPS_ABS_US;
+    A.eta = RTBORN_ETA_US;
     A.tfirst = tfirst;
     A.near = near;
     A.nn = nn;
@@ -594,10 +601,23 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return bcuda(ctx, e, "counter reset");
     const long long rays = (long long)prob->n_tx * fan_rays;
-    constexpr int B = 128;
-    const unsigned blocks = (unsigned)((rays + B - 1) / B);
-    rt::k_born_fan<B, 0><<<blocks, B, 0, s>>>(G, A, (const rt::BNode*)ctx->born_field);
-    rt::k_born_fan<B, 1><<<blocks, B, 0, s>>>(G, A, (const rt::BNode*)ctx->born_field);
+    const rt::BNode* fld = (const rt::BNode*)ctx->born_field;
+    // kernel variants: resident 128-thread blocks per SM the kernel is compiled for
+    const int minb = opt->blocks_per_sm ? opt->blocks_per_sm : 6;
+    const unsigned blocks = (unsigned)((rays + 127) / 128);
+    switch (minb) {
+#define FAN_V(MB)                                                \
+    case MB:                                                     \
+        rt::k_born_fan<128, MB><<<blocks, 128, 0, s>>>(G, A, fld); \
+        break;
+        FAN_V(4)
+        FAN_V(5)
+        FAN_V(6)
+        FAN_V(8)
+#undef FAN_V
+        default:
+            return bfail(ctx, RT_EINVAL, "rtborn_maps: blocks_per_sm must be 0 (= 6), 4, 5, 6 or 8");
+    }
     rt::k_born_unpack<<<(unsigned)std::min<long long>(((long long)n_ent + 255) / 256, 152 * 64), 256, 0, s>>>(
         tfirst, near, (long long)n_ent, T_out, A_out);
     e = cudaGetLastError();

@@ -115,6 +115,63 @@ def test_maps_fermat_against_linking(orc):
     assert rel.min() >= -2e-4 and rel.max() <= 5e-4, (rel.min(), rel.max())
 
 
+def test_maps_match_brute_force_over_all_fan_samples(orc):
+    """Tiny heterogeneous case: every map entry of a few nodes recomputed by
+    brute force from the recorded samples of every fan ray (the per-sample
+    candidates of the map rule, the earliest for T, the least
+    T + eta (b/h)^2 for A), independently of the map routine's loops."""
+    g = P.Grid(48, 48, 0.5)
+    R = 10.0
+    c = P.gaussian_inclusions(g, 31, amp=0.05, sigma_lo=2.0, sigma_hi=3.0, centre_radius=5.0)
+    tx = P.ring(3, R)
+    ds, K, eta = 0.05, P.born_fan_rays(R, g.h), orc.ETA
+    T, A = orc.fan_maps(g, c, tx, R, ds, K)
+    x, y = g.node_xy()
+    rng = P.SplitMix64(32)
+    inside = np.flatnonzero((x * x + y * y).ravel() < (R - 1.0) ** 2)
+    nodes = inside[(rng.uniform(12) * len(inside)).astype(int)]
+    h = g.h
+    for t in range(len(tx)):
+        a_min, step = orc.fan_angles(tx[t], R, ds, K)
+        c_t = orc.sample(g, c, tx[t][None, :])[0, 0]
+        best = {int(k): (np.inf, np.inf, 0.0) for k in nodes}      # T, score, A
+        for k in range(K):
+            r = orc.fan_ray(g, c, R, tx[t], a_min + k * step, ds)
+            sl = slice(1, None)                                      # the transducer itself offers nothing
+            X, Y, DX, DY = r["x"][sl], r["y"][sl], r["dx"][sl], r["dy"][sl]
+            ic = np.floor((X - g.x0) / h + 0.5).astype(int)
+            jc = np.floor((Y - g.y0) / h + 0.5).astype(int)
+            for node in nodes:
+                j, i = divmod(int(node), g.nx)
+                m = np.flatnonzero((np.abs(ic - i) <= 1) & (np.abs(jc - j) <= 1))
+                if len(m) == 0:
+                    continue
+                Dx, Dy = g.x0 + i * h - X[m], g.y0 + j * h - Y[m]
+                al = DX[m] * Dx + DY[m] * Dy
+                ac = -DY[m] * Dx + DX[m] * Dy
+                ok = (al >= -0.5 * ds) & (al < 0.5 * ds)
+                if not ok.any():
+                    continue
+                m, al, ac = m[ok], al[ok], ac[ok]
+                Q, Pp, cc, ss, Tm = (r[f][sl][m] for f in ("Q", "P", "c", "s", "T"))
+                Qf = Q + al * cc * Pp
+                Qc = np.where(np.abs(Qf) >= h, Qf, np.where(Qf < 0, -h, h))
+                curv = Pp / Qf
+                curv = np.where(curv >= 0, curv, Pp / Qc)
+                cand = Tm + ss * al + 0.5 * curv * ac * ac
+                amp = np.sqrt(cc / (c_t * np.abs(Qc)))
+                score = cand + eta * (ac / h) ** 2
+                T0, S0, A0 = best[int(node)]
+                q = int(np.argmin(score))
+                best[int(node)] = (min(T0, cand.min()), min(S0, score[q]),
+                                   amp[q] if score[q] < S0 else A0)
+        for node in nodes:
+            j, i = divmod(int(node), g.nx)
+            Tb, _, Ab = best[int(node)]
+            assert abs(T[t, j, i] - Tb) <= 1e-12 * Tb, (t, node, T[t, j, i], Tb)
+            assert abs(A[t, j, i] - Ab) <= 1e-12 * Ab, (t, node, A[t, j, i], Ab)
+
+
 # --------------------------------------------------------- Born map and adjoint
 
 def _synthetic_maps(g, tx, seed):

@@ -73,8 +73,8 @@ BORN_MUTANTS = {
     "born_first_order_only": ("p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A);",
                               "p->T + p->s * along, fabs(across), A);"),
     "born_curvature_at_sample": ("const double Qf = p->Q + along * p->c * p->P;", "const double Qf = p->Q;"),
-    "born_amplitude_farthest_ray": ("if (b < M->B[k] || (b == M->B[k] && A < M->A[k])) {",
-                                    "if (b > M->B[k] || M->B[k] == INFINITY) {"),
+    "born_amplitude_no_distance_penalty": ("const double score = cand + M->eta * q * q;",
+                                           "const double score = cand + 0.0 * q * q;"),
     "born_nearest_node_only": ("for (int i = ic - 1; i <= ic + 1; ++i) {", "for (int i = ic; i <= ic; ++i) {"),
     "born_latest_arrival": ("if (cand < M->T[k]) M->T[k] = cand;",
                             "if (!(cand <= M->T[k]) || M->T[k] == INFINITY) M->T[k] = cand;"),
@@ -97,6 +97,7 @@ BORN_PINS = [
     lambda orc: bpins.test_paraxial_Q_matches_auxiliary_rays(orc, 0, 0.1),
     lambda orc: bpins.test_paraxial_Q_matches_auxiliary_rays(orc, 9, -0.6),
     bpins.test_maps_homogeneous_match_distance,
+    bpins.test_maps_match_brute_force_over_all_fan_samples,
     bpins.test_born_dot_product_identity,
     bpins.test_born_point_scatterer_homogeneous,
     bpins.test_born_adjoint_single_datum_homogeneous,
