@@ -70,6 +70,19 @@ int prepare(rt_ctx* ctx, const rt_problem* p, const rt_options* o, bool need_lin
     cudaError_t e = rt::launch_pack(p->grid, p->c_mps, ctx->field, ctx->dflag, o->precision, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pack kernel");
     G->bad_field = ctx->dflag;
+    // per-transducer polar angles (NaN = off the ring), read by every pair set-up
+    const size_t phi_bytes = sizeof(double) * (size_t)p->n_tx;
+    if (ctx->txphi_cap < phi_bytes) {
+        if (capturing(s)) return fail(ctx, RT_EINVAL, "transducer table too small during stream capture");
+        if (ctx->txphi) cudaFree(ctx->txphi);
+        ctx->txphi = nullptr;
+        ctx->txphi_cap = 0;
+        if (cudaMalloc(&ctx->txphi, phi_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "transducer table");
+        ctx->txphi_cap = phi_bytes;
+    }
+    e = rt::launch_tx_phi(*G, ctx->txphi, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "transducer table kernel");
+    G->tx_phi = ctx->txphi;
     ctx->last_stream = s;
     return RT_OK;
 }
@@ -109,6 +122,7 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     G->x0 = g.x0_mm;
     G->y0 = g.y0_mm;
     G->R = R;
+    G->inv_R2 = 1.0 / (R * R);
     G->ds = o->ds_mm;
     const double ox = -g.x0_mm / g.h_mm, oy = -g.y0_mm / g.h_mm;
     G->Ox = (int)std::floor(ox);
@@ -126,6 +140,7 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     G->pairs = p->pairs;
     G->n_pairs = p->n_pairs;
     G->bad_field = nullptr;
+    G->tx_phi = nullptr;
     if (G->Q > (long long)INT32_MAX / 2) return fail(ctx, RT_EINVAL, "ring too large in cells");
     G->Qi = (int)G->Q;
     G->Hf = (float)(o->ds_mm / g.h_mm);
@@ -173,6 +188,7 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (ctx->scan_tmp) cudaFree(ctx->scan_tmp);
     if (ctx->fan) cudaFree(ctx->fan);
     if (ctx->fan_need) cudaFree(ctx->fan_need);
+    if (ctx->txphi) cudaFree(ctx->txphi);
     if (ctx->batch_ws) cudaFree(ctx->batch_ws);
     if (ctx->batch_desc) cudaFree(ctx->batch_desc);
     if (ctx->batch_desc_host) cudaFreeHost(ctx->batch_desc_host);

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             L.n_eval = 0;
             L.phase = 0;
             L.psi_at_lo = 0.0;
-            L.best_dist = CUDART_INF;
+            L.best_d2 = CUDART_INF;
             if (fan_rays >= 2 && d.fan && isnan(tin)) {
                 int e, r;
                 pair_of(G, k, e, r);
@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             }
             if (link_update(G, L, o, tol, max_iter)) {
                 const int k = L.k;
-                const int st = (L.best_dist <= tol) ? RT_RAY_OK
-                               : (L.best_dist == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);
+                const int st = (L.best_d2 <= tol * tol) ? RT_RAY_OK
+                               : (L.best_d2 == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);
                 d.theta[k] = L.best_th;
                 d.tof[k] = L.best_T;
                 if (d.hit) { d.hit[2 * k] = L.best_hx; d.hit[2 * k + 1] = L.best_hy; }

@@ -19,6 +19,8 @@ struct rt_ctx {
     double* fan = nullptr;          // [n_tx * fan_rays] interception angles of the emitter fans
     int* fan_need = nullptr;        // [n_tx] emitters with at least one cold-start pair
     size_t fan_cap = 0, need_cap = 0;
+    double* txphi = nullptr;        // [n_tx] polar angles of the transducers (NaN = off the ring)
+    size_t txphi_cap = 0;
     // batch workspace (rt_batch_run): packed fields, fans, flags; descriptors
     void* batch_ws = nullptr;
     size_t batch_ws_bytes = 0;
@@ -76,6 +78,7 @@ cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const dou
                            double* g_c, int* queue, cudaStream_t s);
 cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double* theta,
                         int64_t* row_ptr, int32_t* col, double* val, bool fill, cudaStream_t s);
+cudaError_t launch_tx_phi(const Geom& G, double* phi, cudaStream_t s);
 cudaError_t launch_scan(int64_t* row_ptr, int n, void* tmp, size_t* tmp_bytes, cudaStream_t s);
 
 size_t node_bytes(int prec);

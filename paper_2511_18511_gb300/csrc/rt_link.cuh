@@ -16,10 +16,20 @@ namespace rt {
 
 constexpr double kPi = 3.141592653589793;
 
-__device__ __forceinline__ double mod_2pi(double a) { return a - 2.0 * kPi * floor(a / (2.0 * kPi)); }
+// a mod 2 pi in [0, 2 pi): the multiple from a product with 1/(2 pi) (no FP64
+// division, which is slow on this part), then one correction each way, so the
+// result is the same as a - 2 pi floor(a / (2 pi)) up to the rounding of the
+// last subtraction.
+__device__ __forceinline__ double mod_2pi(double a) {
+    constexpr double two_pi = 2.0 * kPi, inv_two_pi = 1.0 / (2.0 * kPi);
+    double r = fma(-two_pi, floor(a * inv_two_pi), a);
+    if (r < 0.0) r += two_pi;
+    if (r >= two_pi) r -= two_pi;
+    return r;
+}
 
 struct LinkCtx {
-    double xe, ye, xr, yr, phi_e, psi_r, th_lo, th_hi;
+    double xe, ye, xr, yr, phi_e, phi_r, psi_r, th_lo, th_hi;
 };
 
 __device__ __forceinline__ bool on_ring(double x, double y, double R) {
@@ -33,9 +43,16 @@ __device__ __forceinline__ bool setup_pair(const Geom& G, int k, LinkCtx& L) {
     if (*G.bad_field || e < 0 || e >= G.n_tx || r < 0 || r >= G.n_tx || e == r) return false;
     L.xe = G.tx[2 * e]; L.ye = G.tx[2 * e + 1];
     L.xr = G.tx[2 * r]; L.yr = G.tx[2 * r + 1];
-    if (!on_ring(L.xe, L.ye, G.R) || !on_ring(L.xr, L.yr, G.R)) return false;
-    L.phi_e = atan2(L.ye, L.xe);
-    L.psi_r = mod_2pi(atan2(L.yr, L.xr) - L.phi_e);
+    if (G.tx_phi) {   // per-transducer table (NaN = off the ring)
+        L.phi_e = G.tx_phi[e];
+        L.phi_r = G.tx_phi[r];
+        if (isnan(L.phi_e) || isnan(L.phi_r)) return false;
+    } else {
+        if (!on_ring(L.xe, L.ye, G.R) || !on_ring(L.xr, L.yr, G.R)) return false;
+        L.phi_e = atan2(L.ye, L.xe);
+        L.phi_r = atan2(L.yr, L.xr);
+    }
+    L.psi_r = mod_2pi(L.phi_r - L.phi_e);
     L.th_lo = L.phi_e + 0.5 * kPi;
     L.th_hi = L.phi_e + 1.5 * kPi;
     return true;
@@ -46,8 +63,8 @@ __device__ __forceinline__ bool setup_pair(const Geom& G, int k, LinkCtx& L) {
 struct LinkState {
     double xe, ye, xr, yr, phi_e, psi_r, th_lo, th_hi;
     double a_min, a_max;
-    double th0, m0, mp;              // first angle, its misfit, the probe's misfit
-    double best_th, best_T, best_hx, best_hy, best_dist;
+    double th0, m0;                  // first angle and its misfit
+    double best_th, best_T, best_hx, best_hy, best_d2;   // closest ray; best_d2 = |x_hit - x_r|^2
     double ta, fa, tb, fb;           // bracket
     double prev_th, prev_m, cur_th, cur_m;
     double psi_at_lo, next;
@@ -71,17 +88,33 @@ __device__ __forceinline__ void br_insert(LinkState& L, double t, double m) {
     }
 }
 
-// Misfit of an ended trace (same rule as evaluate()).
+// Misfit of an ended trace (same rule as evaluate()) and the squared
+// distance of its hit to the receiver.
 __device__ __forceinline__ void misfit_of(const Geom& G, const LinkState& L, const TraceOut& o, double theta,
-                                          double& m, double& dist) {
+                                          double& m, double& d2) {
     const double dx = o.hx - L.xr, dy = o.hy - L.yr;
-    dist = sqrt(dx * dx + dy * dy);
+    d2 = dx * dx + dy * dy;
     double psi;
     if (o.flags & 3) {
         psi = (theta - L.th_lo < L.th_hi - theta) ? L.psi_at_lo : 2.0 * kPi - L.psi_at_lo;
-        dist = DBL_MAX;
+        d2 = DBL_MAX;
     } else {
-        psi = mod_2pi(atan2(o.hy, o.hx) - L.phi_e);
+        // the hit's angle from the emitter = the receiver's (psi_r) + the angle
+        // delta from the receiver to the hit around the centre. Both lie on the
+        // ring, so sin(delta) = u = (x_r x x_hit) / R^2; near the receiver
+        // delta = asin(u) by its series (|u| < 0.05: terms to u^13 leave
+        // < 1e-20 relative), else atan2.
+        const double cd = L.xr * o.hx + L.yr * o.hy, sd = L.xr * o.hy - L.yr * o.hx;
+        const double u = sd * G.inv_R2;
+        double delta;
+        if (cd > 0.0 && fabs(u) < 0.05) {
+            const double u2 = u * u;
+            delta = u * (1.0 + u2 * (1.0 / 6 + u2 * (3.0 / 40 + u2 * (15.0 / 336 + u2 * (105.0 / 3456 +
+                    u2 * (945.0 / 42240 + u2 * (10395.0 / 599040)))))));
+        } else {
+            delta = atan2(sd, cd);
+        }
+        psi = mod_2pi(L.psi_r + delta);
     }
     m = G.R * (psi - L.psi_r);
 }
@@ -98,13 +131,13 @@ __device__ __forceinline__ double next_angle(const LinkState& L, double cand) {
 // link_pair). Returns true when the pair is finished.
 __device__ inline bool link_update(const Geom& G, LinkState& L, const TraceOut& o, double tol, int max_iter) {
     const double theta = L.next;
-    double m, dist;
-    misfit_of(G, L, o, theta, m, dist);
+    double m, d2;
+    misfit_of(G, L, o, theta, m, d2);
     ++L.n_eval;
-    if (dist < L.best_dist) {
-        L.best_th = theta; L.best_T = o.T; L.best_hx = o.hx; L.best_hy = o.hy; L.best_dist = dist;
+    if (d2 < L.best_d2) {
+        L.best_th = theta; L.best_T = o.T; L.best_hx = o.hx; L.best_hy = o.hy; L.best_d2 = d2;
     }
-    if (dist <= tol) return true;
+    if (d2 <= tol * tol) return true;
     if (L.phase == 0) {
         L.m0 = m;
         L.e0_flagged = (o.flags & 3) != 0;

@@ -68,6 +68,18 @@ __global__ void k_pack(const double* __restrict__ c_mps, int nx, int ny, CellCoe
     }
 }
 
+__global__ void k_tx_phi(const double* __restrict__ tx, int n_tx, double R, double* __restrict__ phi) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tx) return;
+    const double x = tx[2 * t], y = tx[2 * t + 1];
+    phi[t] = on_ring(x, y, R) ? atan2(y, x) : nan("");
+}
+
+cudaError_t launch_tx_phi(const Geom& G, double* phi, cudaStream_t s) {
+    k_tx_phi<<<(G.n_tx + 127) / 128, 128, 0, s>>>(G.tx, G.n_tx, G.R, phi);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
                         cudaStream_t s) {
     const int n = (g.nx - 1) * (g.ny - 1);
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks) k_link(Geom G,
             L.n_eval = 0;
             L.phase = 0;
             L.psi_at_lo = 0.0;
-            L.best_dist = CUDART_INF;
+            L.best_d2 = CUDART_INF;
             if (fan_rays >= 2 && isnan(tin)) {
                 int e, r;
                 pair_of(G, k, e, r);
@@ -186,8 +198,8 @@ __global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks) k_link(Geom G,
             steps += o.steps;
             if (link_update(G, L, o, tol, max_iter)) {
                 const int k = L.k;
-                const int st = (L.best_dist <= tol) ? RT_RAY_OK
-                               : (L.best_dist == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);
+                const int st = (L.best_d2 <= tol * tol) ? RT_RAY_OK
+                               : (L.best_d2 == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);
                 theta[k] = L.best_th;
                 if (tof) tof[k] = L.best_T;
                 if (hit) { hit[2 * k] = L.best_hx; hit[2 * k + 1] = L.best_hy; }

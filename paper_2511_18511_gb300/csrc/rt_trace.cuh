@@ -51,6 +51,7 @@ template <typename T> struct NodeT { using type = CellCoef<T>; };
 struct Geom {
     int nx, ny;
     double h, x0, y0, R;
+    double inv_R2;          // 1 / R^2
     double ds;              // mm
     int Ox, Oy;             // floor of the ring centre in cell coordinates (-x0/h, -y0/h)
     double oxf, oyf;        // fractional parts of the ring centre
@@ -63,6 +64,7 @@ struct Geom {
     const int* pairs;       // [2 n_pairs] or null
     int n_pairs;
     const int* bad_field;   // device flag set by the pack kernel (c <= 0 or NaN)
+    const double* tx_phi;   // [n_tx] polar angle of each transducer, NaN if off the ring; null = compute
     // FP32 copies of the per-step constants, so the FP32 march issues no FP64
     float Hf, dsf, Rcf, oxff, oyff, qf;
     int Qi;                 // Q as 32-bit (grids up to 32k cells per side)
@@ -176,6 +178,7 @@ template <typename T> struct Dir;
 template <> struct Dir<double> {
     double x, y;
     __device__ __forceinline__ void set(double th) { sincos(th, &y, &x); }
+    __device__ __forceinline__ void set_cs(double c, double s) { x = c; y = s; }
     __device__ __forceinline__ double hx() const { return x; }
     __device__ __forceinline__ double hy() const { return y; }
     __device__ __forceinline__ double lx() const { return 0.0; }
@@ -198,6 +201,9 @@ template <> struct Dir<float> {
     __device__ __forceinline__ void set(double th) {
         double c, s;
         sincos(th, &s, &c);
+        set_cs(c, s);
+    }
+    __device__ __forceinline__ void set_cs(double c, double s) {
         x = (float)c; ex = (float)(c - (double)x);
         y = (float)s; ey = (float)(s - (double)y);
     }
@@ -378,8 +384,10 @@ struct TraceState {
     int steps;                // RK4 steps of this trace (incl. landing)
 };
 
+// Starts a trace at (xe, ye) with unit launch direction (c, s).
 template <typename T>
-__device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, double xe, double ye, double theta) {
+__device__ __forceinline__ void trace_begin_cs(TraceState<T>& ts, const Geom& G, double xe, double ye, double c,
+                                               double s) {
     const double u = (xe - G.x0) / G.h, v = (ye - G.y0) / G.h;
     const double fu = floor(u), fv = floor(v);
     ts.S.ci = (int)fu;
@@ -388,7 +396,7 @@ __device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, do
     ts.S.fy = (T)(v - fv);
     ts.S.lx = (T)((u - fu) - (double)ts.S.fx);
     ts.S.ly = (T)((v - fv) - (double)ts.S.fy);
-    ts.S.d.set(theta);
+    ts.S.d.set_cs(c, s);
     ts.s_first = ts.s_cur = (T)0;
     ts.Ssum = ts.Scomp = (T)0;
     ts.m = 0;
@@ -397,6 +405,13 @@ __device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, do
     ts.iL = ts.jL = 0;
     ts.txL = ts.tyL = (T)0;
     ts.steps = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, double xe, double ye, double theta) {
+    double c, s;
+    sincos(theta, &s, &c);
+    trace_begin_cs(ts, G, xe, ye, c, s);
 }
 
 // One RK4 step. Returns true when the trace has ended: the step ended on or
