@@ -540,6 +540,24 @@ def main():
     r64 = timed("fp64", max(1, args.fp64_steps), 1)
     ms64 = float(np.mean(r64["step_ms"]))
 
+    # warm start: the same step relinked from the previous step's angles (the
+    # paper's later linearisations, Sec. 3.4.1), FP32-compensated
+    theta_prev = res["out"]["theta"].clone()
+    out_w, g_w = buffers(), torch.empty_like(prob.c)
+    warm_ms = []
+    for k in range(max(2, min(args.steps, 3)) + 1):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp32c", theta0=theta_prev, ctx=ctx, out=out_w)
+        rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision="fp32c", ctx=ctx, out=g_w)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            warm_ms.append(a.elapsed_time(b))
+    warm_traces = float(out_w["iters"].float().mean().item())
+    warm = float(np.mean(warm_ms))
+
     # roofline of the dominant kernel (the FP32 link kernel), from its live events
     steps_per_launch = res["counts"][7]
     link_ms = float(np.mean(res["link_ms"]))
@@ -596,6 +614,9 @@ def main():
                      "kernel": "k_link<float> (+ its field pack)",
                      "flop_per_rk4_step": FLOP_PER_STEP, "rk4_steps_per_launch": steps_per_launch,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"},
+        "warm_start": {"value": n / (warm / 1e3), "unit": UNIT, "ms_per_step": warm,
+                       "mean_traces_per_pair": warm_traces,
+                       "start": "the previous step's linked angles"},
         "fp64_gpu": {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                      "speedup_fp32c_over_fp64": ms64 / ms_per_step},
         "link": {"mean_traces_per_pair": res["iters"], "all_linked": res["ok"],

@@ -81,6 +81,7 @@ def load(path: str):
     L.orc_adjoint.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
                               C.c_double, _dp, _dp, _dp, C.c_int32]
     L.orc_num_threads.argtypes = []
+    L.orc_set_integrator.argtypes = [C.c_int32]
     L.orc_fan_angles.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, _dp, _dp]
     L.orc_fan_ray.argtypes = [G, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                               C.c_int64, _dp, _lp]
@@ -147,6 +148,23 @@ def _check(rc, what):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+INTEGRATORS = {"rk4": 0, "heun": 1}
+
+
+class integrator:
+    """Context manager: trace with another integrator ("rk4" default, "heun")."""
+
+    def __init__(self, name: str):
+        self.k = INTEGRATORS[name]
+
+    def __enter__(self):
+        _check(lib().orc_set_integrator(self.k), "set_integrator")
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_integrator(0)
 
 
 def field(grid, c_mps):

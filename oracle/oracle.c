@@ -16,7 +16,8 @@
  *      inside the grid with a margin, which is checked);
  *   R3 ray equations dx/ds = d, dd/ds = -(grad c - (grad c . d) d)/c (the
  *      refractive-index form of Sec. 3.2.3 with n = c0/c), classic RK4 at fixed
- *      ds, d renormalised after every step;
+ *      ds (or, with orc_set_integrator(1), Heun's second-order Runge-Kutta, the
+ *      paper's default), d renormalised after every step;
  *   R4 a trace ends at the first step, after the first one, whose end lies on
  *      or outside |x| = R; the last point is then replaced by the boundary
  *      interception, reached by an RK4 step of length ds' <= ds (Sec. 4.2: last
@@ -142,7 +143,7 @@ static void rhs(const Field* F, const double st[4], double k[4]) {
 }
 
 /* R3: one classic RK4 step of length hs, then d renormalised. */
-static void rk4(const Field* F, const double st[4], double hs, double out[4]) {
+static void step_rk4(const Field* F, const double st[4], double hs, double out[4]) {
     double k1[4], k2[4], k3[4], k4[4], t[4];
     rhs(F, st, k1);
     for (int q = 0; q < 4; ++q) t[q] = st[q] + 0.5 * hs * k1[q];
@@ -155,6 +156,34 @@ static void rk4(const Field* F, const double st[4], double hs, double out[4]) {
     double n = sqrt(out[2] * out[2] + out[3] * out[3]);
     out[2] /= n;
     out[3] /= n;
+}
+
+/* R3 (option, the paper's default, Sec. 3.2.3): one step of Heun's
+ * second-order Runge-Kutta method of length hs (the slope at the start, then
+ * the slope at the Euler end point, averaged), then d renormalised. */
+static void step_heun(const Field* F, const double st[4], double hs, double out[4]) {
+    double k1[4], k2[4], t[4];
+    rhs(F, st, k1);
+    for (int q = 0; q < 4; ++q) t[q] = st[q] + hs * k1[q];
+    rhs(F, t, k2);
+    for (int q = 0; q < 4; ++q) out[q] = st[q] + 0.5 * hs * (k1[q] + k2[q]);
+    double n = sqrt(out[2] * out[2] + out[3] * out[3]);
+    out[2] /= n;
+    out[3] /= n;
+}
+
+/* The integrator every trace uses: 0 = classic RK4 (default), 1 = Heun. */
+static int g_integrator = 0;
+
+int orc_set_integrator(int32_t k) {
+    if (k != 0 && k != 1) return ORC_EINVAL;
+    g_integrator = k;
+    return ORC_OK;
+}
+
+static void rk4(const Field* F, const double st[4], double hs, double out[4]) {
+    if (g_integrator == 1) step_heun(F, st, hs, out);
+    else step_rk4(F, st, hs, out);
 }
 
 /* R4: from an inside state st, the step length ds' in [0, ds] whose RK4 end

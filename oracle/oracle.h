@@ -90,6 +90,10 @@ int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const doub
 
 int orc_num_threads(void);
 
+/* Integrator of every later trace (process-wide): 0 = classic RK4 (default),
+ * 1 = Heun's second-order Runge-Kutta. Returns ORC_EINVAL for other values. */
+int orc_set_integrator(int32_t k);
+
 /* ---- ray-Born (born.c) ------------------------------------------------ */
 
 /* Fan angles of transducer (xe, ye): theta_k = a_min + k * step, k < K. */

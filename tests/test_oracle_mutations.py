@@ -40,6 +40,7 @@ MUTANTS = {
                            "gs[S.k[q]] += g_tof[k] * S.w[q];"),
     "speed_units": ("F->c[k] = v * 1e-3;", "F->c[k] = v * 1e-2;"),
     "slowness_uses_c": ("f[3] += S.w[q] * F->s[S.k[q]];", "f[3] += S.w[q] * F->c[S.k[q]];"),
+    "heun_end_slope_only": ("out[q] = st[q] + 0.5 * hs * (k1[q] + k2[q]);", "out[q] = st[q] + hs * k2[q];"),
 }
 
 # fast pins first; a mutant is killed by the first pin that fails
@@ -51,6 +52,8 @@ PINS = [
     pins.test_hits_land_on_ring_and_within_tol,
     lambda orc: pins.test_linear_gradient_closed_form(orc, 1.0),
     pins.test_rk4_fourth_order_on_circular_arc,
+    pins.test_heun_second_order_on_circular_arc,
+    pins.test_heun_linking_converges_to_analytic_circles,
     pins.test_paper_acoustic_length_experiment,
     pins.test_fisheye_ring_closed_form_converges_h2,
     pins.test_adjoint_matches_central_differences,

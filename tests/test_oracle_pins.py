@@ -134,6 +134,61 @@ def test_rk4_fourth_order_on_circular_arc(orc):
     assert 11.0 < r1 < 22.0 and 11.0 < r2 < 22.0, errs
 
 
+def _arc_errors(orc, steps):
+    g = P.Grid(128, 128, 0.5)
+    c = P.linear_gradient(g, 1500.0, 20.0)
+    p = np.array([-20.0, 0.0])
+    th = 0.3
+    d = np.array([np.cos(th), np.sin(th)])
+    yc = -1500.0 / 20.0
+    t = (yc - p[1]) / d[0]
+    centre = np.array([p[0] - t * d[1], yc])
+    errs = []
+    for ds in steps:
+        n = int(round(36.0 / ds))
+        pts = orc.march(g, c, p[0], p[1], th, ds, n)
+        errs.append(np.abs(np.linalg.norm(pts - centre, axis=1) - abs(t)).max())
+    return errs
+
+
+def test_heun_second_order_on_circular_arc(orc):
+    """The paper's default integrator (Sec. 3.2.3, Heun's second-order
+    Runge-Kutta): on the same exact circular arc the deviation shrinks ~4x per
+    halving of ds; straight rays stay exact."""
+    with orc.integrator("heun"):
+        errs = _arc_errors(orc, (1.0, 0.5, 0.25))
+        g = P.Grid(64, 64, 0.5)
+        pts = orc.march(g, P.homogeneous(g), -10.0, 3.0, 0.7, 0.3, 40)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+    s = np.arange(41) * 0.3
+    np.testing.assert_allclose(pts, np.stack([-10.0 + s * np.cos(0.7), 3.0 + s * np.sin(0.7)], 1), atol=1e-12)
+
+
+def test_heun_linking_converges_to_analytic_circles(orc):
+    """Heun linking in c = c_m + g y (g = 5 (m/s)/mm): the linked launch angles
+    approach the tangents of the analytic circles at second order in ds (ratio
+    ~4 per halving; RK4 reaches them to 1e-13 at any of these steps)."""
+    g, tx, R = _small_ring(16)
+    gs = 5.0
+    c = P.linear_gradient(g, 1500.0, gs)
+    pairs = np.array([[0, 5], [3, 11], [8, 14], [2, 9]], np.int32)
+    xe, xr = tx[pairs[:, 0]], tx[pairs[:, 1]]
+    yc = -1500.0 / gs
+    dx = xe[:, 0] - xr[:, 0]
+    xc = ((xe[:, 0] ** 2 - xr[:, 0] ** 2) + (xe[:, 1] - yc) ** 2 - (xr[:, 1] - yc) ** 2) / (2 * dx)
+    t = np.stack([-(xe[:, 1] - yc), xe[:, 0] - xc], 1)
+    t *= np.sign((t * (xr - xe)).sum(1))[:, None]
+    th = np.arctan2(t[:, 1], t[:, 0])
+    errs = []
+    with orc.integrator("heun"):
+        for ds in (0.4, 0.2, 0.1):
+            r = orc.link(g, c, tx, R, ds, tol=1e-10, pairs=pairs)
+            assert (r["status"] == 0).all()
+            errs.append(np.abs(np.angle(np.exp(1j * (th - r["theta"])))).max())
+    assert all(3.6 < errs[k] / errs[k + 1] < 4.4 for k in range(2)), errs
+
+
 # ---------------------------------------------------------------- fish-eye lens
 
 def _fisheye_T(tx, pairs, a=40.0, c0=1.5):
