@@ -65,6 +65,14 @@ enum rt_precision {
                           sums; FP64 linking updates, landing and endpoint */
 };
 
+/* Ray integrator (paper Sec. 3.2.3 lists Heun's second-order Runge-Kutta as
+ * its default; classic RK4 is this library's default). */
+enum rt_integrator {
+    RT_RK4 = 0,        /* classic fourth-order Runge-Kutta */
+    RT_HEUN = 1        /* Heun's second-order Runge-Kutta: slopes at the start and
+                          at the Euler end point, averaged */
+};
+
 typedef struct {
     int32_t nx, ny;      /* nodes per axis, >= 3 */
     double h_mm;         /* node spacing */
@@ -90,6 +98,8 @@ typedef struct {
                             0 = 512 / block_threads. FP32 variants (threads, unroll,
                             blocks): (64,1,8) (64,1,12) (128,1,4) (128,1,5) (128,1,6)
                             (128,2,4) (256,1,2) (256,1,3); FP64: (128,1,1) */
+    int32_t integrator;    /* enum rt_integrator: the ray stepper of every trace of
+                            the ToF calls (rtborn_maps requires RT_RK4) */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system

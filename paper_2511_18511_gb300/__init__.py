@@ -23,6 +23,7 @@ __all__ = ["Context", "Problem", "rt_link", "rt_tof_forward", "rt_tof_adjoint", 
            "BornMaps", "rtborn_maps", "rtborn_apply", "rtborn_adjoint", "Born", "born", "GEMM_MODES"]
 
 PRECISIONS = {"fp64": _L.RT_FP64, "fp32c": _L.RT_FP32_COMP}
+INTEGRATORS = {"rk4": 0, "heun": 1}
 
 
 class Context:
@@ -111,21 +112,24 @@ DEFAULT_FAN = 256
 
 
 def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, block_threads=0,
-          step_unroll=0, blocks_per_sm=0) -> _L.RtOptions:
+          step_unroll=0, blocks_per_sm=0, integrator="rk4") -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    if integrator not in INTEGRATORS:
+        raise ValueError(f"integrator must be one of {sorted(INTEGRATORS)}")
     return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays),
-                        int(block_threads), int(step_unroll), int(blocks_per_sm))
+                        int(block_threads), int(step_unroll), int(blocks_per_sm), INTEGRATORS[integrator])
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
             theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
             ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
-            fan_rays: int = DEFAULT_FAN) -> dict:
+            fan_rays: int = DEFAULT_FAN, integrator: str = "rk4") -> dict:
     """Link every pair (shooting method, paper Sec. 3.4) and return the linked
     angles, travel times (us), interceptions (mm), per-pair status and traces.
     Cold starts (theta0 None / NaN) use a fan of fan_rays rays per emitter, or
-    the straight line to the receiver with fan_rays = 0."""
+    the straight line to the receiver with fan_rays = 0. integrator: "rk4" or
+    "heun" (the paper's default stepper)."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     n = prob.n_pairs
@@ -140,21 +144,22 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     else:
         out["theta"].copy_(theta0)
     ps = prob.struct(c)
-    o = _opts(ds, tol, max_iter, precision, fan_rays)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator)
     _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                     _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
     return out
 
 
 def rt_tof_forward(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
-                   c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None):
+                   c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None,
+                   integrator: str = "rk4"):
     """Travel time and interception of every pair at fixed launch angles."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     tof_ = torch.empty(prob.n_pairs, dtype=torch.float64, device=dev)
     hit = torch.empty((prob.n_pairs, 2), dtype=torch.float64, device=dev)
     ps = prob.struct(c)
-    o = _opts(ds, precision=precision)
+    o = _opts(ds, precision=precision, integrator=integrator)
     _L.check(ctx.h, ctx.lib.rt_tof_forward(ctx.h, C.byref(ps), C.byref(o), _ptr(theta.contiguous()), _ptr(tof_),
                                            _ptr(hit), _stream(stream)))
     return tof_, hit
@@ -163,14 +168,14 @@ def rt_tof_forward(prob: Problem, theta: torch.Tensor, ds: float, precision: str
 def rt_tof_adjoint(prob: Problem, theta: torch.Tensor, g_tof: torch.Tensor, ds: float,
                    tof_ref: Optional[torch.Tensor] = None, precision: str = "fp32c",
                    c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None,
-                   out: Optional[torch.Tensor] = None) -> torch.Tensor:
+                   out: Optional[torch.Tensor] = None, integrator: str = "rk4") -> torch.Tensor:
     """g_c = sum_i (g_tof_i - tof_ref_i) dT_i/dc (us per m/s) with the rays
     frozen at theta: the transpose of the system matrix (paper Sec. 3.1.1)."""
     ctx = ctx or default_context(prob.c.device.index)
     cc = prob.c if c is None else c
     g = torch.empty_like(cc) if out is None else out
     ps = prob.struct(c)
-    o = _opts(ds, precision=precision)
+    o = _opts(ds, precision=precision, integrator=integrator)
     _L.check(ctx.h, ctx.lib.rt_tof_adjoint(ctx.h, C.byref(ps), C.byref(o), _ptr(theta.contiguous()),
                                            _ptr(g_tof.contiguous()),
                                            _ptr(None if tof_ref is None else tof_ref.contiguous()),
@@ -179,7 +184,7 @@ def rt_tof_adjoint(prob: Problem, theta: torch.Tensor, g_tof: torch.Tensor, ds: 
 
 
 def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
-                   ctx: Optional[Context] = None, stream=None):
+                   ctx: Optional[Context] = None, stream=None, integrator: str = "rk4"):
     """Explicit CSR system matrix (row_ptr int64, col int32, val float64) with
     T = L s, s = 1000/c; duplicate (row, col) entries sum."""
     ctx = ctx or default_context(prob.c.device.index)
@@ -187,7 +192,7 @@ def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str
     row_ptr = torch.empty(prob.n_pairs + 1, dtype=torch.int64, device=dev)
     nnz = C.c_int64(0)
     ps = prob.struct()
-    o = _opts(ds, precision=precision)
+    o = _opts(ds, precision=precision, integrator=integrator)
     th = theta.contiguous()
     rc = ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), None, None, 0,
                                 C.byref(nnz), _stream(stream))
@@ -272,7 +277,7 @@ class BatchInstance:
 def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
                  fan_rays: int = DEFAULT_FAN, block_threads: int = 0, step_unroll: int = 0,
                  blocks_per_sm: int = 0, ctx: Optional[Context] = None, stream=None,
-                 reset_angles: bool = True):
+                 reset_angles: bool = True, integrator: str = "rk4"):
     """Link (and, where tof_ref is set, adjoint-scatter) every pair of every
     instance in one persistent launch. reset_angles=True starts cold (NaN)."""
     ctx = ctx or default_context(instances[0].prob.c.device.index)
@@ -280,7 +285,7 @@ def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, pr
         for b in instances:
             b.theta.fill_(float("nan"))
     arr = (_L.RtInstance * len(instances))(*[b.struct() for b in instances])
-    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll, blocks_per_sm)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll, blocks_per_sm, integrator)
     _L.check(ctx.h, ctx.lib.rt_batch_run(ctx.h, len(instances), arr, C.byref(o), _stream(stream)))
     return instances
 

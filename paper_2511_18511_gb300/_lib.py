@@ -33,7 +33,7 @@ class RtGrid(C.Structure):
 class RtOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("ds_mm", C.c_double),
                 ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("block_threads", C.c_int32),
-                ("step_unroll", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("step_unroll", C.c_int32), ("blocks_per_sm", C.c_int32), ("integrator", C.c_int32)]
 
 
 class RtProblem(C.Structure):

@@ -50,6 +50,7 @@ int check_options(rt_ctx* ctx, const rt_options* o, bool need_link) {
     if (!(o->ds_mm > 0) || !std::isfinite(o->ds_mm)) return fail(ctx, RT_EINVAL, "ds_mm must be > 0");
     if (need_link && !(o->tol_mm > 0)) return fail(ctx, RT_EINVAL, "tol_mm must be > 0");
     if (need_link && o->max_iter < 2) return fail(ctx, RT_EINVAL, "max_iter must be >= 2");
+    if (o->integrator != RT_RK4 && o->integrator != RT_HEUN) return fail(ctx, RT_EINVAL, "unknown integrator");
     return RT_OK;
 }
 
@@ -123,6 +124,7 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     G->y0 = g.y0_mm;
     G->R = R;
     G->inv_R2 = 1.0 / (R * R);
+    G->heun = o->integrator == RT_HEUN ? 1 : 0;
     G->ds = o->ds_mm;
     const double ox = -g.x0_mm / g.h_mm, oy = -g.y0_mm / g.h_mm;
     G->Ox = (int)std::floor(ox);

@@ -52,6 +52,7 @@ struct Geom {
     int nx, ny;
     double h, x0, y0, R;
     double inv_R2;          // 1 / R^2
+    int heun;               // 1: Heun's second-order Runge-Kutta, 0: classic RK4
     double ds;              // mm
     int Ox, Oy;             // floor of the ring centre in cell coordinates (-x0/h, -y0/h)
     double oxf, oyf;        // fractional parts of the ring centre
@@ -303,6 +304,46 @@ __device__ __forceinline__ void rk4_step(Cell<T>& C, const RayState<T>& S, T H, 
     N.fy = nfy;
 }
 
+// One step of Heun's second-order Runge-Kutta method (the slopes at S and at
+// the Euler end point S + H (d, k1), averaged), in the same cell-unit,
+// compensated form as rk4_step.
+template <typename T>
+__device__ __forceinline__ void heun_step(Cell<T>& C, const RayState<T>& S, T H, RayState<T>& N, T& s_here,
+                                          T& tx1, T& ty1, int& i1, int& j1) {
+    const T Hh = (T)0.5 * H;
+    const T dx = S.d.hx(), dy = S.d.hy();
+    T c, gx, gy, tx, ty, k1x, k1y, k2x, k2y;
+    C.at(S.ci, S.cj, S.fx, S.fy, c, gx, gy, tx1, ty1);
+    i1 = C.pi;
+    j1 = C.pj;
+    s_here = C.slow(tx1, ty1);
+    ray_rhs(c, gx, gy, dx, dy, k1x, k1y);
+    const T e2x = dx + H * k1x, e2y = dy + H * k1y;
+    C.at(S.ci, S.cj, S.fx + H * dx, S.fy + H * dy, c, gx, gy, tx, ty);
+    ray_rhs(c, gx, gy, e2x, e2y, k2x, k2y);
+    T nfx = S.fx, nfy = S.fy;
+    N.lx = S.lx;
+    N.ly = S.ly;
+    add_frac(nfx, N.lx, Hh * (dx + e2x) + H * S.d.lx());
+    add_frac(nfy, N.ly, Hh * (dy + e2y) + H * S.d.ly());
+    N.d = S.d;
+    N.d.add_normalize(Hh * (k1x + k2x), Hh * (k1y + k2y));
+    N.ci = S.ci;
+    N.cj = S.cj;
+    if (nfx >= (T)1) { N.ci += 1; nfx -= (T)1; } else if (nfx < (T)0) { N.ci -= 1; add_frac(nfx, N.lx, (T)1); }
+    if (nfy >= (T)1) { N.cj += 1; nfy -= (T)1; } else if (nfy < (T)0) { N.cj -= 1; add_frac(nfy, N.ly, (T)1); }
+    N.fx = nfx;
+    N.fy = nfy;
+}
+
+// The step of the configured integrator (uniform over a launch).
+template <typename T>
+__device__ __forceinline__ void ray_step(Cell<T>& C, const Geom& G, const RayState<T>& S, T H, RayState<T>& N,
+                                         T& s_here, T& tx1, T& ty1, int& i1, int& j1) {
+    if (G.heun) heun_step(C, S, H, N, s_here, tx1, ty1, i1, j1);
+    else rk4_step(C, S, H, N, s_here, tx1, ty1, i1, j1);
+}
+
 // |x|^2 - (R/h)^2 in cell^2 units, exact integer part plus a small fractional
 // part, so the sign is reliable to ~1e-7 cell even in FP32.
 template <typename T>
@@ -428,7 +469,7 @@ __device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState
     RayState<T> N;
     T tx1, ty1;
     int i1, j1;
-    rk4_step(C, ts.S, H, N, ts.s_cur, tx1, ty1, i1, j1);
+    ray_step(C, G, ts.S, H, N, ts.s_cur, tx1, ty1, i1, j1);
     ++ts.steps;
     bool ends_out = false;
     if (--ts.safe < 0) {
@@ -503,7 +544,7 @@ __device__ TraceOut trace_end(Cell<T>& C, const Geom& G, TraceState<T>& ts, doub
     T s_dummy, txd, tyd;
     int id, jd;
     for (int it = 0; it < 2; ++it) {
-        rk4_step(C, S, (T)(t / G.h), N, s_dummy, txd, tyd, id, jd);
+        ray_step(C, G, S, (T)(t / G.h), N, s_dummy, txd, tyd, id, jd);
         ++ts.steps;
         double NX, NY;
         abs_pos(G, N, NX, NY);
@@ -513,7 +554,7 @@ __device__ TraceOut trace_end(Cell<T>& C, const Geom& G, TraceState<T>& ts, doub
         if (!(t >= 0)) t = 0;
         if (t > G.ds) t = G.ds;
     }
-    rk4_step(C, S, (T)(t / G.h), N, s_dummy, txd, tyd, id, jd);
+    ray_step(C, G, S, (T)(t / G.h), N, s_dummy, txd, tyd, id, jd);
     ++ts.steps;
     double MX, MY;
     abs_pos(G, N, MX, MY);
