@@ -202,6 +202,24 @@ int rt_path_matrix(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
  */
 int rt_status_counts(rt_ctx* ctx, int64_t counts[8], void* stream);
 
+/*
+ * rt_csr_matvec / rt_csr_rmatvec — products with a system matrix L written by
+ * rt_path_matrix (paper Sec. 3.1.1: the sparse matrix of interpolation-weighted
+ * path lengths, stored explicitly), for inversion steps that apply the matrix
+ * of one linearisation repeatedly at fixed rays (SART, conjugate gradients).
+ *   n_rows    rows of L (pairs); n_cols columns (grid nodes, ny*nx).
+ *   row_ptr   [n_rows+1] int64, col [nnz] int32, val [nnz] double (device),
+ *             as rt_path_matrix writes them; entries whose column lies outside
+ *             [0, n_cols) are skipped.
+ *   matvec:   y[n_rows] = L x, x [n_cols].
+ *   rmatvec:  y[n_cols] = L^T w, w [n_rows]; y is overwritten (FP64 atomics,
+ *             so the summation order, and the last bits, vary between calls).
+ */
+int rt_csr_matvec(rt_ctx* ctx, int32_t n_rows, int32_t n_cols, const int64_t* row_ptr, const int32_t* col,
+                  const double* val, const double* x, double* y, void* stream);
+int rt_csr_rmatvec(rt_ctx* ctx, int32_t n_rows, int32_t n_cols, const int64_t* row_ptr, const int32_t* col,
+                   const double* val, const double* w, double* y, void* stream);
+
 /* One problem of a batch: geometry plus its own outputs (device memory). */
 typedef struct {
     rt_problem prob;

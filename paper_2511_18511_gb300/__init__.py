@@ -184,14 +184,15 @@ def rt_tof_adjoint(prob: Problem, theta: torch.Tensor, g_tof: torch.Tensor, ds: 
 
 
 def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
-                   ctx: Optional[Context] = None, stream=None, integrator: str = "rk4"):
+                   ctx: Optional[Context] = None, stream=None, integrator: str = "rk4",
+                   c: Optional[torch.Tensor] = None):
     """Explicit CSR system matrix (row_ptr int64, col int32, val float64) with
     T = L s, s = 1000/c; duplicate (row, col) entries sum."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     row_ptr = torch.empty(prob.n_pairs + 1, dtype=torch.int64, device=dev)
     nnz = C.c_int64(0)
-    ps = prob.struct()
+    ps = prob.struct(c)
     o = _opts(ds, precision=precision, integrator=integrator)
     th = theta.contiguous()
     rc = ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), None, None, 0,
@@ -203,6 +204,27 @@ def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str
     _L.check(ctx.h, ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), _ptr(col),
                                            _ptr(val), nnz.value, C.byref(nnz), _stream(stream)))
     return row_ptr, col[: nnz.value], val[: nnz.value]
+
+
+def csr_matvec(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, x: torch.Tensor,
+               ctx: Optional[Context] = None, stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """y = L x for a system matrix from rt_path_matrix (x: float64 [n_cols])."""
+    ctx = ctx or default_context(x.device.index)
+    n_rows = row_ptr.numel() - 1
+    y = torch.empty(n_rows, dtype=torch.float64, device=x.device) if out is None else out
+    _L.check(ctx.h, ctx.lib.rt_csr_matvec(ctx.h, n_rows, x.numel(), _ptr(row_ptr), _ptr(col), _ptr(val),
+                                          _ptr(x.contiguous()), _ptr(y), _stream(stream)))
+    return y
+
+
+def csr_rmatvec(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, w: torch.Tensor, n_cols: int,
+                ctx: Optional[Context] = None, stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """y = L^T w for a system matrix from rt_path_matrix (w: float64 [n_rows])."""
+    ctx = ctx or default_context(w.device.index)
+    y = torch.empty(n_cols, dtype=torch.float64, device=w.device) if out is None else out
+    _L.check(ctx.h, ctx.lib.rt_csr_rmatvec(ctx.h, row_ptr.numel() - 1, int(n_cols), _ptr(row_ptr), _ptr(col),
+                                           _ptr(val), _ptr(w.contiguous()), _ptr(y), _stream(stream)))
+    return y
 
 
 def rt_status_counts(ctx: Optional[Context] = None, stream=None):

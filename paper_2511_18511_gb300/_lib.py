@@ -21,6 +21,7 @@ EXPORTED = [
     "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_ctx_reserve",
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
     "rt_tof_forward_noalloc", "rt_batch_run", "rtborn_maps", "rtborn_apply", "rtborn_adjoint",
+    "rt_csr_matvec", "rt_csr_rmatvec",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_BF16X9 = 0, 1
 
@@ -87,6 +88,8 @@ def load():
         L.rt_status_counts.argtypes = [vp, P(C.c_int64), vp]
         L.rt_tof_forward_noalloc.argtypes = [P(RtProblem), P(RtOptions), vp, vp, vp, vp]
         L.rt_batch_run.argtypes = [vp, C.c_int32, P(RtInstance), P(RtOptions), vp]
+        L.rt_csr_matvec.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp]
+        L.rt_csr_rmatvec.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp]
         L.rtborn_maps.argtypes = [vp, P(RtProblem), P(RtOptions), C.c_int32, vp, vp, vp]
         L.rtborn_apply.argtypes = [vp, P(RtGrid), C.c_double, C.c_int32, vp, vp, C.c_int32, P(C.c_double), vp,
                                    C.c_int32, vp, vp]

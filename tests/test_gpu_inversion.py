@@ -1,0 +1,64 @@
+"""Travel-time inversion on the GPU (paper Sec. 3.1): the CSR products with the
+system matrix against scipy, and a few SART / CG linearisations on the
+128^2 / 64-ring Gaussian-inclusion phantom from a homogeneous start."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("scipy.sparse")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_18511_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def case(rt):
+    from paper_2511_18511_gb300 import phantoms as P
+    w = P.cfg_small()
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
+    meas = rt.rt_link(prob, w.ds, tol=1e-6, precision="fp64")
+    return w, prob, meas["tof"].clone(), meas["theta"].clone()
+
+
+def test_csr_products_match_scipy(case, rt):
+    w, prob, _, theta = case
+    row_ptr, col, val = rt.rt_path_matrix(prob, theta, w.ds, precision="fp64")
+    n = w.grid.nx * w.grid.ny
+    A = sp.csr_matrix((val.cpu().numpy(), col.cpu().numpy(), row_ptr.cpu().numpy()), shape=(prob.n_pairs, n))
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=n)
+    wv = rng.normal(size=prob.n_pairs)
+    y = rt.csr_matvec(row_ptr, col, val, torch.as_tensor(x, device="cuda")).cpu().numpy()
+    z = rt.csr_rmatvec(row_ptr, col, val, torch.as_tensor(wv, device="cuda"), n).cpu().numpy()
+    assert np.abs(y - A @ x).max() <= 1e-12 * np.abs(A @ x).max()
+    assert np.abs(z - A.T @ wv).max() <= 1e-12 * np.abs(A.T @ wv).max()
+    # T = L s at the linked rays (the matrix rows are the travel-time weights)
+    T = rt.csr_matvec(row_ptr, col, val, (1000.0 / prob.c).reshape(-1))
+    assert float((T - case[2]).abs().max()) <= 1e-10 * float(case[2].max())
+
+
+@pytest.mark.parametrize("solver", ["sart", "cg"])
+def test_inversion_reduces_misfit_and_model_error(case, rt, solver):
+    from paper_2511_18511_gb300 import inversion as I
+    w, prob, t_meas, _ = case
+    c0 = torch.full_like(prob.c, 1500.0)
+    res = I.invert_tof(prob, t_meas, w.ds, n_lin=4, n_inner=20, solver=solver, c0=c0, damp=0.0)
+    c_true = prob.c
+    x, y = w.grid.node_xy()
+    inside = torch.as_tensor(x * x + y * y < (0.8 * w.ring_radius) ** 2, device="cuda")
+    e0 = float((c0 - c_true)[inside].norm() / (c_true[inside] - 1500.0).norm())
+    e1 = float((res.c - c_true)[inside].norm() / (c_true[inside] - 1500.0).norm())
+    print(f"[{solver}] misfit per linearisation {['%.3e' % m for m in res.misfit]}, traces {res.traces}, "
+          f"model error {e0:.3f} -> {e1:.3f}")
+    assert res.misfit[-1] <= 0.1 * res.misfit[0]
+    assert all(b <= a * 1.05 for a, b in zip(res.misfit, res.misfit[1:]))
+    assert e1 <= 0.8 * e0
