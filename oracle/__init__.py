@@ -82,6 +82,8 @@ def load(path: str):
                               C.c_double, _dp, _dp, _dp, C.c_int32]
     L.orc_num_threads.argtypes = []
     L.orc_set_integrator.argtypes = [C.c_int32]
+    L.orc_set_interpolator.argtypes = [C.c_int32]
+    L.orc_bspline_coef.argtypes = [G, _dp, _dp, C.c_int32]
     L.orc_fan_angles.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, _dp, _dp]
     L.orc_fan_ray.argtypes = [G, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                               C.c_int64, _dp, _lp]
@@ -167,6 +169,24 @@ class integrator:
         lib().orc_set_integrator(0)
 
 
+INTERPOLATORS = {"bilinear": 0, "bspline": 1}
+
+
+class interpolator:
+    """Context manager: sample the field with another interpolator ("bilinear"
+    default, "bspline": cubic B-spline with analytic gradient)."""
+
+    def __init__(self, name: str):
+        self.k = INTERPOLATORS[name]
+
+    def __enter__(self):
+        _check(lib().orc_set_interpolator(self.k), "set_interpolator")
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_interpolator(0)
+
+
 def field(grid, c_mps):
     """Nodal (c, dc/dx, dc/dy, s) in mm/us units, each [ny, nx]."""
     c = _f64(c_mps)
@@ -176,8 +196,18 @@ def field(grid, c_mps):
     return tuple(outs)
 
 
+def bspline_coef(grid, f, transpose=False):
+    """Control coefficients P^-1 f of the interpolating cubic B-spline of the
+    nodal field f[ny, nx] (P^-T f with transpose)."""
+    f = _f64(f)
+    out = np.empty_like(f)
+    g = _grid(grid)
+    _check(lib().orc_bspline_coef(C.byref(g), _d(f), _d(out), int(bool(transpose))), "bspline_coef")
+    return out
+
+
 def sample(grid, c_mps, xy):
-    """Bilinear (c, dc/dx, dc/dy, s) at points xy[n, 2] -> [n, 4]."""
+    """(c, dc/dx, dc/dy, s) at points xy[n, 2] -> [n, 4] by the current interpolator."""
     c = _f64(c_mps)
     xy = _f64(xy).reshape(-1, 2)
     out = np.empty((xy.shape[0], 4))

@@ -44,6 +44,23 @@
  *      halving; at most max_iter traces (the probe counts); the reported ray
  *      is the evaluated one closest to the receiver;
  *   R8 fan start for cold starts (optional, see link_pair_fan);
+ *   S1-S4 cubic B-spline option (orc_set_interpolator(1); Sec. 3.3.1's second
+ *      scheme, the one behind the paper's Sec. 4 experiments): S1 the spline
+ *      interpolates the nodal values: its control coefficients, one per node,
+ *      solve (a_{i-1} + 4 a_i + a_{i+1})/6 = f_i along each axis with the
+ *      mirror extension a_{-1} = a_1, a_n = a_{n-2}, and a sample weights the
+ *      4 x 4 coefficients around its cell by the uniform cubic B-spline basis
+ *      of its in-cell fractions (taking the nodal values themselves as the
+ *      coefficients would smooth the field by h^2/6 times its Laplacian,
+ *      which measured twice the bilinear error on the Sec. 4 lens, against
+ *      the paper's statement that the spline is the more accurate scheme);
+ *      S2 c and grad c are the spline of c and its exact derivative
+ *      (replacing R1); S3 the slowness of the travel time is the spline of
+ *      the nodal slowness, so T = L a_s with a_s its coefficients, the
+ *      system-matrix row holding the basis weights (16 per sample), and the
+ *      adjoint is P^-T L^T; S4 coefficient indices -1 and n fold back by the
+ *      mirror (never reached by a ring that lies inside the grid with a
+ *      margin);
  *   R7 adjoint: the rays are frozen at the linked angles (Fermat: the first
  *      order path change does not move T), so the gradient is the transpose
  *      of the system matrix whose rows are interpolation-weighted path lengths
@@ -62,12 +79,16 @@ typedef struct {
     int nx, ny;
     double h, x0, y0;
     double *c, *gx, *gy, *s;
+    double *ac, *as;    /* B-spline control coefficients of c and s (S1), else NULL */
 } Field;
 
 static void field_free(Field* F) {
-    free(F->c); free(F->gx); free(F->gy); free(F->s);
+    free(F->c); free(F->gx); free(F->gy); free(F->s); free(F->ac); free(F->as);
     memset(F, 0, sizeof(*F));
 }
+
+static int g_interp;
+static int bspline_coef(int nx, int ny, const double* f, double* a, int transpose);
 
 /* R1: nodal c (mm/us), central-difference gradient, slowness. */
 static int field_make(Field* F, const orc_grid* g, const double* c_mps) {
@@ -97,12 +118,92 @@ static int field_make(Field* F, const orc_grid* g, const double* c_mps) {
             else F->gy[k] = (F->c[k + nx] - F->c[k - nx]) / (2.0 * h);
         }
     }
+    if (g_interp == 1) {
+        F->ac = malloc(n * sizeof(double));
+        F->as = malloc(n * sizeof(double));
+        if (!F->ac || !F->as || bspline_coef(nx, ny, F->c, F->ac, 0) || bspline_coef(nx, ny, F->s, F->as, 0)) {
+            field_free(F);
+            return ORC_ENOMEM;
+        }
+    }
     return ORC_OK;
 }
 
-/* Bilinear weights of the four vertices of the enclosing cell (R2 clamps). */
-typedef struct { size_t k[4]; double w[4]; } Stencil;
+/* The interpolator every sample uses: 0 = bilinear (default), 1 = cubic
+ * B-spline (readings S1-S4 in the header). */
+static int g_interp = 0;
 
+int orc_set_interpolator(int32_t k) {
+    if (k != 0 && k != 1) return ORC_EINVAL;
+    g_interp = k;
+    return ORC_OK;
+}
+
+/* S1: the interpolation matrix of one axis, (B a)_i = (a_{i-1} + 4 a_i +
+ * a_{i+1}) / 6 with the mirror extension a_{-1} = a_1, a_n = a_{n-2}: its
+ * sub- and super-diagonal entries of row i (the diagonal is 4/6). */
+static double bs_sub(int i, int n) { return i == n - 1 ? 2.0 / 6.0 : 1.0 / 6.0; }
+static double bs_sup(int i, int n) { return i == 0 ? 2.0 / 6.0 : 1.0 / 6.0; }
+
+/* Solves B x = v (or B^T x = v) in place for the strided vector v[k * st],
+ * k < n, by tridiagonal elimination (Thomas algorithm); cp: n doubles. */
+static void bs_solve_1d(int n, double* v, size_t st, int transpose, double* cp) {
+    const double dg = 4.0 / 6.0;
+    double sub, sup, m;
+    sup = transpose ? bs_sub(1, n) : bs_sup(0, n);
+    cp[0] = sup / dg;
+    v[0] = v[0] / dg;
+    for (int i = 1; i < n; ++i) {
+        sub = transpose ? bs_sup(i - 1, n) : bs_sub(i, n);
+        sup = (i + 1 < n) ? (transpose ? bs_sub(i + 1, n) : bs_sup(i, n)) : 0.0;
+        m = dg - sub * cp[i - 1];
+        cp[i] = sup / m;
+        v[(size_t)i * st] = (v[(size_t)i * st] - sub * v[(size_t)(i - 1) * st]) / m;
+    }
+    for (int i = n - 2; i >= 0; --i) v[(size_t)i * st] -= cp[i] * v[(size_t)(i + 1) * st];
+}
+
+/* S1: control coefficients a = P^-1 f of the 2D interpolating spline (P =
+ * B_y (x) B_x, one axis after the other); transpose = 1 applies P^-T. */
+static int bspline_coef(int nx, int ny, const double* f, double* a, int transpose) {
+    double* cp = malloc((size_t)(nx > ny ? nx : ny) * sizeof(double));
+    if (!cp) return ORC_ENOMEM;
+    memcpy(a, f, (size_t)nx * ny * sizeof(double));
+    for (int j = 0; j < ny; ++j) bs_solve_1d(nx, a + (size_t)j * nx, 1, transpose, cp);
+    for (int i = 0; i < nx; ++i) bs_solve_1d(ny, a + i, (size_t)nx, transpose, cp);
+    free(cp);
+    return ORC_OK;
+}
+
+/* Nodes and weights of one sample: n = 4 (bilinear) or 16 (B-spline); wx, wy
+ * are the weights of the analytic derivative d/dx, d/dy (B-spline only). For
+ * the B-spline the k[] index the control coefficients (one per node). */
+typedef struct { int n; size_t k[16]; double w[16], wx[16], wy[16]; } Stencil;
+
+/* S1: uniform cubic B-spline basis at t in [0, 1): the weights of coefficients
+ * i-1, i, i+1, i+2 of a cell spanning nodes i..i+1, and their derivatives d/dt. */
+static void bspline_basis(double t, double b[4], double db[4]) {
+    const double u = 1.0 - t;
+    b[0] = u * u * u / 6.0;
+    b[1] = (3.0 * t * t * t - 6.0 * t * t + 4.0) / 6.0;
+    b[2] = (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) / 6.0;
+    b[3] = t * t * t / 6.0;
+    db[0] = -u * u / 2.0;
+    db[1] = (3.0 * t * t - 4.0 * t) / 2.0;
+    db[2] = (-3.0 * t * t + 2.0 * t + 1.0) / 2.0;
+    db[3] = t * t / 2.0;
+}
+
+/* S4: coefficient index -1 or n folds back by the mirror extension. */
+static int mirror(int v, int n) {
+    if (v < 0) v = -v;
+    if (v > n - 1) v = 2 * (n - 1) - v;
+    return v;
+}
+
+/* The enclosing cell (R2 clamps) and the sample's weights: the four vertices
+ * bilinearly, or (S1, S4) the 4 x 4 coefficients around the cell by the
+ * B-spline basis. */
 static void stencil_at(const Field* F, double x, double y, Stencil* S) {
     double u = (x - F->x0) / F->h, v = (y - F->y0) / F->h;
     double fi = floor(u), fj = floor(v);
@@ -112,22 +213,49 @@ static void stencil_at(const Field* F, double x, double y, Stencil* S) {
     if (fj > F->ny - 2) fj = F->ny - 2;
     int i = (int)fi, j = (int)fj;
     double tx = u - i, ty = v - j;
+    if (g_interp == 1) {
+        double bx[4], dbx[4], by[4], dby[4];
+        bspline_basis(tx, bx, dbx);
+        bspline_basis(ty, by, dby);
+        S->n = 16;
+        for (int b = 0; b < 4; ++b) {
+            const size_t row = (size_t)mirror(j - 1 + b, F->ny) * F->nx;
+            for (int a = 0; a < 4; ++a) {
+                const int q = 4 * b + a;
+                S->k[q] = row + (size_t)mirror(i - 1 + a, F->nx);
+                S->w[q] = bx[a] * by[b];
+                S->wx[q] = dbx[a] * by[b] / F->h;
+                S->wy[q] = bx[a] * dby[b] / F->h;
+            }
+        }
+        return;
+    }
+    S->n = 4;
     S->k[0] = (size_t)j * F->nx + i;        S->w[0] = (1 - tx) * (1 - ty);
     S->k[1] = S->k[0] + 1;                  S->w[1] = tx * (1 - ty);
     S->k[2] = S->k[0] + F->nx;              S->w[2] = (1 - tx) * ty;
     S->k[3] = S->k[2] + 1;                  S->w[3] = tx * ty;
 }
 
-/* f = (c, dc/dx, dc/dy, s) at (x, y). */
+/* f = (c, dc/dx, dc/dy, s) at (x, y): bilinear with R1's nodal gradient, or
+ * (S2, S3) the splines of c and s with the spline's own gradient. */
 static void sample(const Field* F, double x, double y, double f[4]) {
     Stencil S;
     stencil_at(F, x, y, &S);
     f[0] = f[1] = f[2] = f[3] = 0;
-    for (int q = 0; q < 4; ++q) {
-        f[0] += S.w[q] * F->c[S.k[q]];
-        f[1] += S.w[q] * F->gx[S.k[q]];
-        f[2] += S.w[q] * F->gy[S.k[q]];
-        f[3] += S.w[q] * F->s[S.k[q]];
+    for (int q = 0; q < S.n; ++q) {
+        const size_t k = S.k[q];
+        if (g_interp == 1) {
+            f[0] += S.w[q] * F->ac[k];
+            f[1] += S.wx[q] * F->ac[k];
+            f[2] += S.wy[q] * F->ac[k];
+            f[3] += S.w[q] * F->as[k];
+        } else {
+            f[0] += S.w[q] * F->c[k];
+            f[1] += S.w[q] * F->gx[k];
+            f[2] += S.w[q] * F->gy[k];
+            f[3] += S.w[q] * F->s[k];
+        }
     }
 }
 
@@ -587,6 +715,11 @@ int orc_field(const orc_grid* g, const double* c_mps, double* c, double* gx, dou
     return ORC_OK;
 }
 
+int orc_bspline_coef(const orc_grid* g, const double* f, double* a, int32_t transpose) {
+    if (!g || !f || !a || g->nx < 3 || g->ny < 3) return ORC_EINVAL;
+    return bspline_coef(g->nx, g->ny, f, a, transpose ? 1 : 0);
+}
+
 int orc_sample(const orc_grid* g, const double* c_mps, int32_t n, const double* xy, double* out) {
     Field F;
     int rc = field_make(&F, g, c_mps);
@@ -717,7 +850,7 @@ int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* 
 }
 
 /* One row of L: (node, weight) entries of every sample point, sorted by node
- * and merged. Returns the entry count; ent holds 4 * n_pts slots. */
+ * and merged. Returns the entry count; ent holds 16 * n_pts slots. */
 typedef struct { int64_t node; double w; } Entry;
 
 static int cmp_entry(const void* a, const void* b) {
@@ -731,7 +864,7 @@ static int64_t build_row(const Field* F, const double* pts, const double* alpha,
     for (int64_t m = 0; m < n_pts; ++m) {
         Stencil S;
         stencil_at(F, pts[2 * m], pts[2 * m + 1], &S);
-        for (int q = 0; q < 4; ++q) { ent[n].node = (int64_t)S.k[q]; ent[n].w = alpha[m] * S.w[q]; ++n; }
+        for (int q = 0; q < S.n; ++q) { ent[n].node = (int64_t)S.k[q]; ent[n].w = alpha[m] * S.w[q]; ++n; }
     }
     qsort(ent, (size_t)n, sizeof(Entry), cmp_entry);
     int64_t out = 0;
@@ -757,7 +890,7 @@ int64_t orc_path_matrix(const orc_grid* g, const double* c_mps, int32_t n_tx, co
     {
         double* pts = malloc((size_t)pcap * 2 * sizeof(double));
         double* alpha = malloc((size_t)pcap * sizeof(double));
-        Entry* ent = malloc((size_t)pcap * 4 * sizeof(Entry));
+        Entry* ent = malloc((size_t)pcap * 16 * sizeof(Entry));
 #pragma omp for schedule(dynamic, 8)
         for (int32_t k = 0; k < n_pairs; ++k) {
             int e, r;
@@ -780,7 +913,7 @@ int64_t orc_path_matrix(const orc_grid* g, const double* c_mps, int32_t n_tx, co
     {
         double* pts = malloc((size_t)pcap * 2 * sizeof(double));
         double* alpha = malloc((size_t)pcap * sizeof(double));
-        Entry* ent = malloc((size_t)pcap * 4 * sizeof(Entry));
+        Entry* ent = malloc((size_t)pcap * 16 * sizeof(Entry));
 #pragma omp for schedule(dynamic, 8)
         for (int32_t k = 0; k < n_pairs; ++k) {
             int e, r;
@@ -835,7 +968,7 @@ int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const doub
             for (int64_t m = 0; m < res.n_pts; ++m) {
                 Stencil S;
                 stencil_at(&F, pts[2 * m], pts[2 * m + 1], &S);
-                for (int q = 0; q < 4; ++q) gs[S.k[q]] += g_tof[k] * alpha[m] * S.w[q];
+                for (int q = 0; q < S.n; ++q) gs[S.k[q]] += g_tof[k] * alpha[m] * S.w[q];
             }
         }
         free(pts); free(alpha);
@@ -843,8 +976,13 @@ int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const doub
     for (size_t j = 0; j < nn; ++j) {
         double sum = 0.0;
         for (int t = 0; t < nt; ++t) sum += acc[(size_t)t * nn + j];
+        acc[j] = sum;
+    }
+    /* S3: T = L (P^-1 s) for the B-spline, so d/ds = P^-T (L^T g) */
+    if (g_interp == 1 && bspline_coef(F.nx, F.ny, acc, acc, 1)) bad = 1;
+    for (size_t j = 0; j < nn; ++j) {
         /* s = 1000 / c_mps (us/mm)  =>  ds/dc = -1000 / c_mps^2 */
-        g_c[j] = -1000.0 * sum / (c_mps[j] * c_mps[j]);
+        g_c[j] = -1000.0 * acc[j] / (c_mps[j] * c_mps[j]);
     }
     free(acc);
     field_free(&F);

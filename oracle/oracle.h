@@ -8,7 +8,9 @@
  * The oracle follows the paper (arXiv:2511.18511) step by step:
  *   - the field and its gradient live on grid nodes and are sampled off-grid by
  *     bilinear interpolation, the gradient being interpolated from grid values
- *     (Sec. 3.3.1, "Bilinear interpolation");
+ *     (Sec. 3.3.1, "Bilinear interpolation"), or optionally by a cubic B-spline
+ *     whose control points sit at the nodes, with the analytic gradient
+ *     (Sec. 3.3.1, "Cubic B-spline interpolation");
  *   - rays evolve position x and unit direction d from the sound speed and its
  *     gradient (Sec. 3.2.3; the eikonal/Fermat model of the Appendix), marched
  *     with classic RK4 at a fixed step ds;
@@ -43,7 +45,8 @@ enum { ORC_RAY_OK = 0, ORC_RAY_MAXITER = 1, ORC_RAY_STEPCAP = 2, ORC_RAY_BADINPU
  * one-sided at the edges) and slowness s = 1/c. */
 int orc_field(const orc_grid* g, const double* c_mps, double* c, double* gx, double* gy, double* s);
 
-/* Bilinear samples of (c, dc/dx, dc/dy, s) at n points xy[2n]; out[4n]. */
+/* Samples of (c, dc/dx, dc/dy, s) at n points xy[2n] by the current
+ * interpolator; out[4n]. */
 int orc_sample(const orc_grid* g, const double* c_mps, int32_t n, const double* xy, double* out);
 
 /* n_steps fixed RK4 steps of size ds from (x, y) at angle theta; writes the
@@ -75,15 +78,18 @@ int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* 
             double R, int32_t n_pairs, const int32_t* pairs, double ds, const double* theta,
             double* tof, double* hit_xy, int32_t nthreads);
 
-/* Explicit CSR system matrix L (rows = pairs, cols = nodes), T = L s.
- * Returns nnz (>= 0) or -1 on error. With col == NULL only counts. */
+/* Explicit CSR system matrix L (rows = pairs, cols = nodes), T = L s; with
+ * the B-spline the columns are the slowness spline's control coefficients,
+ * T = L a_s with a_s = orc_bspline_coef(s). Returns nnz (>= 0) or -1 on
+ * error. With col == NULL only counts. Rows may repeat a column. */
 int64_t orc_path_matrix(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
                         double R, int32_t n_pairs, const int32_t* pairs, double ds,
                         const double* theta, int64_t* row_ptr, int32_t* col, double* val,
                         int64_t cap, int32_t nthreads);
 
 /* Adjoint: g_c[node] = d(sum_i g_tof[i] T_i)/d c_node in us/(m/s) with the
- * rays frozen at theta, i.e. -(L^T g)_j * 1000 / c_j^2. */
+ * rays frozen at theta, i.e. -(L^T g)_j * 1000 / c_j^2 (B-spline:
+ * -(P^-T L^T g)_j * 1000 / c_j^2). */
 int orc_adjoint(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
                 double R, int32_t n_pairs, const int32_t* pairs, double ds, const double* theta,
                 const double* g_tof, double* g_c, int32_t nthreads);
@@ -93,6 +99,18 @@ int orc_num_threads(void);
 /* Integrator of every later trace (process-wide): 0 = classic RK4 (default),
  * 1 = Heun's second-order Runge-Kutta. Returns ORC_EINVAL for other values. */
 int orc_set_integrator(int32_t k);
+
+/* Interpolator of every later sample, trace, matrix row and adjoint
+ * (process-wide): 0 = bilinear with interpolated nodal gradient (default),
+ * 1 = interpolating cubic B-spline with control points at the nodes and
+ * analytic gradient (Sec. 3.3.1). Returns ORC_EINVAL for other values. */
+int orc_set_interpolator(int32_t k);
+
+/* Control coefficients a = P^-1 f of the interpolating cubic B-spline of the
+ * nodal field f[ny*nx] (mirror boundary; P is the spline's value at the nodes,
+ * one tridiagonal (1, 4, 1)/6 factor per axis), or a = P^-T f with transpose.
+ * a may alias f. */
+int orc_bspline_coef(const orc_grid* g, const double* f, double* a, int32_t transpose);
 
 /* ---- ray-Born (born.c) ------------------------------------------------ */
 

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_born_pins as bpins
+from tests import test_oracle_bspline_pins as spins
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -34,12 +35,12 @@ MUTANTS = {
                     "next = ok ? cur.theta + cur.m * (cur.theta - prev.theta) / den : 0.0;"),
     "orientation_probe_flipped": ("const int ccw = (ep.m / R + psi_r) < M_PI;",
                                   "const int ccw = (ep.m / R + psi_r) > M_PI;"),
-    "adjoint_missing_chain": ("g_c[j] = -1000.0 * sum / (c_mps[j] * c_mps[j]);",
-                              "g_c[j] = -1000.0 * sum / c_mps[j];"),
+    "adjoint_missing_chain": ("g_c[j] = -1000.0 * acc[j] / (c_mps[j] * c_mps[j]);",
+                              "g_c[j] = -1000.0 * acc[j] / c_mps[j];"),
     "adjoint_drop_alpha": ("gs[S.k[q]] += g_tof[k] * alpha[m] * S.w[q];",
                            "gs[S.k[q]] += g_tof[k] * S.w[q];"),
     "speed_units": ("F->c[k] = v * 1e-3;", "F->c[k] = v * 1e-2;"),
-    "slowness_uses_c": ("f[3] += S.w[q] * F->s[S.k[q]];", "f[3] += S.w[q] * F->c[S.k[q]];"),
+    "slowness_uses_c": ("f[3] += S.w[q] * F->s[k];", "f[3] += S.w[q] * F->c[k];"),
     "heun_end_slope_only": ("out[q] = st[q] + 0.5 * hs * (k1[q] + k2[q]);", "out[q] = st[q] + hs * k2[q];"),
 }
 
@@ -58,6 +59,49 @@ PINS = [
     pins.test_fisheye_ring_closed_form_converges_h2,
     pins.test_adjoint_matches_central_differences,
 ]
+
+
+BSPLINE_MUTANTS = {
+    "bspline_basis_weight": ("b[1] = (3.0 * t * t * t - 6.0 * t * t + 4.0) / 6.0;",
+                             "b[1] = (3.0 * t * t * t - 6.0 * t * t + 3.0) / 6.0;"),
+    "bspline_basis_swapped": ("b[2] = (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) / 6.0;",
+                              "b[2] = (-3.0 * t * t * t + 3.0 * t * t - 3.0 * t + 1.0) / 6.0;"),
+    "bspline_derivative_no_h": ("S->wx[q] = dbx[a] * by[b] / F->h;", "S->wx[q] = dbx[a] * by[b];"),
+    "bspline_derivative_wrong_axis": ("S->wy[q] = bx[a] * dby[b] / F->h;", "S->wy[q] = dbx[a] * by[b] / F->h;"),
+    "bspline_boundary_not_mirrored": ("static double bs_sup(int i, int n) { return i == 0 ? 2.0 / 6.0 : 1.0 / 6.0; }",
+                                      "static double bs_sup(int i, int n) { return i == 0 ? 1.0 / 6.0 : 1.0 / 6.0; }"),
+    "bspline_prefilter_x_only": ("for (int i = 0; i < nx; ++i) bs_solve_1d(ny, a + i, (size_t)nx, transpose, cp);",
+                                 ";"),
+    "bspline_index_clamped": ("if (v > n - 1) v = 2 * (n - 1) - v;", "if (v > n - 1) v = n - 1;"),
+    "bspline_slowness_from_c": ("f[3] += S.w[q] * F->as[k];", "f[3] += S.w[q] / F->ac[k];"),
+    "bspline_adjoint_not_transposed": ("if (g_interp == 1 && bspline_coef(F.nx, F.ny, acc, acc, 1)) bad = 1;",
+                                       "if (g_interp == 1 && bspline_coef(F.nx, F.ny, acc, acc, 0)) bad = 1;"),
+    "bspline_adjoint_no_prefilter": ("if (g_interp == 1 && bspline_coef(F.nx, F.ny, acc, acc, 1)) bad = 1;",
+                                     "if (0 && bspline_coef(F.nx, F.ny, acc, acc, 1)) bad = 1;"),
+    "bspline_transpose_sub": ("sub = transpose ? bs_sup(i - 1, n) : bs_sub(i, n);",
+                              "sub = transpose ? bs_sup(i, n) : bs_sub(i, n);"),
+}
+
+
+def _in_bspline(pin):
+    def run(orc):
+        with orc.interpolator("bspline"):
+            pin(orc)
+    return run
+
+
+BSPLINE_PINS = [_in_bspline(p) for p in (
+    spins.test_bspline_coefficients,
+    spins.test_bspline_samples_match_scipy_everywhere,
+    spins.test_bspline_reproduces_cubics_with_exact_gradient,
+    spins.test_bspline_is_c2_across_cell_edges,
+    spins.test_bspline_gradient_is_the_derivative_of_the_value,
+    spins.test_bspline_homogeneous_straight_rays,
+    spins.test_bspline_path_matrix_and_adjoint,
+    lambda orc: spins.test_bspline_linear_gradient_closed_form(orc, 1.0),
+    spins.test_bspline_paper_radius_experiment,
+    spins.test_bspline_fisheye_ring_closed_form,
+)]
 
 
 BORN_MUTANTS = {
@@ -136,6 +180,14 @@ def test_mutant_is_caught(name, tmp_path):
     old, new = MUTANTS[name]
     L = _compile_mutant(tmp_path, name, "oracle.c", old, new)
     if _survives(L, PINS):
+        pytest.fail(f"mutant {name} survived every pin")
+
+
+@pytest.mark.parametrize("name", sorted(BSPLINE_MUTANTS))
+def test_bspline_mutant_is_caught(name, tmp_path):
+    old, new = BSPLINE_MUTANTS[name]
+    L = _compile_mutant(tmp_path, name, "oracle.c", old, new)
+    if _survives(L, BSPLINE_PINS):
         pytest.fail(f"mutant {name} survived every pin")
 
 
