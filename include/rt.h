@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define RT_ABI_VERSION 1
+#define RT_ABI_VERSION 2   /* 2: rt_options.interpolator, rt_bspline_coef */
 
 enum rt_code {
     RT_OK = 0,
@@ -73,6 +73,17 @@ enum rt_integrator {
                           at the Euler end point, averaged */
 };
 
+/* Field sampler (paper Sec. 3.3.1 offers both; bilinear is its ToF default). */
+enum rt_interpolator {
+    RT_BILINEAR = 0,   /* c, grad c (central differences at the nodes) and s = 1/c
+                          interpolated from the four vertices of the enclosing cell */
+    RT_BSPLINE = 1     /* interpolating cubic B-spline: control coefficients, one per
+                          node, solve (a[i-1] + 4 a[i] + a[i+1])/6 = f[i] per axis with
+                          the mirror extension a[-1] = a[1], a[n] = a[n-2]; c and its
+                          analytic gradient from the spline of c, s from the spline
+                          of the nodal s; 4 x 4 coefficients per sample */
+};
+
 typedef struct {
     int32_t nx, ny;      /* nodes per axis, >= 3 */
     double h_mm;         /* node spacing */
@@ -100,6 +111,10 @@ typedef struct {
                             (128,2,4) (256,1,2) (256,1,3); FP64: (128,1,1) */
     int32_t integrator;    /* enum rt_integrator: the ray stepper of every trace of
                             the ToF calls (rtborn_maps requires RT_RK4) */
+    int32_t interpolator;  /* enum rt_interpolator: the field sampler of rt_link,
+                            rt_tof_forward, rt_tof_adjoint and rt_path_matrix
+                            (rt_batch_run, rt_tof_forward_noalloc and the rtborn_*
+                            calls require RT_BILINEAR) */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
@@ -172,6 +187,8 @@ int rt_tof_forward(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
  * tof_ref = measured times this is the gradient of 0.5*||T - T_ref||^2.
  *   theta [n_pairs], g_tof [n_pairs], tof_ref [n_pairs] or NULL,
  *   g_c   [ny*nx] out, in us/(m/s), FP64 (accumulated with FP64 atomics).
+ * With RT_BSPLINE the sum runs over the rows of the coefficient matrix and is
+ * mapped to the nodes by the transposed prefilter: -(1000/c^2) P^-T L^T w.
  */
 int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
                    const double* theta, const double* g_tof, const double* tof_ref,
@@ -184,7 +201,10 @@ int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
  * of (trapezoid weight * bilinear weight of node j), so that T = L s with
  * s = 1000/c (us/mm). CSR with one group of 4 entries per cell the ray visits;
  * a node shared by two visits appears twice (entries sum; column order is the
- * ray's order, not sorted).
+ * ray's order, not sorted). With RT_BSPLINE, column j is the slowness spline's
+ * control coefficient at node j and L_ij sums (trapezoid weight * B-spline
+ * basis weight), 16 entries per cell visit, so that T = L a_s with
+ * a_s = rt_bspline_coef(s).
  *   row_ptr   [n_pairs+1] int64 out (always written).
  *   col, val  [capacity] out; filled only when capacity >= nnz.
  *   nnz_out   HOST int64 out: number of entries. The call synchronises the
@@ -201,6 +221,19 @@ int rt_path_matrix(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
  * when every pair linked, RT_ENOCONV otherwise.
  */
 int rt_status_counts(rt_ctx* ctx, int64_t counts[8], void* stream);
+
+/*
+ * rt_bspline_coef — control coefficients of the interpolating cubic B-spline
+ * of a nodal field (paper Sec. 3.3.1, the spline defined by control points at
+ * the grid nodes): a = P^-1 f, P = B_y (x) B_x the spline's values at the nodes,
+ * B the (1, 4, 1)/6 tridiagonal matrix of one axis with the mirror extension;
+ * with transpose != 0, a = P^-T f (the adjoint's map back to the nodes).
+ * Recursive filtering along x, then y, in FP64.
+ *   f, a   device [ny*nx] FP64; a == f filters in place (no partial overlap).
+ * Errors: RT_EINVAL for nx or ny < 3 or null pointers.
+ */
+int rt_bspline_coef(rt_ctx* ctx, int32_t nx, int32_t ny, const double* f, double* a, int32_t transpose,
+                    void* stream);
 
 /*
  * rt_csr_matvec / rt_csr_rmatvec — products with a system matrix L written by

@@ -24,6 +24,7 @@ __all__ = ["Context", "Problem", "rt_link", "rt_tof_forward", "rt_tof_adjoint", 
 
 PRECISIONS = {"fp64": _L.RT_FP64, "fp32c": _L.RT_FP32_COMP}
 INTEGRATORS = {"rk4": 0, "heun": 1}
+INTERPOLATORS = {"bilinear": 0, "bspline": 1}
 
 
 class Context:
@@ -112,24 +113,28 @@ DEFAULT_FAN = 256
 
 
 def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, block_threads=0,
-          step_unroll=0, blocks_per_sm=0, integrator="rk4") -> _L.RtOptions:
+          step_unroll=0, blocks_per_sm=0, integrator="rk4", interpolator="bilinear") -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
     if integrator not in INTEGRATORS:
         raise ValueError(f"integrator must be one of {sorted(INTEGRATORS)}")
+    if interpolator not in INTERPOLATORS:
+        raise ValueError(f"interpolator must be one of {sorted(INTERPOLATORS)}")
     return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays),
-                        int(block_threads), int(step_unroll), int(blocks_per_sm), INTEGRATORS[integrator])
+                        int(block_threads), int(step_unroll), int(blocks_per_sm), INTEGRATORS[integrator],
+                        INTERPOLATORS[interpolator])
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
             theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
             ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
-            fan_rays: int = DEFAULT_FAN, integrator: str = "rk4") -> dict:
+            fan_rays: int = DEFAULT_FAN, integrator: str = "rk4", interpolator: str = "bilinear") -> dict:
     """Link every pair (shooting method, paper Sec. 3.4) and return the linked
     angles, travel times (us), interceptions (mm), per-pair status and traces.
     Cold starts (theta0 None / NaN) use a fan of fan_rays rays per emitter, or
     the straight line to the receiver with fan_rays = 0. integrator: "rk4" or
-    "heun" (the paper's default stepper)."""
+    "heun" (the paper's default stepper); interpolator: "bilinear" or "bspline"
+    (the interpolating cubic B-spline, Sec. 3.3.1)."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     n = prob.n_pairs
@@ -144,7 +149,7 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     else:
         out["theta"].copy_(theta0)
     ps = prob.struct(c)
-    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator, interpolator=interpolator)
     _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                     _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
     return out
@@ -152,14 +157,14 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
 
 def rt_tof_forward(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
                    c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None,
-                   integrator: str = "rk4"):
+                   integrator: str = "rk4", interpolator: str = "bilinear"):
     """Travel time and interception of every pair at fixed launch angles."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     tof_ = torch.empty(prob.n_pairs, dtype=torch.float64, device=dev)
     hit = torch.empty((prob.n_pairs, 2), dtype=torch.float64, device=dev)
     ps = prob.struct(c)
-    o = _opts(ds, precision=precision, integrator=integrator)
+    o = _opts(ds, precision=precision, integrator=integrator, interpolator=interpolator)
     _L.check(ctx.h, ctx.lib.rt_tof_forward(ctx.h, C.byref(ps), C.byref(o), _ptr(theta.contiguous()), _ptr(tof_),
                                            _ptr(hit), _stream(stream)))
     return tof_, hit
@@ -168,14 +173,15 @@ def rt_tof_forward(prob: Problem, theta: torch.Tensor, ds: float, precision: str
 def rt_tof_adjoint(prob: Problem, theta: torch.Tensor, g_tof: torch.Tensor, ds: float,
                    tof_ref: Optional[torch.Tensor] = None, precision: str = "fp32c",
                    c: Optional[torch.Tensor] = None, ctx: Optional[Context] = None, stream=None,
-                   out: Optional[torch.Tensor] = None, integrator: str = "rk4") -> torch.Tensor:
+                   out: Optional[torch.Tensor] = None, integrator: str = "rk4",
+                   interpolator: str = "bilinear") -> torch.Tensor:
     """g_c = sum_i (g_tof_i - tof_ref_i) dT_i/dc (us per m/s) with the rays
     frozen at theta: the transpose of the system matrix (paper Sec. 3.1.1)."""
     ctx = ctx or default_context(prob.c.device.index)
     cc = prob.c if c is None else c
     g = torch.empty_like(cc) if out is None else out
     ps = prob.struct(c)
-    o = _opts(ds, precision=precision, integrator=integrator)
+    o = _opts(ds, precision=precision, integrator=integrator, interpolator=interpolator)
     _L.check(ctx.h, ctx.lib.rt_tof_adjoint(ctx.h, C.byref(ps), C.byref(o), _ptr(theta.contiguous()),
                                            _ptr(g_tof.contiguous()),
                                            _ptr(None if tof_ref is None else tof_ref.contiguous()),
@@ -185,15 +191,16 @@ def rt_tof_adjoint(prob: Problem, theta: torch.Tensor, g_tof: torch.Tensor, ds: 
 
 def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",
                    ctx: Optional[Context] = None, stream=None, integrator: str = "rk4",
-                   c: Optional[torch.Tensor] = None):
+                   c: Optional[torch.Tensor] = None, interpolator: str = "bilinear"):
     """Explicit CSR system matrix (row_ptr int64, col int32, val float64) with
-    T = L s, s = 1000/c; duplicate (row, col) entries sum."""
+    T = L s, s = 1000/c; duplicate (row, col) entries sum. With the B-spline
+    the columns are the slowness spline's coefficients: T = L bspline_coef(s)."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     row_ptr = torch.empty(prob.n_pairs + 1, dtype=torch.int64, device=dev)
     nnz = C.c_int64(0)
     ps = prob.struct(c)
-    o = _opts(ds, precision=precision, integrator=integrator)
+    o = _opts(ds, precision=precision, integrator=integrator, interpolator=interpolator)
     th = theta.contiguous()
     rc = ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), None, None, 0,
                                 C.byref(nnz), _stream(stream))
@@ -204,6 +211,20 @@ def rt_path_matrix(prob: Problem, theta: torch.Tensor, ds: float, precision: str
     _L.check(ctx.h, ctx.lib.rt_path_matrix(ctx.h, C.byref(ps), C.byref(o), _ptr(th), _ptr(row_ptr), _ptr(col),
                                            _ptr(val), nnz.value, C.byref(nnz), _stream(stream)))
     return row_ptr, col[: nnz.value], val[: nnz.value]
+
+
+def bspline_coef(f: torch.Tensor, transpose: bool = False, ctx: Optional[Context] = None, stream=None,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Control coefficients P^-1 f (P^-T f with transpose) of the interpolating
+    cubic B-spline of a nodal field f [ny, nx] (float64 CUDA tensor)."""
+    if f.dim() != 2 or f.dtype != torch.float64 or not f.is_cuda:
+        raise ValueError("f must be a 2-D float64 CUDA tensor [ny, nx]")
+    ctx = ctx or default_context(f.device.index)
+    src = f.contiguous()
+    a = torch.empty_like(src) if out is None else out
+    _L.check(ctx.h, ctx.lib.rt_bspline_coef(ctx.h, src.shape[1], src.shape[0], _ptr(src), _ptr(a),
+                                            int(bool(transpose)), _stream(stream)))
+    return a
 
 
 def csr_matvec(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, x: torch.Tensor,

@@ -21,9 +21,10 @@ EXPORTED = [
     "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_ctx_reserve",
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
     "rt_tof_forward_noalloc", "rt_batch_run", "rtborn_maps", "rtborn_apply", "rtborn_adjoint",
-    "rt_csr_matvec", "rt_csr_rmatvec",
+    "rt_csr_matvec", "rt_csr_rmatvec", "rt_bspline_coef",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_BF16X9 = 0, 1
+ABI_VERSION = 2   # layout of RtOptions below
 
 
 class RtGrid(C.Structure):
@@ -34,7 +35,8 @@ class RtGrid(C.Structure):
 class RtOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("ds_mm", C.c_double),
                 ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("block_threads", C.c_int32),
-                ("step_unroll", C.c_int32), ("blocks_per_sm", C.c_int32), ("integrator", C.c_int32)]
+                ("step_unroll", C.c_int32), ("blocks_per_sm", C.c_int32), ("integrator", C.c_int32),
+                ("interpolator", C.c_int32)]
 
 
 class RtProblem(C.Structure):
@@ -74,6 +76,9 @@ def load():
         L = C.CDLL(_build.LIB)
         vp, P = C.c_void_p, C.POINTER
         L.rt_version.restype = C.c_int
+        if L.rt_version() != ABI_VERSION:
+            raise RuntimeError(f"{_build.LIB} has ABI version {L.rt_version()}, the binding expects {ABI_VERSION}; "
+                               "rebuild with __graft_entry__.build()")
         L.rt_ctx_create.argtypes = [P(vp), C.c_int]
         L.rt_ctx_destroy.argtypes = [vp]
         L.rt_ctx_destroy.restype = None
@@ -90,6 +95,7 @@ def load():
         L.rt_batch_run.argtypes = [vp, C.c_int32, P(RtInstance), P(RtOptions), vp]
         L.rt_csr_matvec.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp]
         L.rt_csr_rmatvec.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp]
+        L.rt_bspline_coef.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp]
         L.rtborn_maps.argtypes = [vp, P(RtProblem), P(RtOptions), C.c_int32, vp, vp, vp]
         L.rtborn_apply.argtypes = [vp, P(RtGrid), C.c_double, C.c_int32, vp, vp, C.c_int32, P(C.c_double), vp,
                                    C.c_int32, vp, vp]

@@ -51,6 +51,8 @@ int check_options(rt_ctx* ctx, const rt_options* o, bool need_link) {
     if (need_link && !(o->tol_mm > 0)) return fail(ctx, RT_EINVAL, "tol_mm must be > 0");
     if (need_link && o->max_iter < 2) return fail(ctx, RT_EINVAL, "max_iter must be >= 2");
     if (o->integrator != RT_RK4 && o->integrator != RT_HEUN) return fail(ctx, RT_EINVAL, "unknown integrator");
+    if (o->interpolator != RT_BILINEAR && o->interpolator != RT_BSPLINE)
+        return fail(ctx, RT_EINVAL, "unknown interpolator");
     return RT_OK;
 }
 
@@ -65,10 +67,25 @@ int prepare(rt_ctx* ctx, const rt_problem* p, const rt_options* o, bool need_lin
     if (rc) return rc;
     rc = set_device(ctx);
     if (rc) return rc;
-    const size_t bytes = rt::node_bytes(o->precision) * (size_t)(p->grid.nx - 1) * (size_t)(p->grid.ny - 1);
+    const size_t bytes =
+        rt::node_bytes(o->precision, o->interpolator) * (size_t)(p->grid.nx - 1) * (size_t)(p->grid.ny - 1);
     rc = ensure_field(ctx, bytes, s);
     if (rc) return rc;
-    cudaError_t e = rt::launch_pack(p->grid, p->c_mps, ctx->field, ctx->dflag, o->precision, s);
+    cudaError_t e;
+    if (o->interpolator == RT_BSPLINE) {
+        const size_t cb = 2 * sizeof(double) * (size_t)p->grid.nx * (size_t)p->grid.ny;
+        if (ctx->bs_coef_bytes < cb) {
+            if (capturing(s)) return fail(ctx, RT_EINVAL, "B-spline workspace too small during stream capture");
+            if (ctx->bs_coef) cudaFree(ctx->bs_coef);
+            ctx->bs_coef = nullptr;
+            ctx->bs_coef_bytes = 0;
+            if (cudaMalloc(&ctx->bs_coef, cb) != cudaSuccess) return fail(ctx, RT_ENOMEM, "B-spline workspace");
+            ctx->bs_coef_bytes = cb;
+        }
+        e = rt::launch_pack_bs(p->grid, p->c_mps, ctx->bs_coef, ctx->field, ctx->dflag, o->precision, s);
+    } else {
+        e = rt::launch_pack(p->grid, p->c_mps, ctx->field, ctx->dflag, o->precision, s);
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pack kernel");
     G->bad_field = ctx->dflag;
     // per-transducer polar angles (NaN = off the ring), read by every pair set-up
@@ -125,6 +142,7 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
     G->R = R;
     G->inv_R2 = 1.0 / (R * R);
     G->heun = o->integrator == RT_HEUN ? 1 : 0;
+    G->interp = o->interpolator == RT_BSPLINE ? RT_BSPLINE : RT_BILINEAR;
     G->ds = o->ds_mm;
     const double ox = -g.x0_mm / g.h_mm, oy = -g.y0_mm / g.h_mm;
     G->Ox = (int)std::floor(ox);
@@ -184,6 +202,7 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->field) cudaFree(ctx->field);
+    if (ctx->bs_coef) cudaFree(ctx->bs_coef);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->dflag) cudaFree(ctx->dflag);
     if (ctx->queue) cudaFree(ctx->queue);

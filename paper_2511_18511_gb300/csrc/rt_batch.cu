@@ -298,6 +298,8 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
     if (!(opt->ds_mm > 0) || !(opt->tol_mm > 0) || opt->max_iter < 2)
         return rt::set_error(ctx, RT_EINVAL, "ds_mm and tol_mm must be > 0, max_iter >= 2");
     if (opt->integrator != RT_RK4 && opt->integrator != RT_HEUN) return rt::set_error(ctx, RT_EINVAL, "unknown integrator");
+    if (opt->interpolator != RT_BILINEAR)
+        return rt::set_error(ctx, RT_EINVAL, "rt_batch_run samples bilinearly (interpolator RT_BILINEAR)");
     if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536)
         return rt::set_error(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
     const int block = opt->block_threads ? opt->block_threads : 128;

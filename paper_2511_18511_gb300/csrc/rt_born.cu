@@ -567,6 +567,8 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     if (!(opt->ds_mm > 0) || !std::isfinite(opt->ds_mm)) return bfail(ctx, RT_EINVAL, "ds_mm must be > 0");
     if (fan_rays < 2 || fan_rays > (1 << 20)) return bfail(ctx, RT_EINVAL, "fan_rays must be in [2, 2^20]");
     if (opt->integrator != RT_RK4) return bfail(ctx, RT_EINVAL, "fan maps are traced with RK4 (integrator RT_RK4)");
+    if (opt->interpolator != RT_BILINEAR)
+        return bfail(ctx, RT_EINVAL, "fan maps sample the field bilinearly (interpolator RT_BILINEAR)");
     if (!T_out || !A_out) return bfail(ctx, RT_EINVAL, "T and A outputs are required");
     if (opt->ds_mm > (prob ? prob->grid.h_mm : 0.0)) return bfail(ctx, RT_EINVAL, "ds_mm must not exceed the grid spacing");
     rt::Geom G;

@@ -11,8 +11,10 @@
 struct rt_ctx {
     int device = 0;
     std::string err;
-    void* field = nullptr;          // packed nodes (float4 or 32-byte double4)
+    void* field = nullptr;          // packed cells (bilinear or bicubic coefficients)
     size_t field_bytes = 0;
+    double* bs_coef = nullptr;      // [2][ny*nx] B-spline coefficients of c and s
+    size_t bs_coef_bytes = 0;
     unsigned long long* counters = nullptr;   // [8]: per-status counts, [7] RK4 steps
     int* dflag = nullptr;           // [1]: set by the pack kernel when c <= 0 or NaN
     int* queue = nullptr;           // [1]: work-queue head of the persistent linking kernel
@@ -62,7 +64,8 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G);
 int set_error(rt_ctx* ctx, int code, const std::string& msg);
 bool stream_capturing(cudaStream_t s);
 
-// Kernel launchers (rt_ray.cu). All enqueue on `s` and return a cudaError_t.
+// Kernel launchers (rt_ray.cu). All enqueue on `s` and return a cudaError_t;
+// the field layout (and kernel variant) follows G.interp.
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
                         cudaStream_t s);
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
@@ -79,9 +82,15 @@ cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const dou
 cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double* theta,
                         int64_t* row_ptr, int32_t* col, double* val, bool fill, cudaStream_t s);
 cudaError_t launch_tx_phi(const Geom& G, double* phi, cudaStream_t s);
+// B-spline sampler (rt_bspline.cu): nodal c and s -> coefficients (coef [2][ny*nx])
+// -> per-cell bicubics in `field`; the line filter of nf planes (transpose: P^-T).
+cudaError_t launch_pack_bs(const rt_grid& g, const double* c_mps, double* coef, void* field, int* dflag, int prec,
+                           cudaStream_t s);
+cudaError_t launch_bs_filter(double* f, int nx, int ny, int nf, bool transpose, cudaStream_t s);
 cudaError_t launch_scan(int64_t* row_ptr, int n, void* tmp, size_t* tmp_bytes, cudaStream_t s);
 
-size_t node_bytes(int prec);
+// bytes per packed cell for a precision and interpolator
+size_t node_bytes(int prec, int interp = RT_BILINEAR);
 
 // Releases the context's cuBLAS handle (rt_born.cu).
 void destroy_blas(void* handle);

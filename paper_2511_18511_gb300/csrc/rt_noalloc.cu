@@ -44,6 +44,7 @@ extern "C" int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* 
     if (!prob || !opt) return RT_EINVAL;
     if (opt->precision != RT_FP64 && opt->precision != RT_FP32_COMP) return RT_EINVAL;
     if (opt->integrator != RT_RK4 && opt->integrator != RT_HEUN) return RT_EINVAL;
+    if (opt->interpolator != RT_BILINEAR) return RT_EINVAL;
     if (!(opt->ds_mm > 0)) return RT_EINVAL;
     if (prob->n_pairs > 0 && (!theta || !tof_us)) return RT_EINVAL;
     rt::Geom G;

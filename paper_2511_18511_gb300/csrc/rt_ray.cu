@@ -11,6 +11,7 @@
 #include "rt_internal.h"
 #include "rt_trace.cuh"
 #include "rt_link.cuh"
+#include "rt_bspline.cuh"
 
 namespace rt {
 
@@ -18,7 +19,36 @@ constexpr int kBlock = 128;
 
 static int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
 
-size_t node_bytes(int prec) { return prec == RT_FP64 ? sizeof(CellCoef<double>) : sizeof(CellCoef<float>); }
+size_t node_bytes(int prec, int interp) {
+    if (interp == RT_BSPLINE) return prec == RT_FP64 ? sizeof(CellBS<double>) : sizeof(CellBS<float>);
+    return prec == RT_FP64 ? sizeof(CellCoef<double>) : sizeof(CellCoef<float>);
+}
+
+// Field layout and register cache of each sampler (template argument I =
+// enum rt_interpolator), and the resident blocks per SM the persistent kernels
+// are compiled for.
+template <typename T, int I> struct Samp;
+template <typename T> struct Samp<T, RT_BILINEAR> {
+    using Field = CellCoef<T>;
+    using CellT = Cell<T>;
+};
+template <typename T> struct Samp<T, RT_BSPLINE> {
+    using Field = CellBS<T>;
+    using CellT = CellS<T>;
+};
+template <typename T, int I> struct Occ { static constexpr int blocks = LinkOcc<T>::blocks; };
+template <> struct Occ<float, RT_BSPLINE> { static constexpr int blocks = 4; };
+
+template <typename T, int I>
+__device__ __forceinline__ typename Samp<T, I>::CellT make_cell(const Geom& G, const typename Samp<T, I>::Field* F) {
+    typename Samp<T, I>::CellT C;
+    C.F = F;
+    C.nx = G.nx;
+    C.ny = G.ny;
+    C.pi = INT_MIN;
+    C.pj = INT_MIN;
+    return C;
+}
 
 // ---------------------------------------------------------------- A1: field pack
 
@@ -109,8 +139,8 @@ __global__ void k_fan_mark(Geom G, const double* __restrict__ theta, int* need) 
     if (e >= 0 && e < G.n_tx && isnan(theta[k])) need[e] = 1;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fan(Geom G, const CellCoef<T>* __restrict__ F, int K,
+template <typename T, int I>
+__global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I>::Field* __restrict__ F, int K,
                                                 const int* __restrict__ need, double* fan,
                                                 unsigned long long* counters) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,8 +152,7 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const CellCoef<T>* __res
         const double margin = fmax(G.ds / G.R, 1e-9);
         const double a_min = phi_e + 0.5 * kPi + margin, a_max = phi_e + 1.5 * kPi - margin;
         const double step = (a_max - a_min) / (K - 1);
-        Cell<T> C;
-        C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+        auto C = make_cell<T, I>(G, F);
         NoSink ns;
         const TraceOut o = trace_ray<T>(C, G, xe, ye, fan_theta(a_min, step, k), xe, ye, ns);
         fan[id] = (o.flags & 3) ? nan("") : mod_2pi(atan2(o.hy, o.hx) - phi_e);
@@ -139,16 +168,15 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const CellCoef<T>* __res
 // Persistent linking kernel: each lane takes pairs from the queue, advances
 // its own trace one RK4 step per loop iteration, and updates the linking
 // state when a trace ends, so lanes never wait for other lanes' pairs.
-template <typename T>
-__global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks) k_link(Geom G, const typename NodeT<T>::type* __restrict__ F,
+template <typename T, int I>
+__global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, const typename Samp<T, I>::Field* __restrict__ F,
                                                      double tol, int max_iter, double* theta, double* tof,
                                                      double* hit, int32_t* status, int32_t* iters,
                                                      unsigned long long* counters, int* queue, int fan_rays,
                                                      const double* __restrict__ fan) {
     __shared__ LinkState sh[kLinkBlock];
     LinkState& L = sh[threadIdx.x];
-    Cell<T> C;
-    C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+    auto C = make_cell<T, I>(G, F);
     TraceState<T> ts;
     NoSink ns;
     long long steps = 0;
@@ -233,7 +261,7 @@ __global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks) k_link(Geom G,
 // Blocks of a persistent launch: resident blocks per SM x SMs (cached per slot).
 template <typename K>
 static int persistent_blocks(K kernel, int slot) {
-    static int cache[8] = {0};
+    static int cache[16] = {0};
     if (!cache[slot]) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
@@ -244,20 +272,38 @@ static int persistent_blocks(K kernel, int slot) {
     return cache[slot];
 }
 
+template <typename T, int I>
+static void fan_impl(const Geom& G, const void* field, int fan_rays, double* fan, const int* fan_need,
+                     unsigned long long* counters, cudaStream_t s) {
+    const int nf = G.n_tx * fan_rays;
+    k_fan<T, I><<<grid_for(nf), kBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, fan_rays, fan_need, fan,
+                                                counters);
+}
+
 cudaError_t launch_fan(const Geom& G, const void* field, int prec, int fan_rays, const double* theta, double* fan,
                        int* fan_need, unsigned long long* counters, cudaStream_t s) {
     if (G.n_pairs == 0 || fan_rays < 2) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(fan_need, 0, sizeof(int) * (size_t)G.n_tx, s);
     if (e != cudaSuccess) return e;
     k_fan_mark<<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, theta, fan_need);
-    const int nf = G.n_tx * fan_rays;
-    if (prec == RT_FP64)
-        k_fan<double><<<grid_for(nf), kBlock, 0, s>>>(G, (const CellCoef<double>*)field, fan_rays, fan_need, fan,
-                                                      counters);
-    else
-        k_fan<float><<<grid_for(nf), kBlock, 0, s>>>(G, (const CellCoef<float>*)field, fan_rays, fan_need, fan,
-                                                     counters);
+    const bool bs = G.interp == RT_BSPLINE;
+    if (prec == RT_FP64) {
+        if (bs) fan_impl<double, RT_BSPLINE>(G, field, fan_rays, fan, fan_need, counters, s);
+        else fan_impl<double, RT_BILINEAR>(G, field, fan_rays, fan, fan_need, counters, s);
+    } else {
+        if (bs) fan_impl<float, RT_BSPLINE>(G, field, fan_rays, fan, fan_need, counters, s);
+        else fan_impl<float, RT_BILINEAR>(G, field, fan_rays, fan, fan_need, counters, s);
+    }
     return cudaGetLastError();
+}
+
+template <typename T, int I>
+static void link_impl(const Geom& G, const void* field, double tol, int max_iter, double* theta, double* tof,
+                      double* hit, int32_t* status, int32_t* iters, unsigned long long* counters, int* queue,
+                      int fan_rays, double* fan, int slot, cudaStream_t s) {
+    const int nb = min(persistent_blocks(k_link<T, I>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+    k_link<T, I><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, tol, max_iter, theta, tof,
+                                           hit, status, iters, counters, queue, fan_rays, fan);
 }
 
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
@@ -271,22 +317,25 @@ cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, 
         e = launch_fan(G, field, prec, fan_rays, theta, fan, fan_need, counters, s);
         if (e != cudaSuccess) return e;
     }
+    const bool bs = G.interp == RT_BSPLINE;
     if (prec == RT_FP64) {
-        const int nb = min(persistent_blocks(k_link<double>, 3), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-        k_link<double><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<double>*)field, tol, max_iter, theta, tof, hit,
-                                                 status, iters, counters, queue, fan_rays, fan);
+        if (bs) link_impl<double, RT_BSPLINE>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, queue,
+                                              fan_rays, fan, 9, s);
+        else link_impl<double, RT_BILINEAR>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, queue,
+                                            fan_rays, fan, 3, s);
     } else {
-        const int nb = min(persistent_blocks(k_link<float>, 4), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-        k_link<float><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<float>*)field, tol, max_iter, theta, tof, hit,
-                                                status, iters, counters, queue, fan_rays, fan);
+        if (bs) link_impl<float, RT_BSPLINE>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, queue,
+                                             fan_rays, fan, 10, s);
+        else link_impl<float, RT_BILINEAR>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, queue,
+                                           fan_rays, fan, 4, s);
     }
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- A5: ToF at fixed angles
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_tof(Geom G, const typename NodeT<T>::type* __restrict__ F,
+template <typename T, int I>
+__global__ void __launch_bounds__(kBlock) k_tof(Geom G, const typename Samp<T, I>::Field* __restrict__ F,
                                                 const double* theta, double* tof, double* hit) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.n_pairs) return;
@@ -296,8 +345,7 @@ __global__ void __launch_bounds__(kBlock) k_tof(Geom G, const typename NodeT<T>:
         if (hit) { hit[2 * k] = nan(""); hit[2 * k + 1] = nan(""); }
         return;
     }
-    Cell<T> C;
-    C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+    auto C = make_cell<T, I>(G, F);
     NoSink ns;
     TraceOut o = trace_ray<T>(C, G, L.xe, L.ye, theta[k], L.xr, L.yr, ns);
     tof[k] = o.T;
@@ -307,10 +355,15 @@ __global__ void __launch_bounds__(kBlock) k_tof(Geom G, const typename NodeT<T>:
 cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double* theta, double* tof,
                        double* hit, cudaStream_t s) {
     if (G.n_pairs == 0) return cudaSuccess;
-    if (prec == RT_FP64)
-        k_tof<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, tof, hit);
-    else
-        k_tof<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, tof, hit);
+    const int nb = grid_for(G.n_pairs);
+    const bool bs = G.interp == RT_BSPLINE;
+    if (prec == RT_FP64) {
+        if (bs) k_tof<double, RT_BSPLINE><<<nb, kBlock, 0, s>>>(G, (const CellBS<double>*)field, theta, tof, hit);
+        else k_tof<double, RT_BILINEAR><<<nb, kBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, tof, hit);
+    } else {
+        if (bs) k_tof<float, RT_BSPLINE><<<nb, kBlock, 0, s>>>(G, (const CellBS<float>*)field, theta, tof, hit);
+        else k_tof<float, RT_BILINEAR><<<nb, kBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, tof, hit);
+    }
     return cudaGetLastError();
 }
 
@@ -318,16 +371,18 @@ cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double*
 
 // Persistent adjoint: each lane takes pairs from the queue (longest chords
 // first), retraces the ray at its angle and scatters its weights.
-template <typename T>
-__global__ void __launch_bounds__(kLinkBlock, LinkOcc<T>::blocks)
-    k_adjoint(Geom G, const CellCoef<T>* __restrict__ F, const double* theta, const double* g_tof,
+template <typename T, int I> struct AdjOf { using type = AdjSink<T>; };
+template <typename T> struct AdjOf<T, RT_BSPLINE> { using type = AdjSinkBSp<T>; };
+
+template <typename T, int I>
+__global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks)
+    k_adjoint(Geom G, const typename Samp<T, I>::Field* __restrict__ F, const double* theta, const double* g_tof,
               const double* tof_ref, double* g, int* queue) {
     __shared__ PairEnds sh[kLinkBlock];
     PairEnds& E = sh[threadIdx.x];
-    Cell<T> C;
-    C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+    auto C = make_cell<T, I>(G, F);
     TraceState<T> ts;
-    AdjSink<T> sink;
+    typename AdjOf<T, I>::type sink;
     sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
     sink.acc.reset();
     bool active = false;
@@ -360,6 +415,14 @@ __global__ void k_adjoint_finish(double* g, const double* __restrict__ c_mps, in
     }
 }
 
+template <typename T, int I>
+static void adjoint_impl(const Geom& G, const void* field, const double* theta, const double* g_tof,
+                         const double* tof_ref, double* g_c, int* queue, int slot, cudaStream_t s) {
+    const int nb = min(persistent_blocks(k_adjoint<T, I>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+    k_adjoint<T, I><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, theta, g_tof, tof_ref,
+                                              g_c, queue);
+}
+
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,
                            const double* g_tof, const double* tof_ref, const double* c_mps,
                            double* g_c, int* queue, cudaStream_t s) {
@@ -369,16 +432,20 @@ cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const dou
     if (G.n_pairs > 0) {
         e = cudaMemsetAsync(queue, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
+        const bool bs = G.interp == RT_BSPLINE;
         if (prec == RT_FP64) {
-            const int nb = min(persistent_blocks(k_adjoint<double>, 1), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-            k_adjoint<double><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, g_tof, tof_ref,
-                                                        g_c, queue);
+            if (bs) adjoint_impl<double, RT_BSPLINE>(G, field, theta, g_tof, tof_ref, g_c, queue, 11, s);
+            else adjoint_impl<double, RT_BILINEAR>(G, field, theta, g_tof, tof_ref, g_c, queue, 1, s);
         } else {
-            const int nb = min(persistent_blocks(k_adjoint<float>, 2), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-            k_adjoint<float><<<nb, kLinkBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, g_tof, tof_ref,
-                                                       g_c, queue);
+            if (bs) adjoint_impl<float, RT_BSPLINE>(G, field, theta, g_tof, tof_ref, g_c, queue, 12, s);
+            else adjoint_impl<float, RT_BILINEAR>(G, field, theta, g_tof, tof_ref, g_c, queue, 2, s);
         }
         e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // B-spline: the scatter ran over the slowness coefficients; P^-T maps it to the nodes
+    if (G.interp == RT_BSPLINE) {
+        e = launch_bs_filter(g_c, G.nx, G.ny, 1, true, s);
         if (e != cudaSuccess) return e;
     }
     const int blocks = (n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8;
@@ -427,21 +494,23 @@ struct RowSink {
     __device__ __forceinline__ void finish() { flush(); }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_rows(Geom G, const typename NodeT<T>::type* __restrict__ F,
+template <typename T, int I> struct RowsOf { using type = RowSink<T>; };
+template <typename T> struct RowsOf<T, RT_BSPLINE> { using type = RowSinkBSp<T>; };
+
+template <typename T, int I>
+__global__ void __launch_bounds__(kBlock) k_rows(Geom G, const typename Samp<T, I>::Field* __restrict__ F,
                                                  const double* theta, int64_t* row_ptr, int32_t* col,
                                                  double* val, bool fill) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.n_pairs) return;
     LinkCtx L;
-    RowSink<T> sink;
+    typename RowsOf<T, I>::type sink;
     sink.nx = G.nx; sink.ny = G.ny; sink.col = col; sink.val = val; sink.fill = fill;
     sink.pos = fill ? row_ptr[k] : 0;
     sink.end = fill ? row_ptr[k + 1] : 0;
     sink.acc.reset();
     if (setup_pair(G, k, L)) {
-        Cell<T> C;
-        C.F = F; C.nx = G.nx; C.ny = G.ny; C.pi = INT_MIN; C.pj = INT_MIN;
+        auto C = make_cell<T, I>(G, F);
         trace_ray<T>(C, G, L.xe, L.ye, theta[k], L.xr, L.yr, sink);
     }
     if (!fill) row_ptr[k + 1] = sink.pos;
@@ -450,12 +519,19 @@ __global__ void __launch_bounds__(kBlock) k_rows(Geom G, const typename NodeT<T>
 cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double* theta, int64_t* row_ptr,
                         int32_t* col, double* val, bool fill, cudaStream_t s) {
     if (G.n_pairs == 0) return cudaSuccess;
-    if (prec == RT_FP64)
-        k_rows<double><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, row_ptr, col, val,
-                                                              fill);
-    else
-        k_rows<float><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, row_ptr, col,
-                                                             val, fill);
+    const int nb = grid_for(G.n_pairs);
+    const bool bs = G.interp == RT_BSPLINE;
+    if (prec == RT_FP64) {
+        if (bs) k_rows<double, RT_BSPLINE><<<nb, kBlock, 0, s>>>(G, (const CellBS<double>*)field, theta, row_ptr, col,
+                                                                 val, fill);
+        else k_rows<double, RT_BILINEAR><<<nb, kBlock, 0, s>>>(G, (const CellCoef<double>*)field, theta, row_ptr, col,
+                                                               val, fill);
+    } else {
+        if (bs) k_rows<float, RT_BSPLINE><<<nb, kBlock, 0, s>>>(G, (const CellBS<float>*)field, theta, row_ptr, col,
+                                                                val, fill);
+        else k_rows<float, RT_BILINEAR><<<nb, kBlock, 0, s>>>(G, (const CellCoef<float>*)field, theta, row_ptr, col,
+                                                              val, fill);
+    }
     return cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ struct Geom {
     double h, x0, y0, R;
     double inv_R2;          // 1 / R^2
     int heun;               // 1: Heun's second-order Runge-Kutta, 0: classic RK4
+    int interp;             // enum rt_interpolator of the packed field
     double ds;              // mm
     int Ox, Oy;             // floor of the ring centre in cell coordinates (-x0/h, -y0/h)
     double oxf, oyf;        // fractional parts of the ring centre
@@ -112,6 +113,35 @@ __device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
 
 // ---------------------------------------------------------------- field cache
 
+// The cell (i, j) and in-cell fractions (tx, ty) of a point given by fractions
+// (u, v) relative to cell (ci, cj); returns whether (i, j) differs from the
+// cached cell (pi, pj). Stage points lie within one cell of the current one
+// when ds <= h, so the offsets come from comparisons (no conversion
+// instructions, which are slow on this part); larger offsets take the floor path.
+template <typename T>
+__device__ __forceinline__ bool cell_locate(int ci, int cj, T u, T v, int pi, int pj, int& i, int& j, T& tx,
+                                            T& ty) {
+    if (ci == pi && cj == pj && u >= (T)0 && u < (T)1 && v >= (T)0 && v < (T)1) {
+        tx = u;
+        ty = v;
+        return false;
+    }
+    if (u >= (T)-1 && u < (T)2 && v >= (T)-1 && v < (T)2) {
+        const bool ul = u < (T)0, uh = u >= (T)1, vl = v < (T)0, vh = v >= (T)1;
+        tx = ul ? u + (T)1 : (uh ? u - (T)1 : u);
+        ty = vl ? v + (T)1 : (vh ? v - (T)1 : v);
+        i = ci + (ul ? -1 : (uh ? 1 : 0));
+        j = cj + (vl ? -1 : (vh ? 1 : 0));
+    } else {
+        const T fu = floor(u), fv = floor(v);
+        i = ci + (int)fu;
+        j = cj + (int)fv;
+        tx = u - fu;
+        ty = v - fv;
+    }
+    return i != pi || j != pj;
+}
+
 template <typename T>
 struct Cell {
     using V = CellCoef<T>;
@@ -139,29 +169,8 @@ struct Cell {
 
     // (u, v): fractions relative to cell (ci, cj), possibly outside [0, 1)
     __device__ __forceinline__ void at(int ci, int cj, T u, T v, T& c, T& gx, T& gy, T& tx, T& ty) {
-        if (ci == pi && cj == pj && u >= (T)0 && u < (T)1 && v >= (T)0 && v < (T)1) {
-            tx = u;
-            ty = v;
-        } else {
-            // neighbour cell: offsets from comparisons (no conversion instructions,
-            // which are slow on this part); stage points lie within one cell of the
-            // current one when ds <= h, larger offsets take the floor path
-            int i, j;
-            if (u >= (T)-1 && u < (T)2 && v >= (T)-1 && v < (T)2) {
-                const bool ul = u < (T)0, uh = u >= (T)1, vl = v < (T)0, vh = v >= (T)1;
-                tx = ul ? u + (T)1 : (uh ? u - (T)1 : u);
-                ty = vl ? v + (T)1 : (vh ? v - (T)1 : v);
-                i = ci + (ul ? -1 : (uh ? 1 : 0));
-                j = cj + (vl ? -1 : (vh ? 1 : 0));
-            } else {
-                const T fu = floor(u), fv = floor(v);
-                i = ci + (int)fu;
-                j = cj + (int)fv;
-                tx = u - fu;
-                ty = v - fv;
-            }
-            if (i != pi || j != pj) load(i, j);
-        }
+        int i, j;
+        if (cell_locate(ci, cj, u, v, pi, pj, i, j, tx, ty)) load(i, j);
         c = ca + tx * cbx + ty * (cby + tx * cbxy);
         gx = xa + tx * xbx + ty * (xby + tx * xbxy);
         gy = ya + tx * ybx + ty * (yby + tx * ybxy);
@@ -264,8 +273,8 @@ __device__ __forceinline__ void ray_rhs(T c, T gx, T gy, T ex, T ey, T& kx, T& k
 
 // One RK4 step of length H (cell units) from S into N. s_here receives the
 // slowness at S's position (stage-1 sample) for the trapezoid rule.
-template <typename T>
-__device__ __forceinline__ void rk4_step(Cell<T>& C, const RayState<T>& S, T H, RayState<T>& N, T& s_here,
+template <typename T, typename CellT>
+__device__ __forceinline__ void rk4_step(CellT& C, const RayState<T>& S, T H, RayState<T>& N, T& s_here,
                                          T& tx1, T& ty1, int& i1, int& j1) {
     const T Hh = (T)0.5 * H, H6 = H / (T)6;
     const T dx = S.d.hx(), dy = S.d.hy();
@@ -307,8 +316,8 @@ __device__ __forceinline__ void rk4_step(Cell<T>& C, const RayState<T>& S, T H, 
 // One step of Heun's second-order Runge-Kutta method (the slopes at S and at
 // the Euler end point S + H (d, k1), averaged), in the same cell-unit,
 // compensated form as rk4_step.
-template <typename T>
-__device__ __forceinline__ void heun_step(Cell<T>& C, const RayState<T>& S, T H, RayState<T>& N, T& s_here,
+template <typename T, typename CellT>
+__device__ __forceinline__ void heun_step(CellT& C, const RayState<T>& S, T H, RayState<T>& N, T& s_here,
                                           T& tx1, T& ty1, int& i1, int& j1) {
     const T Hh = (T)0.5 * H;
     const T dx = S.d.hx(), dy = S.d.hy();
@@ -337,8 +346,8 @@ __device__ __forceinline__ void heun_step(Cell<T>& C, const RayState<T>& S, T H,
 }
 
 // The step of the configured integrator (uniform over a launch).
-template <typename T>
-__device__ __forceinline__ void ray_step(Cell<T>& C, const Geom& G, const RayState<T>& S, T H, RayState<T>& N,
+template <typename T, typename CellT>
+__device__ __forceinline__ void ray_step(CellT& C, const Geom& G, const RayState<T>& S, T H, RayState<T>& N,
                                          T& s_here, T& tx1, T& ty1, int& i1, int& j1) {
     if (G.heun) heun_step(C, S, H, N, s_here, tx1, ty1, i1, j1);
     else rk4_step(C, S, H, N, s_here, tx1, ty1, i1, j1);
@@ -458,8 +467,8 @@ __device__ __forceinline__ void trace_begin(TraceState<T>& ts, const Geom& G, do
 // One RK4 step. Returns true when the trace has ended: the step ended on or
 // outside the ring (flags bit1 if that was the very first step) or the step
 // cap was reached (flags bit0). On exit ts.S is still the last inside point.
-template <typename T, typename Sink>
-__device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState<T>& ts, Sink& sink) {
+template <typename T, typename CellT, typename Sink>
+__device__ __forceinline__ bool trace_step(CellT& C, const Geom& G, TraceState<T>& ts, Sink& sink) {
     if (ts.m >= G.max_steps_i) {
         ts.flags |= 1;
         return true;
@@ -508,8 +517,8 @@ __device__ __forceinline__ bool trace_step(Cell<T>& C, const Geom& G, TraceState
 
 // Landing, travel time and final weights of an ended trace. The endpoint
 // correction is taken toward (xr, yr).
-template <typename T, typename Sink>
-__device__ TraceOut trace_end(Cell<T>& C, const Geom& G, TraceState<T>& ts, double xe, double ye, double xr,
+template <typename T, typename CellT, typename Sink>
+__device__ TraceOut trace_end(CellT& C, const Geom& G, TraceState<T>& ts, double xe, double ye, double xr,
                               double yr, Sink& sink) {
     TraceOut out;
     out.flags = ts.flags;
@@ -579,8 +588,8 @@ __device__ TraceOut trace_end(Cell<T>& C, const Geom& G, TraceState<T>& ts, doub
 // Traces one ray from (xe, ye) at angle theta (begin + steps + end). With a
 // sink, every sample point m reports its trapezoid weight alpha_m (and the
 // endpoint weight) with its cell and fractions.
-template <typename T, typename Sink>
-__device__ TraceOut trace_ray(Cell<T>& C, const Geom& G, double xe, double ye, double theta, double xr,
+template <typename T, typename CellT, typename Sink>
+__device__ TraceOut trace_ray(CellT& C, const Geom& G, double xe, double ye, double theta, double xr,
                               double yr, Sink& sink) {
     TraceState<T> ts;
     trace_begin(ts, G, xe, ye, theta);

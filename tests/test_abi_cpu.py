@@ -37,7 +37,19 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_without_gpu(lib):
-    assert lib.rt_version() == 1
+    from paper_2511_18511_gb300 import _lib
+    assert lib.rt_version() == _lib.ABI_VERSION == 2
+
+
+def test_option_checks_without_gpu(lib):
+    """The allocation-free call checks its options before touching the device:
+    an unknown integrator or a non-bilinear interpolator is refused."""
+    from paper_2511_18511_gb300 import _lib
+    g = _lib.RtGrid(8, 8, 1.0, -3.5, -3.5)
+    prob = _lib.RtProblem(g, None, 2, None, 1.0, 0, None)
+    for integ, interp in ((9, 0), (0, 1), (0, 7)):
+        o = _lib.RtOptions(1, 30, 0.1, 1e-4, 0, 0, 0, 0, integ, interp)
+        assert lib.rt_tof_forward_noalloc(ctypes.byref(prob), ctypes.byref(o), None, None, None, None) == _lib.RT_EINVAL
 
 
 def test_null_arguments_are_rejected_without_gpu(lib):
