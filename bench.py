@@ -35,6 +35,7 @@ UNIT = "linked rays/s"
 # combination, renormalisation, the trapezoid slowness sample and the exit
 # test; FMA = 2, div/sqrt = 1); the derivation is in the design notes.
 FLOP_PER_STEP = 219
+FLOP_PER_BSPLINE_STEP = 387   # RK4 step with the bicubic sampler (counted in the design notes)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -558,6 +559,27 @@ def main():
     warm_traces = float(out_w["iters"].float().mean().item())
     warm = float(np.mean(warm_ms))
 
+    # the same step with the interpolating cubic B-spline sampler (Sec. 3.3.1's
+    # second scheme), FP32-compensated, cold start
+    out_b, g_b = buffers(), torch.empty_like(prob.c)
+    kw_b = dict(precision="fp32c", ctx=ctx, interpolator="bspline")
+    bs_ms, bs_link_ms = [], []
+    for k in range(max(2, min(args.steps, 3)) + 1):
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, out=out_b, **kw_b)
+        b.record(stream)
+        rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, out=g_b, **kw_b)
+        c.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            bs_ms.append(a.elapsed_time(c))
+            bs_link_ms.append(a.elapsed_time(b))
+    bs_ok, bs_counts = rt.rt_status_counts(ctx)
+    bs_link = float(np.mean(bs_link_ms))
+    bs_achieved = bs_counts[7] * FLOP_PER_BSPLINE_STEP / (bs_link / 1e3) / 1e12
+
     # roofline of the dominant kernel (the FP32 link kernel), from its live events
     steps_per_launch = res["counts"][7]
     link_ms = float(np.mean(res["link_ms"]))
@@ -617,6 +639,12 @@ def main():
         "warm_start": {"value": n / (warm / 1e3), "unit": UNIT, "ms_per_step": warm,
                        "mean_traces_per_pair": warm_traces,
                        "start": "the previous step's linked angles"},
+        "bspline": {"value": n / (float(np.mean(bs_ms)) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(bs_ms)),
+                    "link_ms": bs_link, "adjoint_ms": float(np.mean(bs_ms)) - bs_link, "all_linked": bs_ok,
+                    "mean_traces_per_pair": float(out_b["iters"].float().mean().item()),
+                    "rk4_steps_per_launch": bs_counts[7], "flop_per_rk4_step": FLOP_PER_BSPLINE_STEP,
+                    "achieved_tflops": bs_achieved, "frac": bs_achieved / FP32_PEAK_TFLOPS,
+                    "sampler": "interpolating cubic B-spline (bicubic per cell, analytic gradient)"},
         "fp64_gpu": {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                      "speedup_fp32c_over_fp64": ms64 / ms_per_step},
         "link": {"mean_traces_per_pair": res["iters"], "all_linked": res["ok"],
