@@ -93,6 +93,12 @@ def load(path: str):
                                  _ip, _dp, C.c_int32]
     L.orc_born_adjoint.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, C.c_int32, _dp, _dp, _dp,
                                    C.c_int32]
+    L.orc_fan_maps_abs.argtypes = [G, _dp, _dp, C.c_int32, _dp, C.c_double, C.c_double, C.c_int32, C.c_double,
+                                   _dp, _dp, _dp, C.c_int32]
+    L.orc_born_apply_abs.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, _dp, C.c_double, C.c_int32, _dp, _dp,
+                                     C.c_int32, _ip, _dp, C.c_int32]
+    L.orc_born_adjoint_abs.argtypes = [G, C.c_double, C.c_int32, _dp, _dp, _dp, C.c_double, C.c_int32, _dp, _dp,
+                                       _dp, C.c_int32]
     return L
 
 
@@ -350,23 +356,33 @@ def fan_ray(grid, c_mps, R, xe, theta, ds):
 ETA = 1e-2   # us: penalty of the squared distance (in cells) to the ray in the amplitude choice
 
 
-def fan_maps(grid, c_mps, tx, R, ds, K, eta=ETA, nthreads=0):
+def fan_maps(grid, c_mps, tx, R, ds, K, eta=ETA, nthreads=0, alpha0=None):
     """First-arrival maps (T us, A) of every transducer -> two [n_tx, ny, nx]
     arrays (T = inf, A = 0 where no fan ray reaches); A from the candidate of
-    least T + eta (b/h)^2, b its distance to the ray."""
+    least T + eta (b/h)^2, b its distance to the ray. With alpha0 [ny, nx]
+    (Np (rad/s)^-y m^-1) also the absorption path integrals Lam -> (T, A, Lam)."""
     c = _f64(c_mps)
     tx = _f64(tx).reshape(-1, 2)
     n_tx = tx.shape[0]
     T = np.empty((n_tx, grid.ny, grid.nx))
     A = np.empty((n_tx, grid.ny, grid.nx))
     g = _grid(grid)
-    _check(lib().orc_fan_maps(C.byref(g), _d(c), n_tx, _d(tx), R, ds, K, eta, _d(T), _d(A), nthreads), "fan_maps")
-    return T, A
+    if alpha0 is None:
+        _check(lib().orc_fan_maps(C.byref(g), _d(c), n_tx, _d(tx), R, ds, K, eta, _d(T), _d(A), nthreads),
+               "fan_maps")
+        return T, A
+    al = _f64(alpha0)
+    Lam = np.empty((n_tx, grid.ny, grid.nx))
+    _check(lib().orc_fan_maps_abs(C.byref(g), _d(c), _d(al), n_tx, _d(tx), R, ds, K, eta, _d(T), _d(A), _d(Lam),
+                                  nthreads), "fan_maps_abs")
+    return T, A, Lam
 
 
-def born_apply(grid, R, T, A, f_mhz, dc, pairs=None, nthreads=0):
-    """Born data, complex: [n_freq, n_tx, n_tx] (pairs None) or [n_freq, n_pairs]."""
+def born_apply(grid, R, T, A, f_mhz, dc, pairs=None, nthreads=0, Lam=None, y=1.0):
+    """Born data, complex: [n_freq, n_tx, n_tx] (pairs None) or [n_freq, n_pairs];
+    with Lam the absorption factor exp(-omega_s^y Lam) multiplies each map."""
     T, A = _f64(T), _f64(A)
+    Lam = None if Lam is None else _f64(Lam)
     n_tx = T.shape[0]
     f = _f64(f_mhz).ravel()
     dc = _f64(dc)
@@ -374,20 +390,21 @@ def born_apply(grid, R, T, A, f_mhz, dc, pairs=None, nthreads=0):
     n_out = n_tx * n_tx if p is None else p.shape[0]
     out = np.empty((len(f), n_out, 2))
     g = _grid(grid)
-    _check(lib().orc_born_apply(C.byref(g), R, n_tx, _d(T), _d(A), len(f), _d(f), _d(dc),
-                                0 if p is None else p.shape[0], _i(p), _d(out), nthreads), "born_apply")
+    _check(lib().orc_born_apply_abs(C.byref(g), R, n_tx, _d(T), _d(A), _d(Lam), float(y), len(f), _d(f), _d(dc),
+                                    0 if p is None else p.shape[0], _i(p), _d(out), nthreads), "born_apply")
     d = out[..., 0] + 1j * out[..., 1]
     return d.reshape(len(f), n_tx, n_tx) if p is None else d
 
 
-def born_adjoint(grid, R, T, A, f_mhz, d, nthreads=0):
+def born_adjoint(grid, R, T, A, f_mhz, d, nthreads=0, Lam=None, y=1.0):
     """Adjoint of born_apply for complex d [n_freq, n_tx, n_tx] -> [ny, nx]."""
     T, A = _f64(T), _f64(A)
+    Lam = None if Lam is None else _f64(Lam)
     n_tx = T.shape[0]
     f = _f64(f_mhz).ravel()
     dd = np.ascontiguousarray(np.stack([np.real(d), np.imag(d)], axis=-1), dtype=np.float64)
     out = np.empty((grid.ny, grid.nx))
     g = _grid(grid)
-    _check(lib().orc_born_adjoint(C.byref(g), R, n_tx, _d(T), _d(A), len(f), _d(f), _d(dd), _d(out),
-                                  nthreads), "born_adjoint")
+    _check(lib().orc_born_adjoint_abs(C.byref(g), R, n_tx, _d(T), _d(A), _d(Lam), float(y), len(f), _d(f), _d(dd),
+                                      _d(out), nthreads), "born_adjoint")
     return out

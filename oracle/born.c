@@ -53,7 +53,17 @@
  *      strictly inside the ring (dc in m/s as given);
  *   B7 adjoint under Re<a, b> = Re sum conj(a) b on the data and the plain dot
  *      product on dc: dc~(x) = Re sum_f omega^2 h^2 sum_{e != r}
- *      conj(E_e(x) E_r(x)) d[f][e][r], 0 outside the ring.
+ *      conj(E_e(x) E_r(x)) d[f][e][r], 0 outside the ring;
+ *   B9 absorption (the Appendix: complex wavenumber k + i alpha with the power
+ *      law alpha = alpha0 omega^y, alpha0 varying in space, in Np (rad/s)^-y
+ *      m^-1; the absorption amplitude is accumulated along the ray, A =
+ *      A_geom A_abs): nodal alpha0 interpolated bilinearly, its path integral
+ *      Lambda = int alpha0 ds (ds in metres) by the trapezoid rule over the
+ *      sample points, carried to a node from its foot to first order
+ *      (Lambda + alpha0 a), and taken from the candidate that supplies A; then
+ *      A_abs = exp(-omega_s^y Lambda) with omega_s = 2 pi f in rad/s, so
+ *      E_t = A_t exp(-omega_s^y Lambda_t) exp(i omega T_t). Without alpha0,
+ *      Lambda = 0 (the maps of B1-B5 exactly).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -64,7 +74,7 @@
 
 #include "oracle.h"
 
-enum { F_C, F_GX, F_GY, F_S, F_HXX, F_HXY, F_HYY, F_N };
+enum { F_C, F_GX, F_GY, F_S, F_HXX, F_HXY, F_HYY, F_AL, F_N };
 
 typedef struct {
     int nx, ny;
@@ -77,8 +87,8 @@ static void bfield_free(BField* F) {
     memset(F, 0, sizeof(*F));
 }
 
-/* B1 */
-static int bfield_make(BField* F, const orc_grid* g, const double* c_mps) {
+/* B1 (and B9: alpha0 as given, or 0) */
+static int bfield_make(BField* F, const orc_grid* g, const double* c_mps, const double* alpha0) {
     memset(F, 0, sizeof(*F));
     if (!g || !c_mps || g->nx < 3 || g->ny < 3 || !(g->h > 0)) return ORC_EINVAL;
     const int nx = g->nx, ny = g->ny;
@@ -94,6 +104,10 @@ static int bfield_make(BField* F, const orc_grid* g, const double* c_mps) {
         if (!(c_mps[k] > 0) || !isfinite(c_mps[k])) { bfield_free(F); return ORC_EINVAL; }
         c[k] = 1e-3 * c_mps[k];
         F->v[F_S][k] = 1.0 / c[k];
+        if (alpha0) {
+            if (!(alpha0[k] >= 0) || !isfinite(alpha0[k])) { bfield_free(F); return ORC_EINVAL; }
+            F->v[F_AL][k] = alpha0[k];
+        }
     }
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -113,7 +127,7 @@ static int bfield_make(BField* F, const orc_grid* g, const double* c_mps) {
     return ORC_OK;
 }
 
-/* all seven fields at (x, y), bilinear; the cell index is clamped into the grid */
+/* all fields at (x, y), bilinear; the cell index is clamped into the grid */
 static void bsample(const BField* F, double x, double y, double f[F_N]) {
     const double u = (x - F->x0) / F->h, v = (y - F->y0) / F->h;
     double fi = floor(u), fj = floor(v);
@@ -162,8 +176,8 @@ static void brk4(const BField* F, const double st[6], double hs, double out[6]) 
     out[3] /= n;
 }
 
-/* One sample point of a fan ray. */
-typedef struct { double x, y, dx, dy, T, Q, P, c, s; } BSample;
+/* One sample point of a fan ray (L: absorption path integral, al: alpha0 there). */
+typedef struct { double x, y, dx, dy, T, Q, P, c, s, L, al; } BSample;
 
 typedef void (*visit_fn)(void* ctx, const BSample* p);
 
@@ -175,15 +189,16 @@ static void fan_ray(const BField* F, double R, double xe, double ye, double thet
     double f[F_N];
     double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, 1.0 / c_t}, nx[6];
     bsample(F, xe, ye, f);
-    BSample p = {st[0], st[1], st[2], st[3], 0.0, st[4], st[5], f[F_C], f[F_S]};
+    BSample p = {st[0], st[1], st[2], st[3], 0.0, st[4], st[5], f[F_C], f[F_S], 0.0, f[F_AL]};
     visit(ctx, &p);
     for (int64_t m = 1; m <= maxstep; ++m) {
         brk4(F, st, ds, nx);
         if (nx[0] * nx[0] + nx[1] * nx[1] >= R * R) break;
         bsample(F, nx[0], nx[1], f);
         const double T = p.T + ds * 0.5 * (p.s + f[F_S]);
+        const double L = p.L + 1e-3 * ds * 0.5 * (p.al + f[F_AL]);   /* B9: ds in metres */
         memcpy(st, nx, sizeof(st));
-        p = (BSample){st[0], st[1], st[2], st[3], T, st[4], st[5], f[F_C], f[F_S]};
+        p = (BSample){st[0], st[1], st[2], st[3], T, st[4], st[5], f[F_C], f[F_S], L, f[F_AL]};
         visit(ctx, &p);
     }
 }
@@ -192,6 +207,7 @@ typedef struct {
     const BField* F;
     double c_t, ds;
     double *T, *A;    /* map mode: [ny*nx] of one transducer */
+    double* L;        /* map mode: absorption path integral of the kept A (B9), or NULL */
     double* rec;      /* record mode: 9 values per sample */
     int64_t cap, n;
     double* S;                  /* map mode: score of the candidate whose A is kept */
@@ -203,7 +219,7 @@ static double clamp_q(double q, double h) {
     return q < 0 ? -h : h;
 }
 
-typedef void (*offer_fn)(MapCtx* M, size_t k, double cand, double b, double A);
+typedef void (*offer_fn)(MapCtx* M, size_t k, double cand, double b, double A, double L);
 
 /* B4 + B5: every candidate (node k, time, amplitude) of sample p */
 static void candidates(MapCtx* M, const BSample* p, offer_fn offer) {
@@ -223,20 +239,22 @@ static void candidates(MapCtx* M, const BSample* p, offer_fn offer) {
             double curv = p->P / Qf;
             if (!(curv >= 0)) curv = p->P / clamp_q(Qf, h);
             const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(Qf, h))));
-            offer(M, (size_t)j * F->nx + i, p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A);
+            const double L = p->L + 1e-3 * p->al * along;   /* B9: first order from the foot */
+            offer(M, (size_t)j * F->nx + i, p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A, L);
         }
     }
 }
 
 /* the first arrival (earliest candidate) for T; for A the candidate of least
  * T + eta (b/h)^2, ties to the smaller amplitude */
-static void keep(MapCtx* M, size_t k, double cand, double b, double A) {
+static void keep(MapCtx* M, size_t k, double cand, double b, double A, double L) {
     if (cand < M->T[k]) M->T[k] = cand;
     const double q = b / M->F->h;
     const double score = cand + M->eta * q * q;
     if (score < M->S[k] || (score == M->S[k] && A < M->A[k])) {
         M->S[k] = score;
         M->A[k] = A;
+        if (M->L) M->L[k] = L;
     }
 }
 
@@ -280,7 +298,7 @@ int orc_fan_ray(const orc_grid* g, const double* c_mps, double R, double xe, dou
                 double ds, int64_t cap, double* rec9, int64_t* n_out) {
     if (!n_out || !(ds > 0) || !(R > 0) || (cap > 0 && !rec9)) return ORC_EINVAL;
     BField F;
-    int rc = bfield_make(&F, g, c_mps);
+    int rc = bfield_make(&F, g, c_mps, NULL);
     if (rc) return rc;
     MapCtx M = {0};
     M.F = &F;
@@ -300,9 +318,15 @@ int orc_fan_angles(double xe, double ye, double R, double ds, int32_t K, double*
 
 int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx, double R,
                  double ds, int32_t K, double eta, double* T, double* A, int32_t nthreads) {
+    return orc_fan_maps_abs(g, c_mps, NULL, n_tx, tx, R, ds, K, eta, T, A, NULL, nthreads);
+}
+
+int orc_fan_maps_abs(const orc_grid* g, const double* c_mps, const double* alpha0, int32_t n_tx, const double* tx,
+                     double R, double ds, int32_t K, double eta, double* T, double* A, double* Lam,
+                     int32_t nthreads) {
     if (!g || !tx || n_tx < 1 || K < 2 || !T || !A || !(ds > 0) || !(R > 0) || !(eta >= 0)) return ORC_EINVAL;
     BField F;
-    int rc = bfield_make(&F, g, c_mps);
+    int rc = bfield_make(&F, g, c_mps, alpha0);
     if (rc) return rc;
     const size_t nn = (size_t)F.nx * F.ny;
     int bad = 0;
@@ -312,10 +336,12 @@ int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const dou
         M.F = &F;
         M.T = T + (size_t)t * nn;
         M.A = A + (size_t)t * nn;
+        M.L = Lam ? Lam + (size_t)t * nn : NULL;
         M.S = malloc(nn * sizeof(double));
         if (!M.S) { bad = 1; continue; }
         M.eta = eta;
         for (size_t k = 0; k < nn; ++k) { M.T[k] = INFINITY; M.A[k] = 0.0; M.S[k] = INFINITY; }
+        if (M.L) for (size_t k = 0; k < nn; ++k) M.L[k] = 0.0;
         const double xe = tx[2 * t], ye = tx[2 * t + 1];
         M.c_t = c_at(&F, xe, ye);
         M.ds = ds;
@@ -328,14 +354,19 @@ int orc_fan_maps(const orc_grid* g, const double* c_mps, int32_t n_tx, const dou
     return bad ? ORC_ENOMEM : ORC_OK;
 }
 
-/* E_t(x) = A exp(i omega T), 0 where unreached; the phase is reduced mod 2 pi */
-static void efield(double T, double A, double omega, double* re, double* im) {
+/* E_t(x) = A exp(-wy L) exp(i omega T), 0 where unreached (wy = omega_s^y of
+ * B9, L = Lambda); the phase is reduced mod 2 pi */
+static void efield(double T, double A, double L, double wy, double omega, double* re, double* im) {
     if (!isfinite(T)) { *re = *im = 0.0; return; }
     double ph = omega * T;
     ph -= 2.0 * M_PI * floor(ph / (2.0 * M_PI));
-    *re = A * cos(ph);
-    *im = A * sin(ph);
+    const double amp = A * exp(-wy * L);
+    *re = amp * cos(ph);
+    *im = amp * sin(ph);
 }
+
+/* B9: omega_s^y for f in MHz (omega_s = 2 pi f 1e6 rad/s) */
+static double omega_pow(double f_mhz, double y) { return pow(2.0 * M_PI * f_mhz * 1e6, y); }
 
 /* nodes strictly inside the ring, row-major order */
 static int64_t inside_nodes(const orc_grid* g, double R, int64_t* idx) {
@@ -356,7 +387,14 @@ static int64_t inside_nodes(const orc_grid* g, double R, int64_t* idx) {
 int orc_born_apply(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
                    int32_t n_freq, const double* f_mhz, const double* dc, int32_t n_pairs,
                    const int32_t* pairs, double* d_out, int32_t nthreads) {
+    return orc_born_apply_abs(g, R, n_tx, T, A, NULL, 0.0, n_freq, f_mhz, dc, n_pairs, pairs, d_out, nthreads);
+}
+
+int orc_born_apply_abs(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
+                       const double* Lam, double y, int32_t n_freq, const double* f_mhz, const double* dc,
+                       int32_t n_pairs, const int32_t* pairs, double* d_out, int32_t nthreads) {
     if (!g || n_tx < 1 || !T || !A || n_freq < 0 || (n_freq > 0 && !f_mhz) || !dc || !d_out) return ORC_EINVAL;
+    if (Lam && !(y >= 0)) return ORC_EINVAL;
     const int64_t n_out = pairs ? n_pairs : (int64_t)n_tx * n_tx;
     const size_t nn = (size_t)g->nx * g->ny;
     const int64_t n_in = inside_nodes(g, R, NULL);
@@ -366,6 +404,7 @@ int orc_born_apply(const orc_grid* g, double R, int32_t n_tx, const double* T, c
     for (int32_t f = 0; f < n_freq; ++f) {
         const double omega = 2.0 * M_PI * f_mhz[f];
         const double scale = omega * omega * g->h * g->h;
+        const double wy = Lam ? omega_pow(f_mhz[f], y) : 0.0;
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads_of(nthreads))
         for (int64_t q = 0; q < n_out; ++q) {
             const int e = pairs ? pairs[2 * q] : (int)(q / n_tx);
@@ -375,8 +414,10 @@ int orc_born_apply(const orc_grid* g, double R, int32_t n_tx, const double* T, c
                 for (int64_t p = 0; p < n_in; ++p) {
                     const size_t k = (size_t)idx[p];
                     double ar, ai, br, bi;
-                    efield(T[(size_t)e * nn + k], A[(size_t)e * nn + k], omega, &ar, &ai);
-                    efield(T[(size_t)r * nn + k], A[(size_t)r * nn + k], omega, &br, &bi);
+                    efield(T[(size_t)e * nn + k], A[(size_t)e * nn + k], Lam ? Lam[(size_t)e * nn + k] : 0.0, wy,
+                           omega, &ar, &ai);
+                    efield(T[(size_t)r * nn + k], A[(size_t)r * nn + k], Lam ? Lam[(size_t)r * nn + k] : 0.0, wy,
+                           omega, &br, &bi);
                     sre += (ar * br - ai * bi) * dc[k];
                     sim += (ar * bi + ai * br) * dc[k];
                 }
@@ -393,7 +434,14 @@ int orc_born_apply(const orc_grid* g, double R, int32_t n_tx, const double* T, c
 int orc_born_adjoint(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
                      int32_t n_freq, const double* f_mhz, const double* d_in, double* dc_out,
                      int32_t nthreads) {
+    return orc_born_adjoint_abs(g, R, n_tx, T, A, NULL, 0.0, n_freq, f_mhz, d_in, dc_out, nthreads);
+}
+
+int orc_born_adjoint_abs(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
+                         const double* Lam, double y, int32_t n_freq, const double* f_mhz, const double* d_in,
+                         double* dc_out, int32_t nthreads) {
     if (!g || n_tx < 1 || !T || !A || n_freq < 0 || (n_freq > 0 && !f_mhz) || !d_in || !dc_out) return ORC_EINVAL;
+    if (Lam && !(y >= 0)) return ORC_EINVAL;
     const size_t nn = (size_t)g->nx * g->ny;
     const int nt = nthreads_of(nthreads);
     const int64_t n_in = inside_nodes(g, R, NULL);
@@ -416,8 +464,10 @@ int orc_born_adjoint(const orc_grid* g, double R, int32_t n_tx, const double* T,
             for (int32_t f = 0; f < n_freq; ++f) {
                 const double omega = 2.0 * M_PI * f_mhz[f];
                 const double scale = omega * omega * g->h * g->h;
+                const double wy = Lam ? omega_pow(f_mhz[f], y) : 0.0;
                 for (int32_t t = 0; t < n_tx; ++t)
-                    efield(T[(size_t)t * nn + k], A[(size_t)t * nn + k], omega, &Et[2 * t], &Et[2 * t + 1]);
+                    efield(T[(size_t)t * nn + k], A[(size_t)t * nn + k], Lam ? Lam[(size_t)t * nn + k] : 0.0, wy,
+                           omega, &Et[2 * t], &Et[2 * t + 1]);
                 for (int32_t e = 0; e < n_tx; ++e) {
                     const double ar = Et[2 * e], ai = Et[2 * e + 1];
                     if (ar == 0.0 && ai == 0.0) continue;

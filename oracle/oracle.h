@@ -140,6 +140,23 @@ int orc_born_adjoint(const orc_grid* g, double R, int32_t n_tx, const double* T,
                      int32_t n_freq, const double* f_mhz, const double* d_in, double* dc_out,
                      int32_t nthreads);
 
+/* With absorption (the Appendix's alpha = alpha0 omega^y): alpha0 [ny*nx] in
+ * Np (rad/s)^-y m^-1 (>= 0; NULL = none) gives, besides T and A, the path
+ * integral Lam [n_tx][ny*nx] = int alpha0 ds (ds in m) of the ray that
+ * supplies A (0 where unreached; Lam may be NULL). */
+int orc_fan_maps_abs(const orc_grid* g, const double* c_mps, const double* alpha0, int32_t n_tx,
+                     const double* tx, double R, double ds, int32_t K, double eta, double* T, double* A,
+                     double* Lam, int32_t nthreads);
+
+/* Born map and adjoint with E_t = A_t exp(-omega_s^y Lam_t) exp(i omega T_t),
+ * omega_s = 2 pi f 1e6 rad/s, y >= 0 (Lam NULL: no absorption). */
+int orc_born_apply_abs(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
+                       const double* Lam, double y, int32_t n_freq, const double* f_mhz, const double* dc,
+                       int32_t n_pairs, const int32_t* pairs, double* d_out, int32_t nthreads);
+int orc_born_adjoint_abs(const orc_grid* g, double R, int32_t n_tx, const double* T, const double* A,
+                         const double* Lam, double y, int32_t n_freq, const double* f_mhz, const double* d_in,
+                         double* dc_out, int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif

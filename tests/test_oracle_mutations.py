@@ -13,6 +13,7 @@ import shutil
 import pytest
 
 import oracle
+from tests import test_oracle_absorption_pins as apins
 from tests import test_oracle_born_pins as bpins
 from tests import test_oracle_bspline_pins as spins
 from tests import test_oracle_pins as pins
@@ -105,6 +106,18 @@ BSPLINE_PINS = [_in_bspline(p) for p in (
 
 
 BORN_MUTANTS = {
+    "born_abs_path_in_mm": ("const double L = p.L + 1e-3 * ds * 0.5 * (p.al + f[F_AL]);",
+                            "const double L = p.L + ds * 0.5 * (p.al + f[F_AL]);"),
+    "born_abs_left_rule": ("const double L = p.L + 1e-3 * ds * 0.5 * (p.al + f[F_AL]);",
+                           "const double L = p.L + 1e-3 * ds * p.al;"),
+    "born_abs_extrapolation_sign": ("const double L = p->L + 1e-3 * p->al * along;",
+                                    "const double L = p->L - 1e-3 * p->al * along;"),
+    "born_abs_no_extrapolation": ("const double L = p->L + 1e-3 * p->al * along;", "const double L = p->L;"),
+    "born_abs_gain": ("const double amp = A * exp(-wy * L);", "const double amp = A * exp(wy * L);"),
+    "born_abs_omega_per_us": ("return pow(2.0 * M_PI * f_mhz * 1e6, y);", "return pow(2.0 * M_PI * f_mhz, y);"),
+    "born_abs_linear_law": ("return pow(2.0 * M_PI * f_mhz * 1e6, y);", "return pow(2.0 * M_PI * f_mhz * 1e6, 1.0);"),
+    "born_abs_adjoint_lossless": ("const double wy = Lam ? omega_pow(f_mhz[f], y) : 0.0;\n                for",
+                                  "const double wy = 0.0;\n                for"),
     "born_drop_cnn": ("k[5] = -cnn / (f[F_C] * f[F_C]) * st[4];", "k[5] = 0.0 * cnn;"),
     "born_cnn_sign": ("k[5] = -cnn / (f[F_C] * f[F_C]) * st[4];", "k[5] = cnn / (f[F_C] * f[F_C]) * st[4];"),
     "born_drop_hxy": ("- 2.0 * dx * dy * f[F_HXY]", "- 0.0 * dx * dy * f[F_HXY]"),
@@ -117,8 +130,8 @@ BORN_MUTANTS = {
     "born_Q_missing_c": ("k[4] = f[F_C] * st[5];", "k[4] = st[5];"),
     "born_amplitude_no_sqrt": ("const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(Qf, h))));",
                                "const double A = p->c / (M->c_t * fabs(clamp_q(Qf, h)));"),
-    "born_first_order_only": ("p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A);",
-                              "p->T + p->s * along, fabs(across), A);"),
+    "born_first_order_only": ("p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A, L);",
+                              "p->T + p->s * along, fabs(across), A, L);"),
     "born_curvature_at_sample": ("const double Qf = p->Q + along * p->c * p->P;", "const double Qf = p->Q;"),
     "born_amplitude_no_distance_penalty": ("const double score = cand + M->eta * q * q;",
                                            "const double score = cand + 0.0 * q * q;"),
@@ -128,14 +141,14 @@ BORN_MUTANTS = {
     "born_T_uses_c": ("const double T = p.T + ds * 0.5 * (p.s + f[F_S]);",
                       "const double T = p.T + ds * 0.5 * (p.c + f[F_C]);"),
     "born_apply_conj": ("sim += (ar * bi + ai * br) * dc[k];", "sim += (ar * bi - ai * br) * dc[k];"),
-    "born_apply_omega_not_squared": ("const double scale = omega * omega * g->h * g->h;\n#pragma omp parallel for schedule(dynamic, 16)",
-                                     "const double scale = omega * g->h * g->h;\n#pragma omp parallel for schedule(dynamic, 16)"),
+    "born_apply_omega_not_squared": ("const double scale = omega * omega * g->h * g->h;\n        const double wy = Lam ? omega_pow(f_mhz[f], y) : 0.0;\n#pragma",
+                                     "const double scale = omega * g->h * g->h;\n        const double wy = Lam ? omega_pow(f_mhz[f], y) : 0.0;\n#pragma"),
     "born_apply_keeps_diagonal": ("if (e != r && e >= 0", "if (e >= 0"),
     "born_adjoint_conj_one_factor": ("acc += scale * (pr * dd[0] + pi * dd[1]);",
                                      "acc += scale * (pr * dd[0] - pi * dd[1]);"),
     "born_adjoint_uses_diagonal": ("if (r == e) continue;\n                        const double br", "const double br"),
-    "born_phase_units": ("const double omega = 2.0 * M_PI * f_mhz[f];\n        const double scale = omega * omega * g->h * g->h;\n#pragma",
-                         "const double omega = M_PI * f_mhz[f];\n        const double scale = omega * omega * g->h * g->h;\n#pragma"),
+    "born_phase_units": ("const double omega = 2.0 * M_PI * f_mhz[f];\n        const double scale = omega * omega * g->h * g->h;\n        const double wy",
+                         "const double omega = M_PI * f_mhz[f];\n        const double scale = omega * omega * g->h * g->h;\n        const double wy"),
 }
 
 BORN_PINS = [
@@ -149,6 +162,11 @@ BORN_PINS = [
     bpins.test_born_point_scatterer_homogeneous,
     bpins.test_born_adjoint_single_datum_homogeneous,
     bpins.test_maps_fermat_against_linking,
+    apins.test_zero_alpha_is_lossless,
+    apins.test_absorption_uniform_alpha_homogeneous,
+    apins.test_absorption_dot_product_identity,
+    apins.test_absorption_point_scatterer_homogeneous,
+    apins.test_absorption_linear_alpha_brute_force,
 ]
 
 
