@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define RT_ABI_VERSION 2   /* 2: rt_options.interpolator, rt_bspline_coef */
+#define RT_ABI_VERSION 2   /* 2: rt_options.interpolator, rt_bspline_coef, rtborn_*_abs */
 
 enum rt_code {
     RT_OK = 0,
@@ -315,7 +315,9 @@ int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* opt, const 
  * geometric amplitude from the transport equation through the ray Jacobian,
  * which a paraxial ray traced with each ray supplies (Sec. 3.5, default). The
  * backward Green's functions of the receivers are the same per-transducer maps
- * (reciprocity). Absorption is not modelled (A_abs = 1).
+ * (reciprocity). The *_abs variants add absorption (Appendix: wavenumber
+ * k + i alpha, alpha = alpha0 omega^y, A = A_geom A_abs with A_abs accumulated
+ * along the ray); the plain calls are the *_abs calls without it (A_abs = 1).
  */
 
 /* Penalty (us) of the squared distance to the ray, in grid steps, in the
@@ -397,6 +399,38 @@ int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_
 int rtborn_adjoint(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
                    const float* A, int32_t n_freq, const double* f_mhz, const float* d_in,
                    int32_t gemm_mode, float* dc_out, void* stream);
+
+/*
+ * rtborn_maps_abs — rtborn_maps plus the absorption path integral of every
+ * map entry: each fan ray also carries Lambda = int alpha0 ds (ds in metres;
+ * trapezoid rule over the bilinearly interpolated alpha0, Kahan-summed); a
+ * node's candidate is Lambda + alpha0 a from its foot (first order along the
+ * ray), and the node keeps the Lambda of the candidate that supplies A (the
+ * same least score; an exact tie of scores may pair A and Lambda of different
+ * rays).
+ *   alpha0    device [ny*nx] double, Np (rad/s)^-y m^-1, >= 0 (a negative or
+ *             NaN value leaves every entry unreached, like a bad c); NULL =
+ *             no absorption (then L_out is not written and may be NULL).
+ *   L_out     [n_tx][ny*nx] float out, Np (rad/s)^-y; 0 where unreached.
+ * Workspace: 20 bytes per map entry with alpha0 (12 without).
+ */
+int rtborn_maps_abs(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int32_t fan_rays,
+                    const double* alpha0, float* T_out, float* A_out, float* L_out, void* stream);
+
+/*
+ * rtborn_apply_abs / rtborn_adjoint_abs — rtborn_apply / rtborn_adjoint with
+ * E_t = A_t exp(-omega_s^y L_t) exp(i omega T_t), omega_s = 2 pi f 1e6 rad/s.
+ *   L         [n_tx][ny*nx] float, as written by rtborn_maps_abs; NULL = none.
+ *   y         power-law exponent in [0, 3] (soft tissue 1 < y <= 1.5); with L,
+ *             every frequency must be >= 0 and omega_s^y finite in FP32.
+ * Other arguments and errors as for rtborn_apply / rtborn_adjoint.
+ */
+int rtborn_apply_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                     const float* A, const float* L, double y, int32_t n_freq, const double* f_mhz,
+                     const float* dc_mps, int32_t gemm_mode, float* d_out, void* stream);
+int rtborn_adjoint_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                       const float* A, const float* L, double y, int32_t n_freq, const double* f_mhz,
+                       const float* d_in, int32_t gemm_mode, float* dc_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -341,11 +341,15 @@ GEMM_MODES = {"fp32": _L.RTBORN_GEMM_FP32, "bf16x9": _L.RTBORN_GEMM_BF16X9}
 @dataclasses.dataclass
 class BornMaps:
     """Per-transducer first-arrival maps (device float32 [n_tx, ny, nx]):
-    travel time T (us, +inf where no ray arrives) and amplitude A."""
+    travel time T (us, +inf where no ray arrives) and amplitude A; with
+    absorption also L, the path integral of alpha0 (Np (rad/s)^-y), and the
+    power-law exponent y of alpha = alpha0 omega^y."""
     grid: Grid
     ring_radius: float
     T: torch.Tensor
     A: torch.Tensor
+    L: Optional[torch.Tensor] = None
+    y: float = 1.0
 
     @property
     def n_tx(self) -> int:
@@ -357,20 +361,32 @@ class BornMaps:
 
 def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tensor] = None,
                 ctx: Optional[Context] = None, stream=None, out: Optional[BornMaps] = None,
-                blocks_per_sm: int = 0) -> BornMaps:
+                blocks_per_sm: int = 0, alpha0: Optional[torch.Tensor] = None, y: float = 1.0) -> BornMaps:
     """Travel-time and amplitude maps of every transducer from fans of
     fan_rays rays traced with their paraxial rays (paper Sec. 3.5).
-    blocks_per_sm selects the fan kernel variant (0 = default)."""
+    blocks_per_sm selects the fan kernel variant (0 = default). With alpha0
+    (float64 CUDA [ny, nx], Np (rad/s)^-y m^-1) the maps also carry the
+    absorption path integrals L and the exponent y (Appendix: alpha0 omega^y)."""
     ctx = ctx or default_context(prob.c.device.index)
     g = prob.grid
+    shape = (prob.n_tx, g.ny, g.nx)
+    dev = prob.c.device
     if out is None:
-        shape = (prob.n_tx, g.ny, g.nx)
-        out = BornMaps(g, prob.ring_radius, torch.empty(shape, dtype=torch.float32, device=prob.c.device),
-                       torch.empty(shape, dtype=torch.float32, device=prob.c.device))
+        out = BornMaps(g, prob.ring_radius, torch.empty(shape, dtype=torch.float32, device=dev),
+                       torch.empty(shape, dtype=torch.float32, device=dev))
+    if alpha0 is not None:
+        alpha0 = alpha0.to(device=dev, dtype=torch.float64).contiguous()
+        if alpha0.numel() != g.nx * g.ny:
+            raise ValueError("alpha0 needs one value per node")
+        if out.L is None:
+            out.L = torch.empty(shape, dtype=torch.float32, device=dev)
+        out.y = float(y)
+    else:
+        out.L = None
     o = _opts(ds, precision="fp32c", blocks_per_sm=blocks_per_sm)
     ps = prob.struct(c)
-    _L.check(ctx.h, ctx.lib.rtborn_maps(ctx.h, C.byref(ps), C.byref(o), int(fan_rays), _ptr(out.T), _ptr(out.A),
-                                        _stream(stream)))
+    _L.check(ctx.h, ctx.lib.rtborn_maps_abs(ctx.h, C.byref(ps), C.byref(o), int(fan_rays), _ptr(alpha0),
+                                            _ptr(out.T), _ptr(out.A), _ptr(out.L), _stream(stream)))
     return out
 
 
@@ -380,7 +396,7 @@ def _freqs(f_mhz):
 
 
 def _check_maps(maps: BornMaps):
-    for t in (maps.T, maps.A):
+    for t in (maps.T, maps.A) + (() if maps.L is None else (maps.L,)):
         if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
             raise ValueError("maps must be contiguous float32 CUDA tensors")
         if t.shape != (maps.n_tx, maps.grid.ny, maps.grid.nx):
@@ -400,8 +416,9 @@ def rtborn_apply(maps: BornMaps, f_mhz, dc: torch.Tensor, gemm: str = "bf16x9", 
     if out is None:
         out = torch.empty((nf, maps.n_tx, maps.n_tx), dtype=torch.complex64, device=maps.T.device)
     g = maps._grid_struct()
-    _L.check(ctx.h, ctx.lib.rtborn_apply(ctx.h, C.byref(g), maps.ring_radius, maps.n_tx, _ptr(maps.T), _ptr(maps.A),
-                                         nf, fa, _ptr(dc), GEMM_MODES[gemm], _ptr(out), _stream(stream)))
+    _L.check(ctx.h, ctx.lib.rtborn_apply_abs(ctx.h, C.byref(g), maps.ring_radius, maps.n_tx, _ptr(maps.T),
+                                             _ptr(maps.A), _ptr(maps.L), float(maps.y), nf, fa, _ptr(dc),
+                                             GEMM_MODES[gemm], _ptr(out), _stream(stream)))
     return out
 
 
@@ -417,9 +434,9 @@ def rtborn_adjoint(maps: BornMaps, f_mhz, d: torch.Tensor, gemm: str = "bf16x9",
     if out is None:
         out = torch.empty((maps.grid.ny, maps.grid.nx), dtype=torch.float32, device=maps.T.device)
     g = maps._grid_struct()
-    _L.check(ctx.h, ctx.lib.rtborn_adjoint(ctx.h, C.byref(g), maps.ring_radius, maps.n_tx, _ptr(maps.T),
-                                           _ptr(maps.A), nf, fa, _ptr(d), GEMM_MODES[gemm], _ptr(out),
-                                           _stream(stream)))
+    _L.check(ctx.h, ctx.lib.rtborn_adjoint_abs(ctx.h, C.byref(g), maps.ring_radius, maps.n_tx, _ptr(maps.T),
+                                               _ptr(maps.A), _ptr(maps.L), float(maps.y), nf, fa, _ptr(d),
+                                               GEMM_MODES[gemm], _ptr(out), _stream(stream)))
     return out
 
 

@@ -21,7 +21,8 @@ EXPORTED = [
     "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt_last_error", "rt_ctx_reserve",
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
     "rt_tof_forward_noalloc", "rt_batch_run", "rtborn_maps", "rtborn_apply", "rtborn_adjoint",
-    "rt_csr_matvec", "rt_csr_rmatvec", "rt_bspline_coef",
+    "rt_csr_matvec", "rt_csr_rmatvec", "rt_bspline_coef", "rtborn_maps_abs", "rtborn_apply_abs",
+    "rtborn_adjoint_abs",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_BF16X9 = 0, 1
 ABI_VERSION = 2   # layout of RtOptions below
@@ -101,6 +102,11 @@ def load():
                                    C.c_int32, vp, vp]
         L.rtborn_adjoint.argtypes = [vp, P(RtGrid), C.c_double, C.c_int32, vp, vp, C.c_int32, P(C.c_double), vp,
                                      C.c_int32, vp, vp]
+        L.rtborn_maps_abs.argtypes = [vp, P(RtProblem), P(RtOptions), C.c_int32, vp, vp, vp, vp, vp]
+        L.rtborn_apply_abs.argtypes = [vp, P(RtGrid), C.c_double, C.c_int32, vp, vp, vp, C.c_double, C.c_int32,
+                                       P(C.c_double), vp, C.c_int32, vp, vp]
+        L.rtborn_adjoint_abs.argtypes = [vp, P(RtGrid), C.c_double, C.c_int32, vp, vp, vp, C.c_double, C.c_int32,
+                                         P(C.c_double), vp, C.c_int32, vp, vp]
         _lib = L
         return L
 

@@ -27,6 +27,14 @@
 // T of one another, so the earliest alone would choose among them by
 // rounding; the penalty takes the ray passing closest to the node.
 //
+// Absorption (the Appendix: wavenumber k + i alpha, alpha = alpha0 omega^y,
+// the absorption amplitude accumulated along the ray): with an alpha0 map each
+// fan ray also carries Lambda = int alpha0 ds (trapezoid, Kahan-summed), a
+// node's candidate is Lambda + alpha0 a from the foot, and the node keeps the
+// Lambda of the candidate that supplies A (a third 64-bit atomicMin with the
+// same score; an exact tie of scores may pair A and Lambda of different rays).
+// E_t = A_t exp(-omega_s^y Lambda_t) exp(i omega T_t), omega_s in rad/s.
+//
 // Born map (rtborn_apply), per frequency f (omega = 2 pi f rad/us):
 //     d[f][e][r] = omega^2 h^2 sum_{|x| < R} E_e(x) E_r(x) dc(x),  e != r,
 // E_t = A_t exp(i omega T_t) over the nodes inside the ring (a compact list).
@@ -55,12 +63,13 @@ namespace {
 constexpr double kPiB = 3.14159265358979323846;
 
 // Nodal fields for the Born march: (c, h dc/dx, h dc/dy, s) and
-// (h^2 d2c/dx2, h^2 d2c/dxdy, h^2 d2c/dy2, 0), mm/us units.
+// (h^2 d2c/dx2, h^2 d2c/dxdy, h^2 d2c/dy2, alpha0 per mm of path), mm/us units.
 struct __align__(32) BNode {
     float4 a, b;
 };
 
-__global__ void k_born_pack(rt_grid g, const double* __restrict__ c_mps, BNode* __restrict__ out, int* bad) {
+__global__ void k_born_pack(rt_grid g, const double* __restrict__ c_mps, const double* __restrict__ alpha0,
+                            BNode* __restrict__ out, int* bad) {
     const int nx = g.nx, ny = g.ny;
     const long long n = (long long)nx * ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -77,20 +86,29 @@ __global__ void k_born_pack(rt_grid g, const double* __restrict__ c_mps, BNode* 
             hyy = C(i, j + 1) - 2.0 * c + C(i, j - 1);
             hxy = 0.25 * (C(i + 1, j + 1) - C(i - 1, j + 1) - C(i + 1, j - 1) + C(i - 1, j - 1));
         }
+        float al = 0.f;
+        if (alpha0) {
+            const double a0 = alpha0[k];
+            if (!(a0 >= 0.0) || !(a0 < 1e300)) atomicExch(bad, 1);
+            al = (float)(1e-3 * a0);   // per mm of path
+        }
         BNode o;
         o.a = make_float4((float)c, (float)gx, (float)gy, (float)(1.0 / c));
-        o.b = make_float4((float)hxx, (float)hxy, (float)hyy, 0.0f);
+        o.b = make_float4((float)hxx, (float)hxy, (float)hyy, al);
         out[k] = o;
     }
 }
 
-// Register cache of one cell: the seven fields in bilinear coefficient form
-// f = a + tx bx + ty (by + tx bxy), built from the cell's four nodes.
+// Register cache of one cell: the seven fields (eight with absorption) in
+// bilinear coefficient form f = a + tx bx + ty (by + tx bxy), built from the
+// cell's four nodes.
+template <bool ABS>
 struct BornCell {
     const BNode* __restrict__ F;
     int nx, ny, pi, pj;
     float c0, c1, c2, c3, x0, x1, x2, x3, y0, y1, y2, y3, s0, s1, s2, s3;
     float p0, p1, p2, p3, q0, q1, q2, q3, r0, r1, r2, r3;   // hxx, hxy, hyy
+    float l0, l1, l2, l3;                                   // alpha0 (ABS only)
 
     __device__ __forceinline__ void load(int i, int j) {
         pi = i;
@@ -109,6 +127,9 @@ struct BornCell {
         BC_(p0, p1, p2, p3, b00.x, b10.x, b01.x, b11.x)
         BC_(q0, q1, q2, q3, b00.y, b10.y, b01.y, b11.y)
         BC_(r0, r1, r2, r3, b00.z, b10.z, b01.z, b11.z)
+        if (ABS) {
+            BC_(l0, l1, l2, l3, b00.w, b10.w, b01.w, b11.w)
+        }
 #undef BC_
     }
 
@@ -143,6 +164,7 @@ struct BornCell {
         hyy = r0 + tx * r1 + ty * (r2 + tx * r3);
     }
     __device__ __forceinline__ float slow(float tx, float ty) const { return s0 + tx * s1 + ty * (s2 + tx * s3); }
+    __device__ __forceinline__ float alpha(float tx, float ty) const { return l0 + tx * l1 + ty * (l2 + tx * l3); }
 };
 
 // ray and paraxial right-hand sides at stage direction (ex, ey)
@@ -164,7 +186,8 @@ struct BornRay {
 
 // One RK4 step of length H (cells). Stage 1 has already been evaluated at S
 // (c1.., passed in), since the deposit of S needs it.
-__device__ __forceinline__ void born_rk4(BornCell& C, const BornRay& B, float H, float c, float gx, float gy,
+template <typename CellB>
+__device__ __forceinline__ void born_rk4(CellB& C, const BornRay& B, float H, float c, float gx, float gy,
                                          float hxx, float hxy, float hyy, BornRay& N) {
     const float Hh = 0.5f * H, H6 = H / 6.f;
     const float dx = B.S.d.hx(), dy = B.S.d.hy();
@@ -212,6 +235,7 @@ struct FanArgs {
     float eta;                    // us: penalty of the squared distance (cells) to the ray, amplitude choice
     unsigned* tfirst;             // [n_tx][ny*nx] order-preserving bits of the first arrival
     unsigned long long* near;     // [n_tx][ny*nx] (ordered bits of T + eta b^2) << 32 | A bits
+    unsigned long long* lam;      // [n_tx][ny*nx] the same score << 32 | bits of Lambda (absorption only)
     long long nn;
     unsigned long long* steps;    // RK4 steps taken (summed over rays)
 };
@@ -229,10 +253,11 @@ struct FanRef {
 // score = T_cand - T_ref + eta b^2. T and T_ref lie within a factor of two of
 // each other, so their difference is exact and the score resolves ~1e-6 us
 // where T itself rounds at ~1e-5 us.
+template <bool ABS>
 __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, const FanRef& F,
                                              unsigned* __restrict__ tfirst, unsigned long long* __restrict__ near,
-                                             const BornRay& B, float T, float Tc, float c, float s,
-                                             float inv_ct_h) {
+                                             unsigned long long* __restrict__ lam, const BornRay& B, float T,
+                                             float Tc, float c, float s, float inv_ct_h, float Lm, float al_h) {
     const float fx = B.S.fx, fy = B.S.fy;
     const bool oi = fx >= 0.5f, oj = fy >= 0.5f;
     const float D0x = oi ? 1.f - fx : -fx, D0y = oj ? 1.f - fy : -fy;
@@ -263,14 +288,17 @@ __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, co
                     const float Tref = F.h_ct * sqrtf(ux * ux + uy * uy);
                     const float score = ((T - Tref) + ext) + A.eta * ac * ac;
                     const float amp = sqrtf(c * inv_ct_h / Qc);
-                    atomicMin(near + node, ((unsigned long long)f2ord(score) << 32) | __float_as_uint(amp));
+                    const unsigned long long sk = (unsigned long long)f2ord(score) << 32;
+                    atomicMin(near + node, sk | __float_as_uint(amp));
+                    // Lambda >= 0: its float bits order like its value
+                    if (ABS) atomicMin(lam + node, sk | __float_as_uint(fmaxf(Lm + al_h * al, 0.f)));
                 }
             }
         }
     }
 }
 
-template <int BLOCK, int MINB>
+template <int BLOCK, int MINB, bool ABS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const FanArgs A, const BNode* __restrict__ field) {
     const long long id = blockIdx.x * (long long)BLOCK + threadIdx.x;
     if (id >= (long long)G.n_tx * A.K) return;
@@ -285,6 +313,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
     const double theta = a_min + k * step;
     unsigned* __restrict__ tfirst = A.tfirst + (size_t)t * A.nn;
     unsigned long long* __restrict__ near = A.near + (size_t)t * A.nn;
+    unsigned long long* __restrict__ lam = ABS ? A.lam + (size_t)t * A.nn : nullptr;
 
     BornRay B;
     {
@@ -298,7 +327,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
         B.S.ly = (float)((v - fv) - (double)B.S.fy);
         B.S.d.set(theta);
     }
-    BornCell C;
+    BornCell<ABS> C;
     C.F = field;
     C.nx = G.nx;
     C.ny = G.ny;
@@ -317,6 +346,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
     B.P = 1.f / c_t;
     float s_prev = C.slow(tx, ty);
     float T = 0.f, Tc = 0.f;       // Kahan sum of the trapezoid increments
+    float a_prev = ABS ? C.alpha(tx, ty) : 0.f;
+    float Lm = 0.f, Lc = 0.f;      // Kahan sum of the absorption path integral (ABS)
     int safe = 0, nsteps = 0;
     for (int m = 1; m <= G.max_steps_i; ++m) {
         BornRay N;
@@ -337,7 +368,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
         Tc = (tt - T) - y;
         T = tt;
         s_prev = s;
-        born_deposit(G, A, F, tfirst, near, B, T, Tc, c, s, inv_ct_h);
+        float al_h = 0.f;
+        if (ABS) {
+            const float a = C.alpha(tx, ty);
+            const float ya = half_ds * (a_prev + a) - Lc;
+            const float tl = Lm + ya;
+            Lc = (tl - Lm) - ya;
+            Lm = tl;
+            a_prev = a;
+            al_h = a * A.hf;   // per cell of the along-ray offset
+        }
+        born_deposit<ABS>(G, A, F, tfirst, near, lam, B, T, Tc, c, s, inv_ct_h, Lm - Lc, al_h);
     }
     const unsigned mask = __activemask();
     const unsigned tot = __reduce_add_sync(mask, (unsigned)nsteps);
@@ -345,24 +386,34 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
 }
 
 __global__ void k_born_unpack(const unsigned* __restrict__ tfirst, const unsigned long long* __restrict__ near,
-                              long long n, float* __restrict__ T, float* __restrict__ A) {
+                              const unsigned long long* __restrict__ lam, long long n, float* __restrict__ T,
+                              float* __restrict__ A, float* __restrict__ L) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const unsigned tf = tfirst[k];
         const unsigned long long key = near[k];
+        const bool none = tf == 0xffffffffu || key == ~0ull;
         T[k] = tf == 0xffffffffu ? __uint_as_float(0x7f800000u) : ord2f(tf);
-        A[k] = (tf == 0xffffffffu || key == ~0ull) ? 0.f : __uint_as_float((unsigned)key);
+        A[k] = none ? 0.f : __uint_as_float((unsigned)key);
+        if (L) {
+            const unsigned long long lk = lam[k];
+            L[k] = (none || lk == ~0ull) ? 0.f : __uint_as_float((unsigned)lk);
+        }
     }
 }
 
-// E[t][p] = A exp(i 2 pi frac(f T)) at inside node idx[p]; W = scale dc E.
+// E[t][p] = A exp(-wy L) exp(i 2 pi frac(f T)) at inside node idx[p] (L and
+// wy = omega_s^y only with absorption); W = scale dc E.
 __global__ void k_born_efield(int n_in, const int* __restrict__ idx, long long nn, const float* __restrict__ Tm,
-                              const float* __restrict__ Am, float f_hi, float f_lo, float scale,
-                              const float* __restrict__ dc, float2* __restrict__ E, float2* __restrict__ W) {
+                              const float* __restrict__ Am, const float* __restrict__ Lm, float wy, float f_hi,
+                              float f_lo, float scale, const float* __restrict__ dc, float2* __restrict__ E,
+                              float2* __restrict__ W) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_in) return;
     const int t = blockIdx.y;
     const int k = idx[p];
-    const float Tv = Tm[(size_t)t * nn + k], Av = Am[(size_t)t * nn + k];
+    const float Tv = Tm[(size_t)t * nn + k];
+    float Av = Am[(size_t)t * nn + k];
+    if (Lm) Av *= expf(-wy * Lm[(size_t)t * nn + k]);
     float2 e = make_float2(0.f, 0.f);
     if (Tv < __uint_as_float(0x7f800000u)) {
         // frac(f T) with f = f_hi + f_lo: the product's rounding error by FMA
@@ -548,6 +599,18 @@ int born_ws(rt_ctx* ctx, int n_tx, int n_in, cudaStream_t s) {
     return rc;
 }
 
+// absorption power law: y in [0, 3], frequencies >= 0 and omega_s^y finite in
+// FP32 at every frequency
+int check_power_law(rt_ctx* ctx, double y, int32_t n_freq, const double* f_mhz) {
+    if (!(y >= 0.0 && y <= 3.0)) return bfail(ctx, RT_EINVAL, "power-law exponent y must be in [0, 3]");
+    for (int f = 0; f < n_freq; ++f) {
+        if (!(f_mhz[f] >= 0.0)) return bfail(ctx, RT_EINVAL, "frequencies must be >= 0 with absorption");
+        const double w = std::pow(2.0 * rt::kPiB * f_mhz[f] * 1e6, y);
+        if (!(w < 3.0e38)) return bfail(ctx, RT_EINVAL, "omega^y overflows at this frequency and exponent");
+    }
+    return RT_OK;
+}
+
 void split_freq(double f, float* hi, float* lo) {
     *hi = (float)f;
     *lo = (float)(f - (double)*hi);
@@ -559,6 +622,11 @@ extern "C" {
 
 int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int32_t fan_rays, float* T_out,
                 float* A_out, void* stream) {
+    return rtborn_maps_abs(ctx, prob, opt, fan_rays, nullptr, T_out, A_out, nullptr, stream);
+}
+
+int rtborn_maps_abs(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int32_t fan_rays,
+                    const double* alpha0, float* T_out, float* A_out, float* L_out, void* stream) {
     if (!ctx) return RT_EINVAL;
     ctx->err.clear();
     cudaStream_t s = (cudaStream_t)stream;
@@ -570,6 +638,8 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     if (opt->interpolator != RT_BILINEAR)
         return bfail(ctx, RT_EINVAL, "fan maps sample the field bilinearly (interpolator RT_BILINEAR)");
     if (!T_out || !A_out) return bfail(ctx, RT_EINVAL, "T and A outputs are required");
+    if (alpha0 && !L_out) return bfail(ctx, RT_EINVAL, "an alpha0 map needs the L_out output");
+    const bool lossy = alpha0 != nullptr;
     if (opt->ds_mm > (prob ? prob->grid.h_mm : 0.0)) return bfail(ctx, RT_EINVAL, "ds_mm must not exceed the grid spacing");
     rt::Geom G;
     int rc = rt::make_geom(ctx, prob, opt, &G);
@@ -580,17 +650,18 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     rc = grow(ctx, &ctx->born_field, &ctx->born_field_bytes, sizeof(rt::BNode) * (size_t)nn, s, "Born field");
     if (rc) return rc;
     const size_t n_ent = (size_t)nn * prob->n_tx;
-    rc = grow(ctx, &ctx->born_keys, &ctx->born_keys_bytes, (sizeof(unsigned long long) + sizeof(unsigned)) * n_ent, s,
-              "fan-map keys");
+    const size_t key_bytes = ((lossy ? 2 : 1) * sizeof(unsigned long long) + sizeof(unsigned)) * n_ent;
+    rc = grow(ctx, &ctx->born_keys, &ctx->born_keys_bytes, key_bytes, s, "fan-map keys");
     if (rc) return rc;
     unsigned long long* near = (unsigned long long*)ctx->born_keys;
-    unsigned* tfirst = (unsigned*)(near + n_ent);
+    unsigned long long* lam = lossy ? near + n_ent : nullptr;
+    unsigned* tfirst = (unsigned*)(near + (lossy ? 2 : 1) * n_ent);
     e = cudaMemsetAsync(ctx->dflag, 0, sizeof(int), s);
     if (e != cudaSuccess) return bcuda(ctx, e, "flag reset");
     G.bad_field = ctx->dflag;
     rt::k_born_pack<<<std::min<long long>((nn + 255) / 256, 152 * 32), 256, 0, s>>>(
-        prob->grid, prob->c_mps, (rt::BNode*)ctx->born_field, ctx->dflag);
-    e = cudaMemsetAsync(ctx->born_keys, 0xff, (sizeof(unsigned long long) + sizeof(unsigned)) * n_ent, s);
+        prob->grid, prob->c_mps, alpha0, (rt::BNode*)ctx->born_field, ctx->dflag);
+    e = cudaMemsetAsync(ctx->born_keys, 0xff, key_bytes, s);
     if (e != cudaSuccess) return bcuda(ctx, e, "key reset");
     rt::FanArgs A;
     A.K = fan_rays;
@@ -599,6 +670,7 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     A.eta = RTBORN_ETA_US;
     A.tfirst = tfirst;
     A.near = near;
+    A.lam = lam;
     A.nn = nn;
     A.steps = ctx->counters + 7;
     e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
@@ -606,12 +678,13 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
     const long long rays = (long long)prob->n_tx * fan_rays;
     const rt::BNode* fld = (const rt::BNode*)ctx->born_field;
     // kernel variants: resident 128-thread blocks per SM the kernel is compiled for
-    const int minb = opt->blocks_per_sm ? opt->blocks_per_sm : 6;
+    const int minb = opt->blocks_per_sm ? opt->blocks_per_sm : (lossy ? 5 : 6);   // lossy at 6 spills
     const unsigned blocks = (unsigned)((rays + 127) / 128);
     switch (minb) {
-#define FAN_V(MB)                                                \
-    case MB:                                                     \
-        rt::k_born_fan<128, MB><<<blocks, 128, 0, s>>>(G, A, fld); \
+#define FAN_V(MB)                                                              \
+    case MB:                                                                   \
+        if (lossy) rt::k_born_fan<128, MB, true><<<blocks, 128, 0, s>>>(G, A, fld);  \
+        else rt::k_born_fan<128, MB, false><<<blocks, 128, 0, s>>>(G, A, fld);     \
         break;
         FAN_V(4)
         FAN_V(5)
@@ -622,7 +695,7 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
             return bfail(ctx, RT_EINVAL, "rtborn_maps: blocks_per_sm must be 0 (= 6), 4, 5, 6 or 8");
     }
     rt::k_born_unpack<<<(unsigned)std::min<long long>(((long long)n_ent + 255) / 256, 152 * 64), 256, 0, s>>>(
-        tfirst, near, (long long)n_ent, T_out, A_out);
+        tfirst, near, lam, (long long)n_ent, T_out, A_out, lossy ? L_out : nullptr);
     e = cudaGetLastError();
     ctx->last_stream = s;
     return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "fan-map kernels");
@@ -631,11 +704,19 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
 int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
                  const float* A, int32_t n_freq, const double* f_mhz, const float* dc_mps, int32_t gemm_mode,
                  float* d_out, void* stream) {
+    return rtborn_apply_abs(ctx, grid, ring_radius_mm, n_tx, T, A, nullptr, 0.0, n_freq, f_mhz, dc_mps, gemm_mode,
+                            d_out, stream);
+}
+
+int rtborn_apply_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                     const float* A, const float* L, double y, int32_t n_freq, const double* f_mhz,
+                     const float* dc_mps, int32_t gemm_mode, float* d_out, void* stream) {
     if (!ctx) return RT_EINVAL;
     ctx->err.clear();
     cudaStream_t s = (cudaStream_t)stream;
     int rc = check_born_args(ctx, grid, ring_radius_mm, n_tx, T, A, n_freq, f_mhz, gemm_mode);
     if (rc) return rc;
+    if (L && (rc = check_power_law(ctx, y, n_freq, f_mhz))) return rc;
     if (!dc_mps || (!d_out && n_freq > 0)) return bfail(ctx, RT_EINVAL, "dc_mps and d_out are required");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return bcuda(ctx, e, "cudaSetDevice");
@@ -656,7 +737,8 @@ int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_
         split_freq(f_mhz[f], &fh, &fl);
         const double om = 2.0 * rt::kPiB * f_mhz[f];
         const float scale = (float)(om * om * grid->h_mm * grid->h_mm);
-        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, fh, fl, scale, dc_mps, E, W);
+        const float wy = L ? (float)std::pow(2.0 * rt::kPiB * f_mhz[f] * 1e6, y) : 0.f;
+        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, L, wy, fh, fl, scale, dc_mps, E, W);
         // d(r, e) = sum_p W(p, r) E(p, e): column-major D = W^T E, stored at r + e n = d[e][r]
         rc = gemm(ctx, h, gemm_mode, CUBLAS_OP_T, CUBLAS_OP_N, n_tx, n_tx, n_in, W, n_in, E, n_in,
                   d + (size_t)f * n_tx * n_tx, n_tx);
@@ -671,11 +753,19 @@ int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_
 int rtborn_adjoint(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
                    const float* A, int32_t n_freq, const double* f_mhz, const float* d_in, int32_t gemm_mode,
                    float* dc_out, void* stream) {
+    return rtborn_adjoint_abs(ctx, grid, ring_radius_mm, n_tx, T, A, nullptr, 0.0, n_freq, f_mhz, d_in, gemm_mode,
+                              dc_out, stream);
+}
+
+int rtborn_adjoint_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
+                       const float* A, const float* L, double y, int32_t n_freq, const double* f_mhz,
+                       const float* d_in, int32_t gemm_mode, float* dc_out, void* stream) {
     if (!ctx) return RT_EINVAL;
     ctx->err.clear();
     cudaStream_t s = (cudaStream_t)stream;
     int rc = check_born_args(ctx, grid, ring_radius_mm, n_tx, T, A, n_freq, f_mhz, gemm_mode);
     if (rc) return rc;
+    if (L && (rc = check_power_law(ctx, y, n_freq, f_mhz))) return rc;
     if (!dc_out || (!d_in && n_freq > 0)) return bfail(ctx, RT_EINVAL, "d_in and dc_out are required");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return bcuda(ctx, e, "cudaSetDevice");
@@ -700,7 +790,8 @@ int rtborn_adjoint(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int3
         split_freq(f_mhz[f], &fh, &fl);
         const double om = 2.0 * rt::kPiB * f_mhz[f];
         const float scale = (float)(om * om * grid->h_mm * grid->h_mm);
-        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, fh, fl, 0.f, nullptr, E, nullptr);
+        const float wy = L ? (float)std::pow(2.0 * rt::kPiB * f_mhz[f] * 1e6, y) : 0.f;
+        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, L, wy, fh, fl, 0.f, nullptr, E, nullptr);
         rt::k_conj_nodiag<<<(n_tx * n_tx + 255) / 256, 256, 0, s>>>(d + (size_t)f * n_tx * n_tx, Dc, n_tx);
         // V(p, e) = sum_r E(p, r) Dc(r, e)
         rc = gemm(ctx, h, gemm_mode, CUBLAS_OP_N, CUBLAS_OP_N, n_in, n_tx, n_tx, E, n_in, Dc, n_tx, V, n_in);
