@@ -63,7 +63,14 @@
  *      (Lambda + alpha0 a), and taken from the candidate that supplies A; then
  *      A_abs = exp(-omega_s^y Lambda) with omega_s = 2 pi f in rad/s, so
  *      E_t = A_t exp(-omega_s^y Lambda_t) exp(i omega T_t). Without alpha0,
- *      Lambda = 0 (the maps of B1-B5 exactly).
+ *      Lambda = 0 (the maps of B1-B5 exactly);
+ *   B10 with orc_set_interpolator(1) (the paper's choice for ray-Born, Sec.
+ *      3.3.1: the cubic B-spline gives analytic first and second derivatives)
+ *      c, its gradient and its Hessian are the interpolating B-spline of the
+ *      nodal c and its exact derivatives, and s is the spline of the nodal s
+ *      (the spline of oracle.c's readings S1 and S4: coefficients from
+ *      orc_bspline_coef, 4 x 4 per sample, mirror at the edges); alpha0 stays
+ *      bilinear.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -80,10 +87,13 @@ typedef struct {
     int nx, ny;
     double h, x0, y0;
     double* v[F_N]; /* nodal fields, [ny*nx] each */
+    double *ac, *as; /* B10: spline coefficients of c and s, or NULL */
 } BField;
 
 static void bfield_free(BField* F) {
     for (int q = 0; q < F_N; ++q) free(F->v[q]);
+    free(F->ac);
+    free(F->as);
     memset(F, 0, sizeof(*F));
 }
 
@@ -124,7 +134,39 @@ static int bfield_make(BField* F, const orc_grid* g, const double* c_mps, const 
                 F->v[F_HXY][k] = (c[k + nx + 1] - c[k + nx - 1] - c[k - nx + 1] + c[k - nx - 1]) / (4 * h * h);
             }
         }
+    if (orc_get_interpolator() == 1) {
+        F->ac = malloc(n * sizeof(double));
+        F->as = malloc(n * sizeof(double));
+        if (!F->ac || !F->as || orc_bspline_coef(g, c, F->ac, 0) || orc_bspline_coef(g, F->v[F_S], F->as, 0)) {
+            bfield_free(F);
+            return ORC_ENOMEM;
+        }
+    }
     return ORC_OK;
+}
+
+/* B10: uniform cubic B-spline basis at t in [0, 1) for coefficients i-1..i+2,
+ * with its first and second derivatives in t */
+static void basis2(double t, double b[4], double d1[4], double d2[4]) {
+    const double u = 1.0 - t;
+    b[0] = u * u * u / 6.0;
+    b[1] = (3.0 * t * t * t - 6.0 * t * t + 4.0) / 6.0;
+    b[2] = (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) / 6.0;
+    b[3] = t * t * t / 6.0;
+    d1[0] = -u * u / 2.0;
+    d1[1] = (3.0 * t * t - 4.0 * t) / 2.0;
+    d1[2] = (-3.0 * t * t + 2.0 * t + 1.0) / 2.0;
+    d1[3] = t * t / 2.0;
+    d2[0] = u;
+    d2[1] = 3.0 * t - 2.0;
+    d2[2] = -3.0 * t + 1.0;
+    d2[3] = t;
+}
+
+static int mirror_ix(int v, int n) {
+    if (v < 0) v = -v;
+    if (v > n - 1) v = 2 * (n - 1) - v;
+    return v;
 }
 
 /* all fields at (x, y), bilinear; the cell index is clamped into the grid */
@@ -142,6 +184,34 @@ static void bsample(const BField* F, double x, double y, double f[F_N]) {
     for (int q = 0; q < F_N; ++q) {
         const double* a = F->v[q];
         f[q] = w00 * a[k00] + w10 * a[k10] + w01 * a[k01] + w11 * a[k11];
+    }
+    if (F->ac) {   /* B10: c, its derivatives and s from the splines (alpha0 stays bilinear) */
+        double bx[4], dx1[4], dx2[4], by[4], dy1[4], dy2[4];
+        basis2(tx, bx, dx1, dx2);
+        basis2(ty, by, dy1, dy2);
+        double c = 0, cx = 0, cy = 0, cxx = 0, cxy = 0, cyy = 0, sv = 0;
+        for (int b = 0; b < 4; ++b) {
+            const size_t row = (size_t)mirror_ix(j - 1 + b, F->ny) * F->nx;
+            for (int a = 0; a < 4; ++a) {
+                const size_t k = row + (size_t)mirror_ix(i - 1 + a, F->nx);
+                const double ak = F->ac[k];
+                c += bx[a] * by[b] * ak;
+                cx += dx1[a] * by[b] * ak;
+                cy += bx[a] * dy1[b] * ak;
+                cxx += dx2[a] * by[b] * ak;
+                cxy += dx1[a] * dy1[b] * ak;
+                cyy += bx[a] * dy2[b] * ak;
+                sv += bx[a] * by[b] * F->as[k];
+            }
+        }
+        const double h = F->h;
+        f[F_C] = c;
+        f[F_GX] = cx / h;
+        f[F_GY] = cy / h;
+        f[F_HXX] = cxx / (h * h);
+        f[F_HXY] = cxy / (h * h);
+        f[F_HYY] = cyy / (h * h);
+        f[F_S] = sv;
     }
 }
 

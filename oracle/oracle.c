@@ -139,6 +139,8 @@ int orc_set_interpolator(int32_t k) {
     return ORC_OK;
 }
 
+int orc_get_interpolator(void) { return g_interp; }
+
 /* S1: the interpolation matrix of one axis, (B a)_i = (a_{i-1} + 4 a_i +
  * a_{i+1}) / 6 with the mirror extension a_{-1} = a_1, a_n = a_{n-2}: its
  * sub- and super-diagonal entries of row i (the diagonal is 4/6). */

@@ -105,6 +105,7 @@ int orc_set_integrator(int32_t k);
  * 1 = interpolating cubic B-spline with control points at the nodes and
  * analytic gradient (Sec. 3.3.1). Returns ORC_EINVAL for other values. */
 int orc_set_interpolator(int32_t k);
+int orc_get_interpolator(void);
 
 /* Control coefficients a = P^-1 f of the interpolating cubic B-spline of the
  * nodal field f[ny*nx] (mirror boundary; P is the spline's value at the nodes,

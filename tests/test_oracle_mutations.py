@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_absorption_pins as apins
+from tests import test_oracle_born_bspline_pins as bbpins
 from tests import test_oracle_born_pins as bpins
 from tests import test_oracle_bspline_pins as spins
 from tests import test_oracle_pins as pins
@@ -206,6 +207,41 @@ def test_bspline_mutant_is_caught(name, tmp_path):
     old, new = BSPLINE_MUTANTS[name]
     L = _compile_mutant(tmp_path, name, "oracle.c", old, new)
     if _survives(L, BSPLINE_PINS):
+        pytest.fail(f"mutant {name} survived every pin")
+
+
+BORN_BSPLINE_MUTANTS = {
+    "born_bs_second_derivative_basis": ("d2[1] = 3.0 * t - 2.0;", "d2[1] = 3.0 * t - 1.0;"),
+    "born_bs_hessian_scale": ("f[F_HXX] = cxx / (h * h);", "f[F_HXX] = cxx / h;"),
+    "born_bs_cross_term": ("cxy += dx1[a] * dy1[b] * ak;", "cxy += dx2[a] * by[b] * ak;"),
+    "born_bs_gradient_axis": ("cy += bx[a] * dy1[b] * ak;", "cy += dx1[a] * by[b] * ak;"),
+    "born_bs_no_prefilter": ("orc_bspline_coef(g, c, F->ac, 0)", "!memcpy(F->ac, c, n * sizeof(double))"),
+}
+
+
+def _born_in_bspline(pin):
+    def run(orc):
+        with orc.interpolator("bspline"):
+            pin(orc)
+    return run
+
+
+BORN_BSPLINE_PINS = [
+    bbpins.test_bspline_fan_ray_homogeneous_straight,
+    lambda orc: bbpins.test_bspline_fan_ray_linear_gradient_closed_form_Q(orc, 0.2),
+    lambda orc: bbpins.test_bspline_paraxial_Q_matches_auxiliary_rays(orc, 0, 0.1),
+    lambda orc: bbpins.test_bspline_paraxial_Q_matches_auxiliary_rays(orc, 40, -0.25),
+    bbpins.test_bspline_maps_brute_force,
+    bbpins.test_bspline_maps_homogeneous_and_fermat,
+]
+BORN_BSPLINE_PINS = [_born_in_bspline(p) for p in BORN_BSPLINE_PINS]
+
+
+@pytest.mark.parametrize("name", sorted(BORN_BSPLINE_MUTANTS))
+def test_born_bspline_mutant_is_caught(name, tmp_path):
+    old, new = BORN_BSPLINE_MUTANTS[name]
+    L = _compile_mutant(tmp_path, name, "born.c", old, new)
+    if _survives(L, BORN_BSPLINE_PINS):
         pytest.fail(f"mutant {name} survived every pin")
 
 
