@@ -112,9 +112,9 @@ typedef struct {
     int32_t integrator;    /* enum rt_integrator: the ray stepper of every trace of
                             the ToF calls (rtborn_maps requires RT_RK4) */
     int32_t interpolator;  /* enum rt_interpolator: the field sampler of rt_link,
-                            rt_tof_forward, rt_tof_adjoint and rt_path_matrix
-                            (rt_batch_run, rt_tof_forward_noalloc and the rtborn_*
-                            calls require RT_BILINEAR) */
+                            rt_tof_forward, rt_tof_adjoint, rt_path_matrix and
+                            rtborn_maps (rt_batch_run and rt_tof_forward_noalloc
+                            require RT_BILINEAR) */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
@@ -353,7 +353,11 @@ enum rtborn_gemm {
  *   prob      grid, c_mps, n_tx, tx_xy_mm, ring_radius_mm (pairs ignored).
  *   opt       precision must be RT_FP32_COMP; ds_mm in (0, h]; blocks_per_sm
  *             picks the fan kernel variant (resident 128-thread blocks per SM
- *             it is compiled for): 0 (= 6), 4, 5, 6 or 8; others ignored.
+ *             it is compiled for): 0 (= 6, or 5 with absorption), 4, 5, 6 or 8;
+ *             interpolator RT_BSPLINE takes c, its gradient and its Hessian
+ *             from the interpolating cubic B-spline of c (analytic derivatives;
+ *             the paper's choice for ray-Born, Sec. 3.3.1) and s from the spline
+ *             of s, instead of the bilinear central differences; others ignored.
  *   fan_rays  rays per fan in [2, 2^20]; about 4 pi R / h covers the far side
  *             of the ring at one ray per half grid step.
  *   T_out     [n_tx][ny*nx] float out, us; +inf where no ray arrives.

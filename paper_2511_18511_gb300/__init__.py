@@ -361,12 +361,15 @@ class BornMaps:
 
 def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tensor] = None,
                 ctx: Optional[Context] = None, stream=None, out: Optional[BornMaps] = None,
-                blocks_per_sm: int = 0, alpha0: Optional[torch.Tensor] = None, y: float = 1.0) -> BornMaps:
+                blocks_per_sm: int = 0, alpha0: Optional[torch.Tensor] = None, y: float = 1.0,
+                interpolator: str = "bilinear") -> BornMaps:
     """Travel-time and amplitude maps of every transducer from fans of
     fan_rays rays traced with their paraxial rays (paper Sec. 3.5).
     blocks_per_sm selects the fan kernel variant (0 = default). With alpha0
     (float64 CUDA [ny, nx], Np (rad/s)^-y m^-1) the maps also carry the
-    absorption path integrals L and the exponent y (Appendix: alpha0 omega^y)."""
+    absorption path integrals L and the exponent y (Appendix: alpha0 omega^y).
+    interpolator "bspline" samples c, its gradient and Hessian, and s from the
+    interpolating cubic B-spline (the paper's choice for ray-Born)."""
     ctx = ctx or default_context(prob.c.device.index)
     g = prob.grid
     shape = (prob.n_tx, g.ny, g.nx)
@@ -383,7 +386,7 @@ def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tenso
         out.y = float(y)
     else:
         out.L = None
-    o = _opts(ds, precision="fp32c", blocks_per_sm=blocks_per_sm)
+    o = _opts(ds, precision="fp32c", blocks_per_sm=blocks_per_sm, interpolator=interpolator)
     ps = prob.struct(c)
     _L.check(ctx.h, ctx.lib.rtborn_maps_abs(ctx.h, C.byref(ps), C.byref(o), int(fan_rays), _ptr(alpha0),
                                             _ptr(out.T), _ptr(out.A), _ptr(out.L), _stream(stream)))

@@ -27,6 +27,12 @@
 // T of one another, so the earliest alone would choose among them by
 // rounding; the penalty takes the ray passing closest to the node.
 //
+// With the cubic B-spline sampler (rt_options.interpolator = RT_BSPLINE; the
+// paper's choice for ray-Born, Sec. 3.3.1) c, its gradient and its Hessian come
+// from the per-cell bicubic of the interpolating spline of c (the ToF path's
+// packed CellBS field: 16 coefficients cached per cell, derivatives by Horner)
+// and s from the bicubic of s; alpha0 stays bilinear.
+//
 // Absorption (the Appendix: wavenumber k + i alpha, alpha = alpha0 omega^y,
 // the absorption amplitude accumulated along the ray): with an alpha0 map each
 // fan ray also carries Lambda = int alpha0 ds (trapezoid, Kahan-summed), a
@@ -47,6 +53,7 @@
 // (diagonal of D zeroed): one GEMM and one column reduction per frequency.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -56,6 +63,7 @@
 
 #include "rt_internal.h"
 #include "rt_trace.cuh"
+#include "rt_bspline.cuh"
 
 namespace rt {
 namespace {
@@ -109,6 +117,12 @@ struct BornCell {
     float c0, c1, c2, c3, x0, x1, x2, x3, y0, y1, y2, y3, s0, s1, s2, s3;
     float p0, p1, p2, p3, q0, q1, q2, q3, r0, r1, r2, r3;   // hxx, hxy, hyy
     float l0, l1, l2, l3;                                   // alpha0 (ABS only)
+
+    __device__ __forceinline__ void init(const BNode* f, const CellBS<float>*, int nx_, int ny_) {
+        F = f;
+        nx = nx_;
+        ny = ny_;
+    }
 
     __device__ __forceinline__ void load(int i, int j) {
         pi = i;
@@ -164,6 +178,74 @@ struct BornCell {
         hyy = r0 + tx * r1 + ty * (r2 + tx * r3);
     }
     __device__ __forceinline__ float slow(float tx, float ty) const { return s0 + tx * s1 + ty * (s2 + tx * s3); }
+    __device__ __forceinline__ float alpha(float tx, float ty) const { return l0 + tx * l1 + ty * (l2 + tx * l3); }
+};
+
+// The same interface over the B-spline field: the 16 coefficients of the
+// current cell's bicubic of c in registers, c and its first and second
+// fraction derivatives by Horner; s from the cell's bicubic of s (L2); alpha0
+// bilinear from the node field (ABS only).
+template <bool ABS>
+struct BornCellS {
+    const CellBS<float>* __restrict__ B;
+    const BNode* __restrict__ F;
+    int nx, ny, pi, pj;
+    const CellBS<float>* pc;
+    float a[16];
+    float l0, l1, l2, l3;
+
+    __device__ __forceinline__ void init(const BNode* f, const CellBS<float>* b, int nx_, int ny_) {
+        F = f;
+        B = b;
+        nx = nx_;
+        ny = ny_;
+    }
+
+    __device__ __forceinline__ void load(int i, int j) {
+        pi = i;
+        pj = j;
+        i = min(max(i, 0), nx - 2);
+        j = min(max(j, 0), ny - 2);
+        pc = B + (size_t)j * (nx - 1) + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = pc->c[q];
+            a[4 * q] = v.x;
+            a[4 * q + 1] = v.y;
+            a[4 * q + 2] = v.z;
+            a[4 * q + 3] = v.w;
+        }
+        if (ABS) {
+            const BNode* p = F + (size_t)j * nx + i;
+            const float w00 = p[0].b.w, w10 = p[1].b.w, w01 = p[nx].b.w, w11 = p[nx + 1].b.w;
+            l0 = w00;
+            l1 = w10 - w00;
+            l2 = w01 - w00;
+            l3 = (w11 - w10) - (w01 - w00);
+        }
+    }
+
+    __device__ __forceinline__ void at(int ci, int cj, float u, float v, float& c, float& gx, float& gy, float& hxx,
+                                       float& hxy, float& hyy, float& tx, float& ty) {
+        int i, j;
+        if (cell_locate(ci, cj, u, v, pi, pj, i, j, tx, ty)) load(i, j);
+        const float tx3 = 3.f * tx, tx6 = 6.f * tx;
+        float r[4], d[4], e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float a0 = a[4 * q], a1 = a[4 * q + 1], a2 = a[4 * q + 2], a3 = a[4 * q + 3];
+            r[q] = a0 + tx * (a1 + tx * (a2 + tx * a3));
+            d[q] = a1 + tx * (2.f * a2 + tx3 * a3);
+            e[q] = 2.f * a2 + tx6 * a3;
+        }
+        c = r[0] + ty * (r[1] + ty * (r[2] + ty * r[3]));
+        gx = d[0] + ty * (d[1] + ty * (d[2] + ty * d[3]));
+        hxx = e[0] + ty * (e[1] + ty * (e[2] + ty * e[3]));
+        gy = r[1] + ty * (2.f * r[2] + 3.f * ty * r[3]);
+        hxy = d[1] + ty * (2.f * d[2] + 3.f * ty * d[3]);
+        hyy = 2.f * r[2] + 6.f * ty * r[3];
+    }
+    __device__ __forceinline__ float slow(float tx, float ty) const { return bicubic<float>(pc->s, tx, ty); }
     __device__ __forceinline__ float alpha(float tx, float ty) const { return l0 + tx * l1 + ty * (l2 + tx * l3); }
 };
 
@@ -298,8 +380,9 @@ __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, co
     }
 }
 
-template <int BLOCK, int MINB, bool ABS>
-__global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const FanArgs A, const BNode* __restrict__ field) {
+template <int BLOCK, int MINB, bool ABS, bool BS>
+__global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const FanArgs A, const BNode* __restrict__ field,
+                                                          const CellBS<float>* __restrict__ bsfield) {
     const long long id = blockIdx.x * (long long)BLOCK + threadIdx.x;
     if (id >= (long long)G.n_tx * A.K) return;
     if (*G.bad_field) return;   // c <= 0 or NaN somewhere: every node stays unreached
@@ -327,10 +410,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
         B.S.ly = (float)((v - fv) - (double)B.S.fy);
         B.S.d.set(theta);
     }
-    BornCell<ABS> C;
-    C.F = field;
-    C.nx = G.nx;
-    C.ny = G.ny;
+    typename std::conditional<BS, BornCellS<ABS>, BornCell<ABS>>::type C;
+    C.init(field, bsfield, G.nx, G.ny);
     C.load(B.S.ci, B.S.cj);
     const float H = G.Hf;
     const float half_ds = 0.5f * G.dsf;
@@ -635,8 +716,9 @@ int rtborn_maps_abs(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, 
     if (!(opt->ds_mm > 0) || !std::isfinite(opt->ds_mm)) return bfail(ctx, RT_EINVAL, "ds_mm must be > 0");
     if (fan_rays < 2 || fan_rays > (1 << 20)) return bfail(ctx, RT_EINVAL, "fan_rays must be in [2, 2^20]");
     if (opt->integrator != RT_RK4) return bfail(ctx, RT_EINVAL, "fan maps are traced with RK4 (integrator RT_RK4)");
-    if (opt->interpolator != RT_BILINEAR)
-        return bfail(ctx, RT_EINVAL, "fan maps sample the field bilinearly (interpolator RT_BILINEAR)");
+    if (opt->interpolator != RT_BILINEAR && opt->interpolator != RT_BSPLINE)
+        return bfail(ctx, RT_EINVAL, "unknown interpolator");
+    const bool spline = opt->interpolator == RT_BSPLINE;
     if (!T_out || !A_out) return bfail(ctx, RT_EINVAL, "T and A outputs are required");
     if (alpha0 && !L_out) return bfail(ctx, RT_EINVAL, "an alpha0 map needs the L_out output");
     const bool lossy = alpha0 != nullptr;
@@ -659,6 +741,17 @@ int rtborn_maps_abs(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, 
     e = cudaMemsetAsync(ctx->dflag, 0, sizeof(int), s);
     if (e != cudaSuccess) return bcuda(ctx, e, "flag reset");
     G.bad_field = ctx->dflag;
+    const rt::CellBS<float>* bsf = nullptr;
+    if (spline) {
+        // coefficients and per-cell bicubics of c and s (clears and sets the flag first)
+        rc = grow(ctx, (void**)&ctx->bs_coef, &ctx->bs_coef_bytes, 2 * sizeof(double) * (size_t)nn, s, "B-spline");
+        if (!rc) rc = grow(ctx, &ctx->born_bsf, &ctx->born_bsf_bytes,
+                           sizeof(rt::CellBS<float>) * (size_t)(G.nx - 1) * (size_t)(G.ny - 1), s, "B-spline field");
+        if (rc) return rc;
+        e = rt::launch_pack_bs(prob->grid, prob->c_mps, ctx->bs_coef, ctx->born_bsf, ctx->dflag, RT_FP32_COMP, s);
+        if (e != cudaSuccess) return bcuda(ctx, e, "B-spline pack");
+        bsf = (const rt::CellBS<float>*)ctx->born_bsf;
+    }
     rt::k_born_pack<<<std::min<long long>((nn + 255) / 256, 152 * 32), 256, 0, s>>>(
         prob->grid, prob->c_mps, alpha0, (rt::BNode*)ctx->born_field, ctx->dflag);
     e = cudaMemsetAsync(ctx->born_keys, 0xff, key_bytes, s);
@@ -681,10 +774,15 @@ int rtborn_maps_abs(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, 
     const int minb = opt->blocks_per_sm ? opt->blocks_per_sm : (lossy ? 5 : 6);   // lossy at 6 spills
     const unsigned blocks = (unsigned)((rays + 127) / 128);
     switch (minb) {
-#define FAN_V(MB)                                                              \
-    case MB:                                                                   \
-        if (lossy) rt::k_born_fan<128, MB, true><<<blocks, 128, 0, s>>>(G, A, fld);  \
-        else rt::k_born_fan<128, MB, false><<<blocks, 128, 0, s>>>(G, A, fld);     \
+#define FAN_V(MB)                                                                               \
+    case MB:                                                                                    \
+        if (spline) {                                                                           \
+            if (lossy) rt::k_born_fan<128, MB, true, true><<<blocks, 128, 0, s>>>(G, A, fld, bsf);   \
+            else rt::k_born_fan<128, MB, false, true><<<blocks, 128, 0, s>>>(G, A, fld, bsf);        \
+        } else {                                                                                \
+            if (lossy) rt::k_born_fan<128, MB, true, false><<<blocks, 128, 0, s>>>(G, A, fld, bsf);  \
+            else rt::k_born_fan<128, MB, false, false><<<blocks, 128, 0, s>>>(G, A, fld, bsf);       \
+        }                                                                                       \
         break;
         FAN_V(4)
         FAN_V(5)

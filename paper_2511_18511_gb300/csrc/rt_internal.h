@@ -36,6 +36,8 @@ struct rt_ctx {
     // inside-ring node list, per-frequency E / W(V) and small buffers, cuBLAS
     void* born_field = nullptr;
     size_t born_field_bytes = 0;
+    void* born_bsf = nullptr;       // per-cell bicubics of c and s (B-spline fans)
+    size_t born_bsf_bytes = 0;
     void* born_keys = nullptr;
     size_t born_keys_bytes = 0;
     int* born_idx = nullptr;

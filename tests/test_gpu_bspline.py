@@ -116,8 +116,7 @@ def test_bspline_path_matrix_matches_oracle(case, rt, prec):
 
 
 def test_bspline_differs_from_bilinear_and_bad_interpolator(case, rt):
-    """The option reaches the kernels, and unknown or unsupported samplers are
-    refused (batch, allocation-free and ray-Born calls sample bilinearly)."""
+    """The option reaches the kernels, and unknown samplers are refused."""
     w, prob, _, refs = case
     th = torch.as_tensor(refs["rk4"][0]["theta"], device="cuda")
     Tb, _ = rt.rt_tof_forward(prob, th, w.ds, precision="fp64", interpolator="bspline")
@@ -132,9 +131,10 @@ def test_bspline_differs_from_bilinear_and_bad_interpolator(case, rt):
     o.interpolator = 7
     assert L.rt_link(rt.default_context().h, C.byref(ps), C.byref(o), C.c_void_p(theta.data_ptr()), None, None,
                      None, None, None) == rt._L.RT_EINVAL
-    # ray-Born maps: full-size outputs, so nothing could be written out of bounds
+    # ray-Born maps take both samplers, not others (full-size outputs, so
+    # nothing could be written out of bounds)
     o = rt._opts(w.ds)
-    o.interpolator = rt.INTERPOLATORS["bspline"]
+    o.interpolator = 7
     T = torch.empty(prob.n_tx * w.grid.nx * w.grid.ny, dtype=torch.float32, device="cuda")
     A = torch.empty_like(T)
     assert L.rtborn_maps(rt.default_context().h, C.byref(ps), C.byref(o), 64, C.c_void_p(T.data_ptr()),
