@@ -304,7 +304,9 @@ def run_born(args):
             "e2e": {"value": data / e2e_s, "unit": "Born data/s",
                     "h2d_bytes_per_step": c_host.numel() * 8 + dc_host.numel() * 4,
                     "d2h_bytes_per_step": d_host.numel() * 8 + g_host.numel() * 4},
-            "gpu_launches": args.steps * (4 + (nf + 1) + (3 * nf + 1)),
+            # maps: pack, fan, unpack; apply: per frequency efield (+ cuBLAS), then
+            # zero_diag; adjoint: per frequency efield, conj_nodiag, reduce, then scatter
+            "gpu_launches": args.steps * (3 + (nf + 1) + (3 * nf + 1)),
             "library_launches": {"cublas_gemm": 2 * nf * args.steps},
             "clocks": clk}
     if not args.no_cpu_baseline:
@@ -651,7 +653,9 @@ def main():
                  "status_counts": res["counts"][:7], "link_ms": link_ms,
                  "adjoint_ms": float(np.mean(res["step_ms"]) - link_ms)},
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 5 * args.steps,
+        # per step: rt_link = k_pack, k_tx_phi, k_fan_mark, k_fan, k_link;
+        # rt_tof_adjoint = k_pack, k_tx_phi, k_adjoint, k_adjoint_finish
+        "gpu_launches": 9 * args.steps,
         "clocks": res["clocks"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
