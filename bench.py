@@ -4,9 +4,10 @@ RK4 step 0.02 mm, linking tolerance 1e-4 mm), FP32-compensated (headline)
 next to the plain FP64 GPU form, with the roofline of the dominant kernel
 and the FP64 CPU oracle timed on the host as a baseline.
 
-One step = rt_link from straight-line launch angles (cold start, travel time
-fused) + rt_tof_adjoint of the L2 misfit 0.5*||T - T_meas||^2, on inputs
-already resident in HBM. L2 is flushed (256 MB write) between timed steps.
+One step = rt_link from a cold start (a fan of 768 rays per transducer
+predicts every pair's first angle and bracket; travel time fused) +
+rt_tof_adjoint of the L2 misfit 0.5*||T - T_meas||^2, on inputs already
+resident in HBM. L2 is flushed (256 MB write) between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -35,6 +36,12 @@ UNIT = "linked rays/s"
 # combination, renormalisation, the trapezoid slowness sample and the exit
 # test; FMA = 2, div/sqrt = 1); the derivation is in the design notes.
 FLOP_PER_STEP = 219
+# Cold-start fan of the breast workload: 1.5 rays per transducer of the 512-ring.
+# A denser fan costs more fan rays (one balanced launch) but leaves fewer
+# linking traces, and the multi-trace pairs are what drags out the persistent
+# link kernel's drain: over four phantom seeds, link times averaged 108 ms at
+# 256 rays, 97 ms at 384, 99 at 512, 98 at 640, 94 at 768 and 102 at 1024.
+BREAST_FAN = 768
 FLOP_PER_BSPLINE_STEP = 387   # RK4 step with the bicubic sampler (counted in the design notes)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -339,7 +346,7 @@ def run_profile_case(args):
     pairs = pairs[pairs[:, 0] < args.profile]
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, pairs=pairs)
     for _ in range(2):
-        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision, fan_rays=BREAST_FAN)
         rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=r["tof"] * 0.999, precision=args.precision)
     torch.cuda.synchronize()
     ok, counts = rt.rt_status_counts()
@@ -489,7 +496,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(prec, out, g):
-        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, ctx=ctx, out=out)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, ctx=ctx, out=out, fan_rays=BREAST_FAN)
         rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, ctx=ctx, out=g)
         return r
 
@@ -515,7 +522,7 @@ def main():
         for k in range(steps):
             flush.zero_()
             ev[k][0].record(stream)
-            r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, ctx=ctx, out=out)
+            r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, ctx=ctx, out=out, fan_rays=BREAST_FAN)
             ev[k][1].record(stream)
             rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, ctx=ctx, out=g)
             ev[k][2].record(stream)
@@ -570,7 +577,7 @@ def main():
         flush.zero_()
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
-        r = rt.rt_link(prob, w.ds, tol=w.tol, out=out_b, **kw_b)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, out=out_b, fan_rays=BREAST_FAN, **kw_b)
         b.record(stream)
         rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, out=g_b, **kw_b)
         c.record(stream)
@@ -608,7 +615,7 @@ def main():
     def e2e_step():
         c_dev.copy_(c_host, non_blocking=True)
         tm_dev.copy_(tm_host, non_blocking=True)
-        r = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp32c", c=c_dev, ctx=ctx, out=out_e)
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp32c", c=c_dev, ctx=ctx, out=out_e, fan_rays=BREAST_FAN)
         rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=tm_dev, precision="fp32c", c=c_dev, ctx=ctx,
                           out=g_e)
         T_host.copy_(r["tof"], non_blocking=True)
@@ -630,7 +637,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "grid": f"{w.grid.nx}x{w.grid.ny}", "h_mm": w.grid.h, "ring": w.n_tx,
                    "ring_radius_mm": w.ring_radius, "pairs": n, "ds_mm": w.ds, "tol_mm": w.tol,
-                   "start": "straight-line launch angles (cold)", "step": "rt_link + rt_tof_adjoint (L2 misfit)",
+                   "start": f"cold: fan of {BREAST_FAN} rays per transducer", "fan_rays": BREAST_FAN,
+                   "step": "rt_link + rt_tof_adjoint (L2 misfit)",
                    "precision": "fp32c (FP32 march, compensated direction/sums, FP64 linking)",
                    "l2": "flushed between timed steps (256 MB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
