@@ -200,24 +200,40 @@ __device__ inline void fan_start(const Geom& G, LinkState& L, const double* __re
     const long long b_r = __double_as_longlong(L.psi_r);
     const long long b_lo = __double_as_longlong(L.psi_at_lo), b_hi = __double_as_longlong(psi_hi_end);
     const long long b_nan = 0x7ff0000000000000ll;
-    bool neg_prev = b_lo < b_r;
-    int jsel = K + 1;
-    double best_gap = CUDART_INF;
-    for (int j = 1; j <= K + 1; ++j) {
+    // entry j of the sequence (fan end, rays 0..K-1, fan end), j = 0..K+1
+    auto neg_at = [&](int j) {
         long long b;
-        if (j <= K) {
+        if (j == 0) {
+            b = b_lo;
+        } else if (j <= K) {
             const int k = j - 1;
             b = pb[k];
             if (b > b_nan) b = (k < K / 2) ? b_lo : b_hi;
         } else {
             b = b_hi;
         }
-        const bool neg = b < b_r;
-        if (neg != neg_prev) {
-            const double gap = fabs((j - 1.5) - u_s);
-            if (gap < best_gap) { best_gap = gap; jsel = j; }
+        return b < b_r;
+    };
+    // The interval (j-1, j) with a sign change whose gap |(j - 1.5) - u_s| is
+    // least, the smaller j on a tie: visited outward from u_s in the order of
+    // that gap, so the first change found is the one the full scan in index
+    // order selects (the sequence always changes sign somewhere, its two ends
+    // lie on either side of psi_r), usually a few rays from the start.
+    int jsel = K + 1;
+    {
+        int jl = (int)floor(u_s + 1.5);
+        jl = jl < 0 ? 0 : (jl > K + 1 ? K + 1 : jl);
+        int jr = jl + 1;
+        for (int it = 0; it < K + 2; ++it) {
+            const bool has_l = jl >= 1, has_r = jr <= K + 1;
+            if (!has_l && !has_r) break;
+            bool take_l;
+            if (has_l && has_r) take_l = fabs((jl - 1.5) - u_s) <= fabs((jr - 1.5) - u_s);
+            else take_l = has_l;
+            const int j = take_l ? jl : jr;
+            if (neg_at(j) != neg_at(j - 1)) { jsel = j; break; }
+            if (take_l) --jl; else ++jr;
         }
-        neg_prev = neg;
     }
     const double R = G.R;
     double t0, t1, p0, p1;
