@@ -677,7 +677,7 @@ def main():
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in ("rt_trace.cuh", "rt_ray.cu"):
+    for f in ("rt_trace.cuh", "rt_link.cuh", "rt_bspline.cuh", "rt_ray.cu"):
         h.update(open(os.path.join(ROOT, "paper_2511_18511_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
