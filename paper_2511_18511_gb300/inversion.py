@@ -124,3 +124,88 @@ def invert_tof(prob, t_meas: torch.Tensor, ds: float, n_lin: int = 3, n_inner: i
     misfit.append(0.5 * float(((r["tof"] - t_meas) ** 2).sum()))
     traces.append(float(r["iters"].float().mean()))
     return InversionResult(c, r["theta"].clone(), misfit, traces)
+
+
+# ---------------------------------------------------------------- ray-Born
+
+def cg_complex_data(apply: Callable[[torch.Tensor], torch.Tensor], adjoint: Callable[[torch.Tensor], torch.Tensor],
+                    b: torch.Tensor, x0: torch.Tensor, n_iter: int, rtol: float = 1e-8) -> torch.Tensor:
+    """min ||F x - b||^2 over real x for a real-to-complex linear F given by its
+    products (apply: x -> F x, adjoint: d -> Re(F^H d)): conjugate gradients on
+    the normal equations Re(F^H F) x = Re(F^H b) in the CGLS form, with the
+    data-space inner product Re <u, v> = Re sum conj(u) v. Stops early once the
+    normal-equation residual falls below rtol of its initial value."""
+    x = x0.clone()
+    r = b - apply(x)
+    s = adjoint(r)
+    p = s.clone()
+    gamma = float((s.double() ** 2).sum())
+    stop = gamma * rtol * rtol
+    for _ in range(n_iter):
+        if gamma <= stop or gamma == 0.0:
+            break
+        q = apply(p)
+        qq = float((q.abs().double() ** 2).sum())
+        if qq == 0.0:
+            break
+        alpha = gamma / qq
+        x += alpha * p
+        r -= alpha * q
+        s = adjoint(r)
+        gamma_new = float((s.double() ** 2).sum())
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+    return x
+
+
+@dataclasses.dataclass
+class BornInversionResult:
+    dc: torch.Tensor                # final sound-speed perturbation [ny, nx] (m/s)
+    misfit: list                    # 0.5 ||F_level dc - d_level||^2 before and after each level
+    update: list                    # ||dc_level - dc_previous|| / ||dc_level|| per level
+    levels_run: int
+
+
+def born_frequency_marching(maps, d_meas: torch.Tensor, f_mhz, levels, n_inner: int = 10,
+                            tol_update: float = 1e-3, gemm: str = "fp32",
+                            dc0: Optional[torch.Tensor] = None, ops=None) -> BornInversionResult:
+    """Ray-Born linearisations by frequency (arXiv:2511.18511 Sec. 3.1): the
+    levels (lists of indices into f_mhz, ordered from low to high frequency)
+    are solved in turn, each with the Hessian-based iterative solver (linear
+    conjugate gradients with n_inner inner iterations on its linear equation,
+    Sec. 3.1 item 1), warm-started from the previous level's estimate, until the
+    relative l2 norm of the update falls below tol_update.
+
+    The Green's functions are the given maps (one background medium); the
+    paper's per-level ray update, and its Hessian-free single step whose data-
+    and solution-space weights it does not specify, are not part of this loop.
+    d_meas: complex [n_freq, n_tx, n_tx] data at the frequencies f_mhz.
+    ops: optional (apply(f_list, dc), adjoint(f_list, d)) in place of the
+    library's rtborn_apply / rtborn_adjoint on the maps (the GPU operators)."""
+    if ops is None:
+        from . import rtborn_adjoint, rtborn_apply
+        ops = (lambda f, x: rtborn_apply(maps, f, x, gemm=gemm), lambda f, d: rtborn_adjoint(maps, f, d, gemm=gemm))
+        g = maps.grid
+        dc = torch.zeros((g.ny, g.nx), dtype=torch.float32, device=maps.T.device) if dc0 is None else dc0.clone()
+    else:
+        dc = dc0.clone()
+    misfit, update = [], []
+    run = 0
+    for lev in levels:
+        idx = list(lev)
+        f = [float(f_mhz[i]) for i in idx]
+        b = d_meas[idx].contiguous()
+        apply = lambda x, f=f: ops[0](f, x)
+        adjoint = lambda d, f=f: ops[1](f, d)
+        r0 = apply(dc) - b
+        misfit.append(0.5 * float((r0.abs().double() ** 2).sum()))
+        new = cg_complex_data(apply, adjoint, b, dc, n_inner)
+        r1 = apply(new) - b
+        misfit.append(0.5 * float((r1.abs().double() ** 2).sum()))
+        du = float((new - dc).double().norm() / max(float(new.double().norm()), 1e-300))
+        update.append(du)
+        dc = new
+        run += 1
+        if du < tol_update:
+            break
+    return BornInversionResult(dc, misfit, update, run)

@@ -62,3 +62,53 @@ def test_inversion_reduces_misfit_and_model_error(case, rt, solver):
     assert res.misfit[-1] <= 0.1 * res.misfit[0]
     assert all(b <= a * 1.05 for a, b in zip(res.misfit, res.misfit[1:]))
     assert e1 <= 0.8 * e0
+
+
+# ---------------------------------------------------------------- ray-Born frequency marching
+
+def test_born_marching_gpu_matches_oracle_loop(rt, orc):
+    """The marching loop over the GPU Born operators against the same loop over
+    the FP64 oracle operators, on the same (oracle) maps: every level lowers
+    its misfit by a large factor on both, and the estimates agree."""
+    from tests.test_inversion_cpu import _born_case, oracle_born_ops
+    from paper_2511_18511_gb300 import inversion as I
+    g, R, T, A, f, d, dc_true = _born_case(orc)
+    levels = [[0, 1], [2, 3], [4, 5]]
+    ref = I.born_frequency_marching(None, torch.as_tensor(d), f, levels, n_inner=15, tol_update=0.0,
+                                    dc0=torch.zeros(g.ny, g.nx, dtype=torch.float64),
+                                    ops=oracle_born_ops(orc, g, R, T, A))
+    maps = rt.BornMaps(g, R, torch.as_tensor(T, dtype=torch.float32, device="cuda"),
+                       torch.as_tensor(A, dtype=torch.float32, device="cuda"))
+    res = I.born_frequency_marching(maps, torch.as_tensor(d, dtype=torch.complex64, device="cuda"), f, levels,
+                                    n_inner=15, tol_update=0.0, gemm="fp32")
+    e_gpu = float(np.linalg.norm(res.dc.cpu().numpy() - dc_true) / np.linalg.norm(dc_true))
+    e_ref = float(np.linalg.norm(ref.dc.numpy() - dc_true) / np.linalg.norm(dc_true))
+    diff = float(np.linalg.norm(res.dc.cpu().numpy() - ref.dc.numpy()) / np.linalg.norm(ref.dc.numpy()))
+    print(f"Born marching: misfit GPU {['%.2e' % m for m in res.misfit]}, oracle {['%.2e' % m for m in ref.misfit]}; "
+          f"model error GPU {e_gpu:.3f} oracle {e_ref:.3f}; estimates differ by {diff:.2e}")
+    for k in range(3):
+        assert res.misfit[2 * k + 1] <= 0.05 * res.misfit[2 * k]
+    assert abs(e_gpu - e_ref) <= 0.02 and diff <= 0.05
+
+
+def test_born_marching_on_gpu_maps(rt):
+    """The loop at the scaled-down ray-Born size (128^2, 64-ring, 8 frequencies
+    in four levels) on GPU maps: consistent data of a smooth perturbation."""
+    from paper_2511_18511_gb300 import inversion as I
+    from paper_2511_18511_gb300 import phantoms as P
+    w = P.cfg_born_small()
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
+    maps = rt.rtborn_maps(prob, w.ds, w.fan_rays)
+    x, y = w.grid.node_xy()
+    dc_true = 8.0 * np.exp(-((x - 6.0) ** 2 + (y + 4.0) ** 2) / 18.0) - 5.0 * np.exp(-((x + 8.0) ** 2 + (y - 5.0) ** 2) / 8.0)
+    dc_true[x * x + y * y >= w.ring_radius ** 2] = 0.0
+    dct = torch.as_tensor(dc_true, dtype=torch.float32, device="cuda")
+    d = rt.rtborn_apply(maps, w.f_mhz, dct, gemm="fp32")
+    res = I.born_frequency_marching(maps, d, w.f_mhz, [[0, 1], [2, 3], [4, 5], [6, 7]], n_inner=10,
+                                    tol_update=0.0, gemm="fp32")
+    err = float((res.dc - dct).norm() / dct.norm())
+    print(f"Born marching 128^2/64-ring: misfit {['%.2e' % m for m in res.misfit]}, updates "
+          f"{['%.2e' % u for u in res.update]}, model error {err:.3f}")
+    for k in range(4):
+        assert res.misfit[2 * k + 1] <= 0.1 * res.misfit[2 * k]
+    assert err < 0.7

@@ -57,3 +57,60 @@ def test_sart_fixed_point_is_weighted_least_squares():
     w = 1.0 / np.sqrt(np.asarray(A.sum(axis=1)).ravel())
     xw = np.linalg.lstsq(A.toarray() * w[:, None], b.numpy() * w, rcond=None)[0]
     assert np.linalg.norm(x - xw) <= 1e-8 * np.linalg.norm(xw)
+
+
+# ---------------------------------------------------------------- ray-Born
+
+def test_complex_data_cg_reaches_least_squares():
+    """min ||F x - b||^2 over real x, F complex: the CG iterate equals the
+    solution of Re(F^H F) x = Re(F^H b) from numpy."""
+    rng = np.random.default_rng(5)
+    F = rng.normal(size=(120, 40)) + 1j * rng.normal(size=(120, 40))
+    b = rng.normal(size=120) + 1j * rng.normal(size=120)
+    Ft = torch.as_tensor(F)
+    apply = lambda x: Ft @ x.to(torch.complex128)
+    adjoint = lambda d: (Ft.conj().T @ d).real
+    x = I.cg_complex_data(apply, adjoint, torch.as_tensor(b), torch.zeros(40, dtype=torch.float64), 200, rtol=1e-14)
+    H = (F.conj().T @ F).real
+    xl = np.linalg.solve(H, (F.conj().T @ b).real)
+    assert np.linalg.norm(x.numpy() - xl) <= 1e-9 * np.linalg.norm(xl)
+
+
+def _born_case(orc):
+    from paper_2511_18511_gb300 import phantoms as P
+    g = P.Grid(32, 32, 0.5)
+    R = 7.0
+    tx = P.ring(8, R)
+    c = P.homogeneous(g, 1500.0)
+    K = P.born_fan_rays(R, g.h)
+    T, A = orc.fan_maps(g, c, tx, R, 0.05, K)
+    x, y = g.node_xy()
+    dc_true = 6.0 * np.exp(-((x - 1.5) ** 2 + (y + 1.0) ** 2) / 4.0) - 4.0 * np.exp(-((x + 2.0) ** 2 + y ** 2) / 2.0)
+    dc_true[x * x + y * y >= R * R] = 0.0
+    f = np.array([0.3, 0.45, 0.6, 0.75, 0.9, 1.05])
+    d = orc.born_apply(g, R, T, A, f, dc_true)
+    return g, R, T, A, f, d, dc_true
+
+
+def oracle_born_ops(orc, g, R, T, A):
+    apply = lambda f, x: torch.as_tensor(orc.born_apply(g, R, T, A, np.array(f), x.numpy()))
+    adjoint = lambda f, d: torch.as_tensor(orc.born_adjoint(g, R, T, A, np.array(f), d.numpy()))
+    return apply, adjoint
+
+
+def test_born_frequency_marching_on_oracle_operators(orc):
+    """Frequency marching (three levels of two frequencies, low to high) on
+    consistent Born data of a smooth two-blob perturbation: each level lowers
+    its own misfit by a large factor, the estimate approaches the truth, and
+    the updates shrink from level to level."""
+    g, R, T, A, f, d, dc_true = _born_case(orc)
+    ops = oracle_born_ops(orc, g, R, T, A)
+    res = I.born_frequency_marching(None, torch.as_tensor(d), f, [[0, 1], [2, 3], [4, 5]], n_inner=15,
+                                    tol_update=0.0, dc0=torch.zeros(g.ny, g.nx, dtype=torch.float64), ops=ops)
+    m = res.misfit
+    assert res.levels_run == 3
+    for k in range(3):
+        assert m[2 * k + 1] <= 0.05 * m[2 * k], m
+    err = np.linalg.norm(res.dc.numpy() - dc_true) / np.linalg.norm(dc_true)
+    assert err < 0.6, err
+    assert res.update[2] < res.update[0], res.update
