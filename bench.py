@@ -245,6 +245,39 @@ def run_born(args):
     _, counts = rt.rt_status_counts()
     steps_per_call = counts[7]
     part32, _ = timed("fp32", 1, 1)
+
+    # the same step with absorption (alpha0 following the medium, y = 1.3) and,
+    # separately, with the cubic B-spline sampler in the fans
+    alpha0 = torch.as_tensor(P.absorption_map(w.c), device=dev)
+
+    def variant(steps, **kw):
+        m = rt.rtborn_maps(prob, w.ds, w.fan_rays, **kw)
+        dd = rt.rtborn_apply(m, w.f_mhz, dc)
+        gg = rt.rtborn_adjoint(m, w.f_mhz, dd)
+        torch.cuda.synchronize()
+        parts = []
+        for _ in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(s)
+            rt.rtborn_maps(prob, w.ds, w.fan_rays, out=m, **kw)
+            ev[1].record(s)
+            rt.rtborn_apply(m, w.f_mhz, dc, out=dd)
+            ev[2].record(s)
+            rt.rtborn_adjoint(m, w.f_mhz, dd, out=gg)
+            ev[3].record(s)
+            torch.cuda.synchronize()
+            parts.append([ev[k].elapsed_time(ev[k + 1]) for k in range(3)])
+        del m, dd, gg
+        p_ = np.array(parts).mean(0)
+        return {"value": nf * w.n_tx * (w.n_tx - 1) / (p_.sum() / 1e3), "unit": "Born data/s",
+                "ms_per_step": float(p_.sum()),
+                "parts_ms": {"maps": float(p_[0]), "apply": float(p_[1]), "adjoint": float(p_[2])}}
+
+    leg_abs = variant(2, alpha0=alpha0, y=1.3)
+    leg_abs["absorption"] = "alpha0 = 2e-8 (1 + 20 |c/1500 - 1|) Np (rad/s)^-y m^-1, y = 1.3"
+    leg_bs = variant(2, interpolator="bspline")
+    leg_bs["sampler"] = "interpolating cubic B-spline (c, gradient, Hessian, s)"
     ms = float(part.sum())
     data = nf * w.n_tx * (w.n_tx - 1)
     n_in = int(np.sum(np.hypot(*w.grid.node_xy()) < w.ring_radius))
@@ -259,7 +292,7 @@ def run_born(args):
     if dominant == 0:
         roof = {"bound": "alu", "achieved": maps_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": maps_tflops / FP32_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_born_fan (two passes) + pack + unpack",
+                "kernel": "k_born_fan + pack + unpack",
                 "flop_per_rk4_step": FLOP_PER_BORN_STEP, "rk4_steps_per_launch": steps_per_call,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"}
     else:
@@ -308,6 +341,8 @@ def run_born(args):
             "maps": {"rays": w.n_tx * w.fan_rays, "rk4_steps_both_passes": steps_per_call,
                      "tflops": maps_tflops, "rays_per_s": w.n_tx * w.fan_rays / (part[0] / 1e3)},
             "roofline": roof,
+            "absorption": leg_abs,
+            "bspline": leg_bs,
             "e2e": {"value": data / e2e_s, "unit": "Born data/s",
                     "h2d_bytes_per_step": c_host.numel() * 8 + dc_host.numel() * 4,
                     "d2h_bytes_per_step": d_host.numel() * 8 + g_host.numel() * 4},
