@@ -19,7 +19,8 @@
  *   B2 fan: per transducer, K rays at evenly spaced angles over the inward
  *      half-plane, the two tangent directions excluded by a margin ds/R (the
  *      same fan as the linking's cold start);
- *   B3 march: classic RK4 at fixed ds on (x, d, Q, P) together, with
+ *   B3 march: classic RK4 (or, with orc_set_integrator(1), Heun's RK2, the
+ *      paper's default) at fixed ds on (x, d, Q, P) together, with
  *      dx/ds = d, dd/ds = -(grad c - (grad c . d) d)/c and the paraxial pair
  *      dQ/ds = c P, dP/ds = -(c_nn / c^2) Q, c_nn = n^T H n for the unit normal
  *      n of d (Sec. 3.5, paraxial ray, default); Q(0) = 0, P(0) = 1/c_t with c_t
@@ -231,7 +232,24 @@ static void brhs(const BField* F, const double st[6], double k[6]) {
     k[5] = -cnn / (f[F_C] * f[F_C]) * st[4];
 }
 
+/* B3 with orc_set_integrator(1): Heun's second-order Runge-Kutta on the same
+ * state (x, d, Q, P), the slopes at the start and at the Euler end averaged. */
+static void bheun(const BField* F, const double st[6], double hs, double out[6]) {
+    double k1[6], k2[6], t[6];
+    brhs(F, st, k1);
+    for (int q = 0; q < 6; ++q) t[q] = st[q] + hs * k1[q];
+    brhs(F, t, k2);
+    for (int q = 0; q < 6; ++q) out[q] = st[q] + 0.5 * hs * (k1[q] + k2[q]);
+    const double n = sqrt(out[2] * out[2] + out[3] * out[3]);
+    out[2] /= n;
+    out[3] /= n;
+}
+
 static void brk4(const BField* F, const double st[6], double hs, double out[6]) {
+    if (orc_get_integrator() == 1) {
+        bheun(F, st, hs, out);
+        return;
+    }
     double k1[6], k2[6], k3[6], k4[6], t[6];
     brhs(F, st, k1);
     for (int q = 0; q < 6; ++q) t[q] = st[q] + 0.5 * hs * k1[q];

@@ -311,6 +311,8 @@ int orc_set_integrator(int32_t k) {
     return ORC_OK;
 }
 
+int orc_get_integrator(void) { return g_integrator; }
+
 static void rk4(const Field* F, const double st[4], double hs, double out[4]) {
     if (g_integrator == 1) step_heun(F, st, hs, out);
     else step_rk4(F, st, hs, out);

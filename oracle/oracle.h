@@ -106,6 +106,7 @@ int orc_set_integrator(int32_t k);
  * analytic gradient (Sec. 3.3.1). Returns ORC_EINVAL for other values. */
 int orc_set_interpolator(int32_t k);
 int orc_get_interpolator(void);
+int orc_get_integrator(void);
 
 /* Control coefficients a = P^-1 f of the interpolating cubic B-spline of the
  * nodal field f[ny*nx] (mirror boundary; P is the spline's value at the nodes,

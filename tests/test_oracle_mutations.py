@@ -216,6 +216,8 @@ BORN_BSPLINE_MUTANTS = {
     "born_bs_cross_term": ("cxy += dx1[a] * dy1[b] * ak;", "cxy += dx2[a] * by[b] * ak;"),
     "born_bs_gradient_axis": ("cy += bx[a] * dy1[b] * ak;", "cy += dx1[a] * by[b] * ak;"),
     "born_bs_no_prefilter": ("orc_bspline_coef(g, c, F->ac, 0)", "!memcpy(F->ac, c, n * sizeof(double))"),
+    "born_heun_end_slope_only": ("for (int q = 0; q < 6; ++q) out[q] = st[q] + 0.5 * hs * (k1[q] + k2[q]);",
+                                 "for (int q = 0; q < 6; ++q) out[q] = st[q] + hs * k2[q];"),
 }
 
 
@@ -233,6 +235,8 @@ BORN_BSPLINE_PINS = [
     lambda orc: bbpins.test_bspline_paraxial_Q_matches_auxiliary_rays(orc, 40, -0.25),
     bbpins.test_bspline_maps_brute_force,
     bbpins.test_bspline_maps_homogeneous_and_fermat,
+    bbpins.test_heun_fan_ray_second_order_Q,
+    lambda orc: bbpins.test_heun_paraxial_Q_matches_auxiliary_rays(orc, 0, 0.1),
 ]
 BORN_BSPLINE_PINS = [_born_in_bspline(p) for p in BORN_BSPLINE_PINS]
 
