@@ -110,7 +110,7 @@ typedef struct {
                             blocks): (64,1,8) (64,1,12) (128,1,4) (128,1,5) (128,1,6)
                             (128,2,4) (256,1,2) (256,1,3); FP64: (128,1,1) */
     int32_t integrator;    /* enum rt_integrator: the ray stepper of every trace of
-                            the ToF calls (rtborn_maps requires RT_RK4) */
+                            the ToF calls and of the rtborn_maps fans */
     int32_t interpolator;  /* enum rt_interpolator: the field sampler of rt_link,
                             rt_tof_forward, rt_tof_adjoint, rt_path_matrix and
                             rtborn_maps (rt_batch_run and rt_tof_forward_noalloc
@@ -335,7 +335,8 @@ enum rtborn_gemm {
  * rtborn_maps — first-arrival travel-time and amplitude maps of every
  * transducer, from a fan of fan_rays rays per transducer at evenly spaced
  * angles over the inward half-plane (tangents excluded by a margin ds/R).
- * Each ray is marched with RK4 at the fixed step opt->ds_mm (<= h) together
+ * Each ray is marched with RK4 (or Heun's RK2, opt->integrator) at the fixed
+ * step opt->ds_mm (<= h) together
  * with its paraxial ray (Q, P): dQ/ds = c P, dP/ds = -(c_nn/c^2) Q, Q(0) = 0,
  * P(0) = 1/c_t, c_nn the second derivative of c across the ray (central
  * second differences interpolated bilinearly); the travel time by the

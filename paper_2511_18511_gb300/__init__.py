@@ -362,7 +362,7 @@ class BornMaps:
 def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tensor] = None,
                 ctx: Optional[Context] = None, stream=None, out: Optional[BornMaps] = None,
                 blocks_per_sm: int = 0, alpha0: Optional[torch.Tensor] = None, y: float = 1.0,
-                interpolator: str = "bilinear") -> BornMaps:
+                interpolator: str = "bilinear", integrator: str = "rk4") -> BornMaps:
     """Travel-time and amplitude maps of every transducer from fans of
     fan_rays rays traced with their paraxial rays (paper Sec. 3.5).
     blocks_per_sm selects the fan kernel variant (0 = default). With alpha0
@@ -386,7 +386,7 @@ def rtborn_maps(prob: Problem, ds: float, fan_rays: int, c: Optional[torch.Tenso
         out.y = float(y)
     else:
         out.L = None
-    o = _opts(ds, precision="fp32c", blocks_per_sm=blocks_per_sm, interpolator=interpolator)
+    o = _opts(ds, precision="fp32c", blocks_per_sm=blocks_per_sm, interpolator=interpolator, integrator=integrator)
     ps = prob.struct(c)
     _L.check(ctx.h, ctx.lib.rtborn_maps_abs(ctx.h, C.byref(ps), C.byref(o), int(fan_rays), _ptr(alpha0),
                                             _ptr(out.T), _ptr(out.A), _ptr(out.L), _stream(stream)))

@@ -8,8 +8,8 @@
 // Fan maps (rtborn_maps). One thread per fan ray, K rays per transducer at
 // evenly spaced angles over the inward half-plane (the two tangents excluded
 // by a margin ds/R). The march is the FP32-compensated one of the ToF path
-// (cell-local position with a two-sum residual, double-float direction, RK4 in
-// cell units) extended by the paraxial pair in cell units Q~ = Q/h:
+// (cell-local position with a two-sum residual, double-float direction, RK4 or
+// Heun's RK2 in cell units) extended by the paraxial pair in cell units Q~ = Q/h:
 //     dQ~/ds~ = c P,   dP/ds~ = -(h^2 c_nn / c^2) Q~,   Q~(0) = 0, P(0) = 1/c_t,
 // with c_nn = n^T H n, H the Hessian of c from central second differences
 // interpolated bilinearly. The travel time is the trapezoid rule over the
@@ -301,6 +301,36 @@ __device__ __forceinline__ void born_rk4(CellB& C, const BornRay& B, float H, fl
     N.S.fy = nfy;
 }
 
+// One step of Heun's second-order Runge-Kutta method on (x, d, Q, P) (the
+// slopes at the start, given as stage 1, and at the Euler end point, averaged),
+// in the same cell-unit, compensated form as born_rk4.
+template <typename CellB>
+__device__ __forceinline__ void born_heun(CellB& C, const BornRay& B, float H, float c, float gx, float gy,
+                                          float hxx, float hxy, float hyy, BornRay& N) {
+    const float Hh = 0.5f * H;
+    const float dx = B.S.d.hx(), dy = B.S.d.hy();
+    float tx, ty, k1x, k1y, k1Q, k1P, k2x, k2y, k2Q, k2P;
+    born_rhs(c, gx, gy, hxx, hxy, hyy, dx, dy, B.Q, B.P, k1x, k1y, k1Q, k1P);
+    const float e2x = dx + H * k1x, e2y = dy + H * k1y, Q2 = B.Q + H * k1Q, P2 = B.P + H * k1P;
+    C.at(B.S.ci, B.S.cj, B.S.fx + H * dx, B.S.fy + H * dy, c, gx, gy, hxx, hxy, hyy, tx, ty);
+    born_rhs(c, gx, gy, hxx, hxy, hyy, e2x, e2y, Q2, P2, k2x, k2y, k2Q, k2P);
+    N.Q = B.Q + Hh * (k1Q + k2Q);
+    N.P = B.P + Hh * (k1P + k2P);
+    float nfx = B.S.fx, nfy = B.S.fy;
+    N.S.lx = B.S.lx;
+    N.S.ly = B.S.ly;
+    add_frac(nfx, N.S.lx, Hh * (dx + e2x) + H * B.S.d.lx());
+    add_frac(nfy, N.S.ly, Hh * (dy + e2y) + H * B.S.d.ly());
+    N.S.d = B.S.d;
+    N.S.d.add_normalize(Hh * (k1x + k2x), Hh * (k1y + k2y));
+    N.S.ci = B.S.ci;
+    N.S.cj = B.S.cj;
+    if (nfx >= 1.f) { N.S.ci += 1; nfx -= 1.f; } else if (nfx < 0.f) { N.S.ci -= 1; add_frac(nfx, N.S.lx, 1.f); }
+    if (nfy >= 1.f) { N.S.cj += 1; nfy -= 1.f; } else if (nfy < 0.f) { N.S.cj -= 1; add_frac(nfy, N.S.ly, 1.f); }
+    N.S.fx = nfx;
+    N.S.fy = nfy;
+}
+
 // order-preserving map of float bits to unsigned (negative values included)
 __device__ __forceinline__ unsigned f2ord(float f) {
     const unsigned u = __float_as_uint(f);
@@ -432,7 +462,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_born_fan(const Geom G, const Fa
     int safe = 0, nsteps = 0;
     for (int m = 1; m <= G.max_steps_i; ++m) {
         BornRay N;
-        born_rk4(C, B, H, c, gx, gy, hxx, hxy, hyy, N);
+        if (G.heun) born_heun(C, B, H, c, gx, gy, hxx, hxy, hyy, N);
+        else born_rk4(C, B, H, c, gx, gy, hxx, hxy, hyy, N);
         ++nsteps;
         if (--safe < 0) {
             const float ex = ring_excess(G, N.S);
@@ -715,7 +746,7 @@ int rtborn_maps_abs(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, 
     if (opt->precision != RT_FP32_COMP) return bfail(ctx, RT_EINVAL, "fan maps are computed in RT_FP32_COMP only");
     if (!(opt->ds_mm > 0) || !std::isfinite(opt->ds_mm)) return bfail(ctx, RT_EINVAL, "ds_mm must be > 0");
     if (fan_rays < 2 || fan_rays > (1 << 20)) return bfail(ctx, RT_EINVAL, "fan_rays must be in [2, 2^20]");
-    if (opt->integrator != RT_RK4) return bfail(ctx, RT_EINVAL, "fan maps are traced with RK4 (integrator RT_RK4)");
+    if (opt->integrator != RT_RK4 && opt->integrator != RT_HEUN) return bfail(ctx, RT_EINVAL, "unknown integrator");
     if (opt->interpolator != RT_BILINEAR && opt->interpolator != RT_BSPLINE)
         return bfail(ctx, RT_EINVAL, "unknown interpolator");
     const bool spline = opt->interpolator == RT_BSPLINE;
