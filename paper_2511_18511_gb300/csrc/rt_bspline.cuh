@@ -128,37 +128,103 @@ struct CellAccBS {
     }
 };
 
-// Adjoint scatter onto the slowness coefficients: w * alpha_m * B_pq(x_m), one
-// flush of 16 FP64 atomics per run of points in one cell. The coefficient-space
-// result is mapped back to nodes by the transposed prefilter afterwards.
+// Adjoint scatter onto the slowness coefficients: w * alpha_m * B_pq(x_m). The
+// weights of the 4 x 4 coefficients around the current cell accumulate in a
+// window that slides with the ray: when the ray steps into a neighbouring cell
+// only the column (or row) of coefficients that leaves the window is flushed
+// (4 FP64 atomics instead of 16 per cell crossing), the rest shifts along;
+// the whole window is flushed at the end of the trace (or on a jump of more
+// than one cell). The coefficient-space result is mapped back to nodes by the
+// transposed prefilter afterwards.
 template <typename T>
 struct AdjSinkBSp {
     double* g;
     T w;
     int nx, ny;
-    CellAccBS<T> acc;
-    __device__ __forceinline__ void flush() {
-        if (acc.ai == INT_MIN) return;
-        const int i = min(max(acc.ai, 0), nx - 2), j = min(max(acc.aj, 0), ny - 2);
+    int ai, aj;        // cell the window is centred on (INT_MIN: empty)
+    T W[16];           // W[4 b + a]: coefficient (ai - 1 + a, aj - 1 + b)
+
+    __device__ __forceinline__ void init() {
+        ai = INT_MIN;
+        aj = INT_MIN;
+        clear();
+    }
+
+    __device__ __forceinline__ void put(int a, int b) {
+        const int i = min(max(ai, 0), nx - 2), j = min(max(aj, 0), ny - 2);
+        atomicAdd(g + (size_t)mirror_index(j - 1 + b, ny) * nx + mirror_index(i - 1 + a, nx), to_double(w * W[4 * b + a]));
+    }
+    __device__ __forceinline__ void flush_all() {
+        if (ai == INT_MIN) return;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double* row = g + (size_t)mirror_index(j - 1 + q, ny) * nx;
+        for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int p = 0; p < 4; ++p) atomicAdd(row + mirror_index(i - 1 + p, nx), to_double(w * acc.W[4 * q + p]));
-        }
+            for (int a = 0; a < 4; ++a) put(a, b);
+    }
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) W[k] = (T)0;
     }
     __device__ __forceinline__ void add(int ci, int cj, T tx, T ty, T a) {
-        if (ci != acc.ai || cj != acc.aj) {
-            flush();
-            acc.reset();
-            acc.ai = ci;
-            acc.aj = cj;
+        if (ci != ai || cj != aj) {
+            const int di = ci - ai, dj = cj - aj;
+            if (ai == INT_MIN || di < -1 || di > 1 || dj < -1 || dj > 1) {
+                flush_all();
+                clear();
+                ai = ci;
+                aj = cj;
+            } else {
+                if (di == 1) {            // column a = 0 leaves, the others move left
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) put(0, b);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        W[4 * b] = W[4 * b + 1]; W[4 * b + 1] = W[4 * b + 2]; W[4 * b + 2] = W[4 * b + 3]; W[4 * b + 3] = (T)0;
+                    }
+                    ai += 1;
+                } else if (di == -1) {    // column a = 3 leaves, the others move right
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) put(3, b);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        W[4 * b + 3] = W[4 * b + 2]; W[4 * b + 2] = W[4 * b + 1]; W[4 * b + 1] = W[4 * b]; W[4 * b] = (T)0;
+                    }
+                    ai -= 1;
+                }
+                if (dj == 1) {            // row b = 0 leaves, the others move down
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) put(q, 0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        W[q] = W[4 + q]; W[4 + q] = W[8 + q]; W[8 + q] = W[12 + q]; W[12 + q] = (T)0;
+                    }
+                    aj += 1;
+                } else if (dj == -1) {    // row b = 3 leaves, the others move up
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) put(q, 3);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        W[12 + q] = W[8 + q]; W[8 + q] = W[4 + q]; W[4 + q] = W[q]; W[q] = (T)0;
+                    }
+                    aj -= 1;
+                }
+            }
         }
-        acc.add(tx, ty, a);
+        T bx[4], by[4];
+        bspline_weights(tx, bx);
+        bspline_weights(ty, by);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) bx[p] *= a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) W[4 * q + p] += bx[p] * by[q];
     }
     __device__ __forceinline__ void finish() {
-        flush();
-        acc.reset();
+        flush_all();
+        clear();
+        ai = INT_MIN;
+        aj = INT_MIN;
     }
 };
 

@@ -350,6 +350,7 @@ struct AdjSink {
         flush();
         acc.reset();
     }
+    __device__ __forceinline__ void init() { acc.reset(); }
 };
 
 struct PairEnds {

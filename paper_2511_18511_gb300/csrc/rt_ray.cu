@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks)
     TraceState<T> ts;
     typename AdjOf<T, I>::type sink;
     sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
-    sink.acc.reset();
+    sink.init();
     bool active = false;
     for (;;) {
         if (!active) {
