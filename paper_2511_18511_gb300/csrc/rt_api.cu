@@ -290,7 +290,7 @@ int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, c
     int rc = prepare(ctx, prob, opt, false, s, &G);
     if (rc) return rc;
     cudaError_t e =
-        rt::launch_adjoint(G, ctx->field, opt->precision, theta, g_tof, tof_ref, prob->c_mps, g_c, ctx->queue, s);
+        rt::launch_adjoint(G, ctx->field, opt->precision, theta, g_tof, tof_ref, prob->c_mps, g_c, s);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "adjoint kernel");
 }
 

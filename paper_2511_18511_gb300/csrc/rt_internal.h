@@ -80,7 +80,7 @@ cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double*
                        double* hit, cudaStream_t s);
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,
                            const double* g_tof, const double* tof_ref, const double* c_mps,
-                           double* g_c, int* queue, cudaStream_t s);
+                           double* g_c, cudaStream_t s);
 cudaError_t launch_rows(const Geom& G, const void* field, int prec, const double* theta,
                         int64_t* row_ptr, int32_t* col, double* val, bool fill, cudaStream_t s);
 cudaError_t launch_tx_phi(const Geom& G, double* phi, cudaStream_t s);

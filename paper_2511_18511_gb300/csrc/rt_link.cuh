@@ -353,9 +353,7 @@ struct AdjSink {
     __device__ __forceinline__ void init() { acc.reset(); }
 };
 
-struct PairEnds {
-    double xe, ye, xr, yr;
-};
+
 
 
 }  // namespace rt

@@ -369,42 +369,32 @@ cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double*
 
 // ---------------------------------------------------------------- A6: adjoint scatter
 
-// Persistent adjoint: each lane takes pairs from the queue (longest chords
-// first), retraces the ray at its angle and scatters its weights.
 template <typename T, int I> struct AdjOf { using type = AdjSink<T>; };
 template <typename T> struct AdjOf<T, RT_BSPLINE> { using type = AdjSinkBSp<T>; };
 
+// Adjoint scatter: one thread per pair retraces the ray at its angle and
+// scatters its weights, in the work-queue order (longest chords first,
+// consecutive emitters at one ring offset, so a warp's rays have equal chords
+// and run through nearby cells). A plain launch whose blocks retire as they
+// finish measured faster than a persistent one with a work queue (26.1 vs
+// 27.9 ms on the breast workload; 52.6 vs 61.0 ms with the B-spline).
 template <typename T, int I>
-__global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks)
+__global__ void __launch_bounds__(kBlock, Occ<T, I>::blocks)
     k_adjoint(Geom G, const typename Samp<T, I>::Field* __restrict__ F, const double* theta, const double* g_tof,
-              const double* tof_ref, double* g, int* queue) {
-    __shared__ PairEnds sh[kLinkBlock];
-    PairEnds& E = sh[threadIdx.x];
+                 const double* tof_ref, double* g) {
+    const int slot = blockIdx.x * kBlock + threadIdx.x;
+    if (slot >= G.n_pairs) return;
+    const int k = queue_pair(G, slot);
+    const double w = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
+    if (w == 0.0 || !isfinite(w)) return;
+    LinkCtx X;
+    if (!setup_pair(G, k, X)) return;
     auto C = make_cell<T, I>(G, F);
-    TraceState<T> ts;
     typename AdjOf<T, I>::type sink;
     sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
     sink.init();
-    bool active = false;
-    for (;;) {
-        if (!active) {
-            const int qslot = fetch_pair(queue);
-            if (qslot >= G.n_pairs) break;
-            const int k = queue_pair(G, qslot);
-            const double w = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
-            if (w == 0.0 || !isfinite(w)) continue;
-            LinkCtx X;
-            if (!setup_pair(G, k, X)) continue;
-            E.xe = X.xe; E.ye = X.ye; E.xr = X.xr; E.yr = X.yr;
-            sink.w = (T)w;
-            trace_begin(ts, G, X.xe, X.ye, theta[k]);
-            active = true;
-        }
-        if (trace_step(C, G, ts, sink)) {
-            trace_end(C, G, ts, E.xe, E.ye, E.xr, E.yr, sink);
-            active = false;
-        }
-    }
+    sink.w = (T)w;
+    trace_ray<T>(C, G, X.xe, X.ye, theta[k], X.xr, X.yr, sink);
 }
 
 // g_c = -1000 * (L^T w) / c_mps^2 : s = 1000/c_mps (us/mm)
@@ -417,28 +407,25 @@ __global__ void k_adjoint_finish(double* g, const double* __restrict__ c_mps, in
 
 template <typename T, int I>
 static void adjoint_impl(const Geom& G, const void* field, const double* theta, const double* g_tof,
-                         const double* tof_ref, double* g_c, int* queue, int slot, cudaStream_t s) {
-    const int nb = min(persistent_blocks(k_adjoint<T, I>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-    k_adjoint<T, I><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, theta, g_tof, tof_ref,
-                                              g_c, queue);
+                         const double* tof_ref, double* g_c, cudaStream_t s) {
+    k_adjoint<T, I><<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, theta,
+                                                             g_tof, tof_ref, g_c);
 }
 
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,
                            const double* g_tof, const double* tof_ref, const double* c_mps,
-                           double* g_c, int* queue, cudaStream_t s) {
+                           double* g_c, cudaStream_t s) {
     const int n = G.nx * G.ny;
     cudaError_t e = cudaMemsetAsync(g_c, 0, sizeof(double) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     if (G.n_pairs > 0) {
-        e = cudaMemsetAsync(queue, 0, sizeof(int), s);
-        if (e != cudaSuccess) return e;
         const bool bs = G.interp == RT_BSPLINE;
         if (prec == RT_FP64) {
-            if (bs) adjoint_impl<double, RT_BSPLINE>(G, field, theta, g_tof, tof_ref, g_c, queue, 11, s);
-            else adjoint_impl<double, RT_BILINEAR>(G, field, theta, g_tof, tof_ref, g_c, queue, 1, s);
+            if (bs) adjoint_impl<double, RT_BSPLINE>(G, field, theta, g_tof, tof_ref, g_c, s);
+            else adjoint_impl<double, RT_BILINEAR>(G, field, theta, g_tof, tof_ref, g_c, s);
         } else {
-            if (bs) adjoint_impl<float, RT_BSPLINE>(G, field, theta, g_tof, tof_ref, g_c, queue, 12, s);
-            else adjoint_impl<float, RT_BILINEAR>(G, field, theta, g_tof, tof_ref, g_c, queue, 2, s);
+            if (bs) adjoint_impl<float, RT_BSPLINE>(G, field, theta, g_tof, tof_ref, g_c, s);
+            else adjoint_impl<float, RT_BILINEAR>(G, field, theta, g_tof, tof_ref, g_c, s);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
