@@ -379,7 +379,8 @@ def run_profile_case(args):
     w = workload(0)
     pairs = P.all_pairs(w.n_tx)
     pairs = pairs[pairs[:, 0] < args.profile]
-    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, pairs=pairs)
+    # all emitters: the implicit all-pairs list, served in the bench's queue order
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, pairs=None if args.profile >= w.n_tx else pairs)
     for _ in range(2):
         r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision, fan_rays=BREAST_FAN)
         rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=r["tof"] * 0.999, precision=args.precision)
