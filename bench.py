@@ -291,7 +291,8 @@ def run_born(args):
     dominant = int(np.argmax(part))
     if dominant == 0:
         roof = {"bound": "alu", "achieved": maps_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": maps_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": maps_tflops / FP32_PEAK_TFLOPS,
+                "traffic": _traffic(os.path.join(ROOT, "profiles", "born_traffic.json"), BORN_HASH_FILES),
                 "kernel": "k_born_fan + pack + unpack",
                 "flop_per_rk4_step": FLOP_PER_BORN_STEP, "rk4_steps_per_launch": steps_per_call,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"}
@@ -629,14 +630,7 @@ def main():
     steps_per_launch = res["counts"][7]
     link_ms = float(np.mean(res["link_ms"]))
     achieved = steps_per_launch * FLOP_PER_STEP / (link_ms / 1e3) / 1e12
-    traffic = None
-    if os.path.exists(args.traffic_json):
-        try:
-            tj = json.load(open(args.traffic_json))
-            if tj.get("kernel_source_hash") == _kernel_hash():
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = _traffic(args.traffic_json, ("rt_trace.cuh", "rt_link.cuh", "rt_bspline.cuh", "rt_ray.cu"))
 
     # e2e through the public API with host buffers (pinned), copies timed
     c_host = torch.as_tensor(w.c).pin_memory()
@@ -679,7 +673,7 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "k_link<float> (+ its field pack)",
+                     "kernel": "rt_link call: k_fan<float> + k_link<float> (+ field pack)",
                      "flop_per_rk4_step": FLOP_PER_STEP, "rk4_steps_per_launch": steps_per_launch,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"},
         "warm_start": {"value": n / (warm / 1e3), "unit": UNIT, "ms_per_step": warm,
@@ -710,12 +704,25 @@ def main():
         dist.destroy_process_group()
 
 
-def _kernel_hash() -> str:
+def _kernel_hash(files=("rt_trace.cuh", "rt_link.cuh", "rt_bspline.cuh", "rt_ray.cu")) -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in ("rt_trace.cuh", "rt_link.cuh", "rt_bspline.cuh", "rt_ray.cu"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2511_18511_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
+
+
+BORN_HASH_FILES = ("rt_trace.cuh", "rt_bspline.cuh", "rt_born.cu")
+
+
+def _traffic(path: str, files) -> "int | None":
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel sources changed since it was captured."""
+    try:
+        tj = json.load(open(path))
+        return tj.get("bytes_per_launch") if tj.get("kernel_source_hash") == _kernel_hash(files) else None
+    except Exception:
+        return None
 
 
 if __name__ == "__main__":
