@@ -139,12 +139,20 @@ __global__ void k_fan_mark(Geom G, const double* __restrict__ theta, int* need) 
     if (e >= 0 && e < G.n_tx && isnan(theta[k])) need[e] = 1;
 }
 
+// Thread order: the ray of fan index k of emitter e runs on thread
+// e + n_tx * rank(k), where rank orders the fan indices from the middle of the
+// fan (toward the centre, the longest rays) outward. A warp then marches the
+// same relative angle from consecutive emitters: nearly parallel rays of nearly
+// equal length through nearby cells, and the launch ends with the short rays
+// near the tangents.
 template <typename T, int I>
 __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I>::Field* __restrict__ F, int K,
                                                 const int* __restrict__ need, double* fan,
                                                 unsigned long long* counters) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    const int e = id / K, k = id - e * K;
+    const int rank = id / G.n_tx, e = id - rank * G.n_tx;
+    const int half = K / 2;
+    const int k = (rank & 1) ? half - (rank + 1) / 2 : half + rank / 2;
     long long steps = 0;
     if (id < G.n_tx * K && need[e] && !*G.bad_field) {
         const double xe = G.tx[2 * e], ye = G.tx[2 * e + 1];
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I
         auto C = make_cell<T, I>(G, F);
         NoSink ns;
         const TraceOut o = trace_ray<T>(C, G, xe, ye, fan_theta(a_min, step, k), xe, ye, ns);
-        fan[id] = (o.flags & 3) ? nan("") : mod_2pi(atan2(o.hy, o.hx) - phi_e);
+        fan[(size_t)e * K + k] = (o.flags & 3) ? nan("") : mod_2pi(atan2(o.hy, o.hx) - phi_e);
         steps = o.steps;
     }
     // every thread of the block reaches this point
