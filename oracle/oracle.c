@@ -569,12 +569,49 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
  * the sweep orientation exactly as the probe does. For a pair, the sequence of
  * misfits (fan end, rays 0..K-1, fan end) is scanned for sign changes; the one
  * whose middle lies closest to the straight-line angle, both counted in fan-ray
- * index units, is taken and its ends form the bracket. The first angle is the root of the inverse cubic
- * through the four fan rays around the interval when they exist and their
- * misfits are strictly monotone and the root falls inside the interval, else
- * the linear interpolation of the interval. The end with the smaller |misfit|
- * is the secant partner of the first trace. */
+ * index units, is taken and its ends form the bracket. The first angle is the
+ * root of the inverse interpolating polynomial (theta as a polynomial in the
+ * misfit, evaluated at misfit 0) through the eight fan rays around the
+ * interval, else through the four around it, each when those rays exist,
+ * their misfits are strictly monotone and the root falls inside the interval;
+ * else the linear interpolation of the interval. When the first trace misses
+ * the receiver, the second angle is the root of the inverse polynomial through
+ * that trace and the four fan rays (when those were usable and the trace
+ * reached the ring), else the secant of the first trace and the interval end
+ * with the smaller |misfit|; from there on the secant of the last two traces.
+ * Either candidate outside the bracket gives way to the Regula-Falsi point. */
 static double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
+
+/* Value at m = 0 of the polynomial theta(m) through the n points (m_q, t_q),
+ * Lagrange form. */
+static double inverse_poly_root(const double* t, const double* m, int n) {
+    double v = 0.0;
+    for (int a = 0; a < n; ++a) {
+        double l = 1.0;
+        for (int b = 0; b < n; ++b)
+            if (b != a) l *= (0.0 - m[b]) / (m[a] - m[b]);
+        v += l * t[a];
+    }
+    return v;
+}
+
+/* Fan rays k_first .. k_first + n - 1 as (theta, misfit) points; 1 when all of
+ * them exist and intercept the ring and their misfits change strictly
+ * monotonically, in the direction of the middle pair (n/2 - 1, n/2). */
+static int fan_points(const double* psi, int K, int k_first, int n, double a_min, double step, double R,
+                      double psi_r, double* t, double* m) {
+    if (k_first < 0 || k_first + n > K) return 0;
+    for (int q = 0; q < n; ++q) {
+        const int k = k_first + q;
+        if (isnan(psi[k])) return 0;
+        t[q] = fan_theta(a_min, step, k);
+        m[q] = R * (psi[k] - psi_r);
+    }
+    const double dir = m[n / 2] - m[n / 2 - 1];
+    for (int q = 0; q + 1 < n; ++q)
+        if (!((m[q + 1] - m[q]) * dir > 0)) return 0;
+    return 1;
+}
 
 static void fan_for_emitter(const Field* F, double R, const double* xe, double ds, int K, double* psi) {
     const double phi_e = atan2(xe[1], xe[0]);
@@ -646,27 +683,16 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
     double th0 = t0 - m0 * (t1 - t0) / (m1 - m0);
     /* rays around the interval (j-1, j): k0 = j-2 and k0+1 = j-1 */
     const int k0 = jsel - 2;
-    if (k0 >= 1 && k0 + 2 <= K - 1) {
-        double tt[4], mm[4];
-        int ok = 1;
-        for (int q = 0; q < 4; ++q) {
-            const int k = k0 - 1 + q;
-            if (isnan(psi[k])) ok = 0;
-            tt[q] = fan_theta(a_min, step, k);
-            mm[q] = R * (psi[k] - psi_r);
-        }
-        for (int q = 0; q < 3 && ok; ++q)
-            if (!((mm[q + 1] - mm[q]) * (mm[2] - mm[1]) > 0)) ok = 0;
-        if (ok) {
-            double v = 0.0;
-            for (int a = 0; a < 4; ++a) {
-                double l = 1.0;
-                for (int b = 0; b < 4; ++b)
-                    if (b != a) l *= (0.0 - mm[b]) / (mm[a] - mm[b]);
-                v += l * tt[a];
-            }
-            if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
-        }
+    double t8[8], m8[8], t4[4], m4[4];
+    int done = 0;
+    if (fan_points(psi, K, k0 - 3, 8, a_min, step, R, psi_r, t8, m8)) {
+        const double v = inverse_poly_root(t8, m8, 8);
+        if (v > fmin(t0, t1) && v < fmax(t0, t1)) { th0 = v; done = 1; }
+    }
+    const int ok4 = fan_points(psi, K, k0 - 1, 4, a_min, step, R, psi_r, t4, m4);
+    if (ok4 && !done) {
+        const double v = inverse_poly_root(t4, m4, 4);
+        if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
     }
     if (!(th0 > fmin(B.ta, B.tb) && th0 < fmax(B.ta, B.tb))) th0 = 0.5 * (B.ta + B.tb);
     Eval prev, cur;
@@ -677,8 +703,14 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
     double next = th0;
     while (n_eval < max_iter) {
         if (n_eval > 0) {
-            double den = cur.m - prev.m;
-            next = (den != 0.0) ? cur.theta - cur.m * (cur.theta - prev.theta) / den : NAN;
+            if (n_eval == 1 && ok4 && !(cur.tr.flags & 3)) {
+                const double t5[5] = {cur.theta, t4[0], t4[1], t4[2], t4[3]};
+                const double m5[5] = {cur.m, m4[0], m4[1], m4[2], m4[3]};
+                next = inverse_poly_root(t5, m5, 5);
+            } else {
+                double den = cur.m - prev.m;
+                next = (den != 0.0) ? cur.theta - cur.m * (cur.theta - prev.theta) / den : NAN;
+            }
             if (!(isfinite(next) && next > fmin(B.ta, B.tb) && next < fmax(B.ta, B.tb)))
                 next = (B.ta * B.fb - B.tb * B.fa) / (B.fb - B.fa);
         }

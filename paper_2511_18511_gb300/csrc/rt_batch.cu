@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             L.phase = 0;
             L.psi_at_lo = 0.0;
             L.best_d2 = CUDART_INF;
+            L.fan_k0 = -1;
             if (fan_rays >= 2 && d.fan && isnan(tin)) {
                 int e, r;
                 pair_of(G, k, e, r);
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
                 active = false;
                 break;
             }
-            if (link_update(G, L, o, tol, max_iter)) {
+            if (link_update(G, L, o, tol, max_iter, fan_rays >= 2 ? d.fan : nullptr, fan_rays)) {
                 const int k = L.k;
                 const int st = (L.best_d2 <= tol * tol) ? RT_RAY_OK
                                : (L.best_d2 == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);

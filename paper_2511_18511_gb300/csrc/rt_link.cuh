@@ -69,6 +69,8 @@ struct LinkState {
     double prev_th, prev_m, cur_th, cur_m;
     double psi_at_lo, next;
     int k, n_eval, phase, last, e0_flagged;
+    int fan_k0;                      // fan start: interval between rays fan_k0, fan_k0 + 1 whose
+                                     // four surrounding rays are usable for the second angle; else -1
     // adjoint retrace of the batched kernel (read on flushes only)
     double* adj_g;
     double adj_w;
@@ -127,9 +129,75 @@ __device__ __forceinline__ double next_angle(const LinkState& L, double cand) {
     return cand;
 }
 
+__device__ __forceinline__ double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
+
+// Misfit R (psi_k - psi_r) of fan ray k, read from memory at each use (the
+// row stays in L1/L2), so that the predictions keep no arrays in registers.
+__device__ __forceinline__ double fan_m(const double* psi, int k, double R, double psi_r) {
+    return R * (*(const volatile double*)(psi + k) - psi_r);
+}
+
+// Fan rays kf .. kf + N - 1: true when all of them exist and intercept the
+// ring and their misfits change strictly monotonically, in the direction of
+// the middle pair (N/2 - 1, N/2).
+template <int N>
+__device__ __forceinline__ bool fan_usable(const double* psi, int K, int kf, double R, double psi_r) {
+    if (kf < 0 || kf + N > K) return false;
+    const double dir = fan_m(psi, kf + N / 2, R, psi_r) - fan_m(psi, kf + N / 2 - 1, R, psi_r);
+    double prev = fan_m(psi, kf, R, psi_r);
+    if (isnan(prev)) return false;
+#pragma unroll 1
+    for (int q = 1; q < N; ++q) {
+        const double cur = fan_m(psi, kf + q, R, psi_r);
+        if (!((cur - prev) * dir > 0.0)) return false;
+        prev = cur;
+    }
+    return true;
+}
+
+// Position at m = 0 of the polynomial u(m) through the fan rays kf .. kf+N-1
+// (positions 0..N-1) and, with extra, the point (u0, m0) first: inverse
+// interpolation, Lagrange form with one division per node.
+template <int N>
+__device__ __forceinline__ double fan_root(const double* psi, int kf, double R, double psi_r, bool extra, double u0,
+                                           double m0) {
+    const int x = extra ? 1 : 0, n = N + x;
+    double v = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < n; ++a) {
+        const double ma = (a < x) ? m0 : fan_m(psi, kf + a - x, R, psi_r);
+        const double ua = (a < x) ? u0 : (double)(a - x);
+        double num = 1.0, den = 1.0;
+#pragma unroll 1
+        for (int b = 0; b < n; ++b) {
+            if (b == a) continue;
+            const double mb = (b < x) ? m0 : fan_m(psi, kf + b - x, R, psi_r);
+            num *= -mb;
+            den *= ma - mb;
+        }
+        v += ua * (num / den);
+    }
+    return v;
+}
+
+// Second angle of a fan-started pair whose first trace (theta, m) missed: the
+// inverse quartic through that trace and the four fan rays around the
+// interval, in fan-index units.
+__device__ __forceinline__ double fan_second_angle(const Geom& G, const LinkState& L, double theta, double m,
+                                                  const double* __restrict__ fan, int K) {
+    int e, r;
+    pair_of(G, L.k, e, r);
+    const double step = (L.a_max - L.a_min) / (K - 1);
+    const int kf = L.fan_k0 - 1;
+    const double base = fan_theta(L.a_min, step, kf);
+    return base + step * fan_root<4>(fan + (size_t)e * K, kf, G.R, L.psi_r, true, (theta - base) / step, m);
+}
+
 // Linking update after the trace of L.next ended (the same decisions as
-// link_pair). Returns true when the pair is finished.
-__device__ inline bool link_update(const Geom& G, LinkState& L, const TraceOut& o, double tol, int max_iter) {
+// link_pair). fan / K: the fan of the launch (null when it has none), for the
+// second angle of a fan-started pair. Returns true when the pair is finished.
+__device__ inline bool link_update(const Geom& G, LinkState& L, const TraceOut& o, double tol, int max_iter,
+                                   const double* __restrict__ fan, int K) {
     const double theta = L.next;
     double m, d2;
     misfit_of(G, L, o, theta, m, d2);
@@ -171,21 +239,26 @@ __device__ inline bool link_update(const Geom& G, LinkState& L, const TraceOut& 
     L.prev_th = L.cur_th; L.prev_m = L.cur_m;
     L.cur_th = theta; L.cur_m = m;
     if (L.n_eval >= max_iter) return true;
-    const double den = L.cur_m - L.prev_m;
-    const double cand = (den != 0.0) ? L.cur_th - L.cur_m * (L.cur_th - L.prev_th) / den : nan("");
+    double cand;
+    if (L.n_eval == 1 && L.fan_k0 >= 0 && fan && !(o.flags & 3)) {
+        cand = fan_second_angle(G, L, theta, m, fan, K);
+    } else {
+        const double den = L.cur_m - L.prev_m;
+        cand = (den != 0.0) ? L.cur_th - L.cur_m * (L.cur_th - L.prev_th) / den : nan("");
+    }
     L.next = next_angle(L, cand);
     return false;
 }
 
 // ---------------------------------------------------------------- fan start
 
-__device__ __forceinline__ double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
-
 // Fan start of a cold pair (the rule of the CPU reference, written so that the
 // per-ray scan issues no FP64 instruction): the interval of the sequence (fan
 // end, rays 0..K-1, fan end) where psi crosses psi_r whose middle lies closest
 // to the straight-line angle in fan-index units; first angle from the inverse
-// cubic of the four rays around it (when monotone and inside), else linear.
+// interpolating polynomial of the eight rays around it, else of the four (each
+// when those rays are monotone and the root falls inside), else linear. The
+// four rays also serve the second angle (link_update).
 // psi values are non-negative, so "psi < psi_r" is the signed compare of their
 // IEEE bit patterns; NaN (no interception) has the largest patterns.
 __device__ inline void fan_start(const Geom& G, LinkState& L, const double* __restrict__ psi, int K) {
@@ -249,28 +322,21 @@ __device__ inline void fan_start(const Geom& G, LinkState& L, const double* __re
     else { L.ta = t1; L.fa = m1; L.tb = t0; L.fb = m0; }
     L.last = 0;
     double th0 = t0 - m0 * (t1 - t0) / (m1 - m0);
+    // rays around the interval: k0 = jsel - 2 and k0 + 1
     const int k0 = jsel - 2;
-    if (k0 >= 1 && k0 + 2 <= K - 1) {
-        double tt[4], mm[4];
-        bool ok = true;
-        for (int q = 0; q < 4; ++q) {
-            const int k = k0 - 1 + q;
-            const double pk = psi[k];
-            if (isnan(pk)) ok = false;
-            tt[q] = fan_theta(L.a_min, step, k);
-            mm[q] = R * (pk - L.psi_r);
+    {
+        bool done = false;
+        if (fan_usable<8>(psi, K, k0 - 3, R, L.psi_r)) {
+            const double v = fan_theta(L.a_min, step, k0 - 3) + step * fan_root<8>(psi, k0 - 3, R, L.psi_r, false, 0.0, 0.0);
+            if (v > fmin(t0, t1) && v < fmax(t0, t1)) { th0 = v; done = true; }
         }
-        for (int q = 0; q < 3 && ok; ++q)
-            if (!((mm[q + 1] - mm[q]) * (mm[2] - mm[1]) > 0)) ok = false;
-        if (ok) {
-            double v = 0.0;
-            for (int a = 0; a < 4; ++a) {
-                double l = 1.0;
-                for (int b = 0; b < 4; ++b)
-                    if (b != a) l *= (0.0 - mm[b]) / (mm[a] - mm[b]);
-                v += l * tt[a];
+        L.fan_k0 = -1;
+        if (fan_usable<4>(psi, K, k0 - 1, R, L.psi_r)) {
+            L.fan_k0 = k0;
+            if (!done) {
+                const double v = fan_theta(L.a_min, step, k0 - 1) + step * fan_root<4>(psi, k0 - 1, R, L.psi_r, false, 0.0, 0.0);
+                if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
             }
-            if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
         }
     }
     if (!(th0 > fmin(L.ta, L.tb) && th0 < fmax(L.ta, L.tb))) th0 = 0.5 * (L.ta + L.tb);

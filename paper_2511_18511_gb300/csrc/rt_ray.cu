@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, 
             L.phase = 0;
             L.psi_at_lo = 0.0;
             L.best_d2 = CUDART_INF;
+            L.fan_k0 = -1;
             if (fan_rays >= 2 && isnan(tin)) {
                 int e, r;
                 pair_of(G, k, e, r);
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, 
         if (trace_step(C, G, ts, ns)) {
             const TraceOut o = trace_end(C, G, ts, L.xe, L.ye, L.xr, L.yr, ns);
             steps += o.steps;
-            if (link_update(G, L, o, tol, max_iter)) {
+            if (link_update(G, L, o, tol, max_iter, fan_rays >= 2 ? fan : nullptr, fan_rays)) {
                 const int k = L.k;
                 const int st = (L.best_d2 <= tol * tol) ? RT_RAY_OK
                                : (L.best_d2 == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);

@@ -44,6 +44,12 @@ MUTANTS = {
     "speed_units": ("F->c[k] = v * 1e-3;", "F->c[k] = v * 1e-2;"),
     "slowness_uses_c": ("f[3] += S.w[q] * F->s[k];", "f[3] += S.w[q] * F->c[k];"),
     "heun_end_slope_only": ("out[q] = st[q] + 0.5 * hs * (k1[q] + k2[q]);", "out[q] = st[q] + hs * k2[q];"),
+    "fan_points_angle_off_by_one": ("        t[q] = fan_theta(a_min, step, k);\n",
+                                    "        t[q] = fan_theta(a_min, step, k + 1);\n"),
+    "fan_inverse_poly_node_dropped": ("if (b != a) l *= (0.0 - m[b]) / (m[a] - m[b]);",
+                                      "if (b != a && b != n - 1) l *= (0.0 - m[b]) / (m[a] - m[b]);"),
+    "fan_second_angle_without_trace": ("const double m5[5] = {cur.m, m4[0], m4[1], m4[2], m4[3]};",
+                                       "const double m5[5] = {prev.m, m4[0], m4[1], m4[2], m4[3]};"),
 }
 
 # fast pins first; a mutant is killed by the first pin that fails
@@ -60,6 +66,7 @@ PINS = [
     pins.test_paper_acoustic_length_experiment,
     pins.test_fisheye_ring_closed_form_converges_h2,
     pins.test_adjoint_matches_central_differences,
+    pins.test_fan_start_prediction_accuracy,
 ]
 
 

@@ -477,3 +477,23 @@ def test_fan_start_brute_force_bracket(orc):
     assert (r["status"] == 0).all()
     d = np.angle(np.exp(1j * (r["theta"] - r0["theta"])))
     assert np.abs(d).max() < 1e-6
+
+
+def test_fan_start_prediction_accuracy(orc):
+    """The fan start's predictions are high order: on the 128^2 / 64-ring
+    medium with 128 fan rays the first angle (inverse polynomial through the
+    eight rays around the interval) links >= 90 % of the pairs to 1e-4 mm in
+    one trace (measured 93.7 %; the four-ray cubic alone: 76.7 %); with 64 fan
+    rays the second angle (inverse quartic through the first trace and four
+    rays) leaves <= 1 % of the pairs needing a third trace (measured 0.1 %; the
+    secant with the interval end: 8.0 %). The rays linked are the
+    straight-start ones."""
+    w = P.cfg_small()
+    r = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=128)
+    assert (r["status"] == 0).all()
+    assert (r["iters"] == 1).mean() >= 0.90, np.bincount(r["iters"])
+    r64 = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=64)
+    assert (r64["status"] == 0).all()
+    assert (r64["iters"] >= 3).mean() <= 0.01, np.bincount(r64["iters"])
+    r0 = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=0)
+    np.testing.assert_allclose(r["tof"], r0["tof"], rtol=1e-8)
