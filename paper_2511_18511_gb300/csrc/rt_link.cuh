@@ -383,17 +383,23 @@ template <> struct LinkOcc<float> { static constexpr int blocks = 6; };
 // Scatters w * alpha_m * phi_j(x_m) into g (FP64 atomics), one flush of the
 // four nodes per run of consecutive points in one cell. The node weights are
 // formed in the marching precision and widened exactly to FP64 for the atomic.
+// A run the ray has left waits in `prev` for the next periodic flush (every
+// kFlushEvery points), which the lanes of a warp whose rays started together
+// reach together, instead of each lane flushing at its own cell crossings
+// while the warp's other lanes wait; a second crossing before that flush
+// flushes the waiting run at once. Each run is still flushed exactly once.
+constexpr int kFlushEvery = 2;
 template <typename T>
 struct AdjSink {
     double* g;
     T w;
     int nx, ny;
-    CellAcc<T> acc;
-    __device__ __forceinline__ void flush() {
-        if (acc.ai == INT_MIN) return;
-        const T w11 = acc.Wxy, w10 = acc.Wx - acc.Wxy, w01 = acc.Wy - acc.Wxy;
-        const T w00 = (acc.W - acc.Wx) - w01;
-        const int i = min(max(acc.ai, 0), nx - 2), j = min(max(acc.aj, 0), ny - 2);
+    int tick;
+    CellAcc<T> acc, prev;
+    __device__ __forceinline__ void flush(const CellAcc<T>& a) {
+        const T w11 = a.Wxy, w10 = a.Wx - a.Wxy, w01 = a.Wy - a.Wxy;
+        const T w00 = (a.W - a.Wx) - w01;
+        const int i = min(max(a.ai, 0), nx - 2), j = min(max(a.aj, 0), ny - 2);
         double* p = g + (size_t)j * nx + i;
         atomicAdd(p, to_double(w * w00));
         atomicAdd(p + 1, to_double(w * w10));
@@ -402,7 +408,8 @@ struct AdjSink {
     }
     __device__ __forceinline__ void add(int ci, int cj, T tx, T ty, T a) {
         if (ci != acc.ai || cj != acc.aj) {
-            flush();
+            if (prev.ai != INT_MIN) flush(prev);
+            prev = acc;
             acc.reset();
             acc.ai = ci;
             acc.aj = cj;
@@ -411,15 +418,22 @@ struct AdjSink {
         acc.Wx += a * tx;
         acc.Wy += a * ty;
         acc.Wxy += a * tx * ty;
+        if (++tick == kFlushEvery) {
+            tick = 0;
+            if (prev.ai != INT_MIN) flush(prev);
+            prev.ai = INT_MIN;
+        }
     }
     __device__ __forceinline__ void finish() {
-        flush();
-        acc.reset();
+        if (prev.ai != INT_MIN) flush(prev);
+        if (acc.ai != INT_MIN) flush(acc);
+        init();
     }
-    __device__ __forceinline__ void init() { acc.reset(); }
+    __device__ __forceinline__ void init() {
+        acc.reset();
+        prev.reset();
+        tick = 0;
+    }
 };
-
-
-
 
 }  // namespace rt
