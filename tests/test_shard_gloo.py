@@ -61,3 +61,59 @@ def test_sharded_adjoint_equals_unsharded(tmp_path, orc):
     g_all = P.SplitMix64(3).normal(w.n_pairs)
     full = orc.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, r["theta"], g_all)
     assert np.abs(sharded - full).max() <= 1e-13 * np.abs(full).max()
+
+
+def test_frequency_blocks_partition():
+    for n_freq, world in ((8, 2), (8, 3), (3, 4), (1, 2), (16, 8)):
+        parts = [shard.frequencies_of(r, world, n_freq) for r in range(world)]
+        np.testing.assert_array_equal(np.concatenate(parts), np.arange(n_freq))
+
+
+def _born_case():
+    from paper_2511_18511_gb300 import phantoms as P
+    from tests.test_oracle_born_pins import _synthetic_maps
+    g = P.Grid(24, 24, 0.5)
+    R = 5.5
+    tx = P.ring(6, R)
+    T, A = _synthetic_maps(g, tx, 3)
+    f = P.born_frequencies(5)
+    rng = P.SplitMix64(17)
+    dc = rng.normal(g.nx * g.ny).reshape(g.ny, g.nx)
+    n = len(f) * len(tx) ** 2
+    d = (rng.normal(n) + 1j * rng.normal(n)).reshape(len(f), len(tx), len(tx))
+    return g, R, T, A, f, dc, d
+
+
+def _born_worker(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    g, R, T, A, f, dc, d = _born_case()
+    mine = shard.frequencies_of(rank, world, len(f))
+    d_loc = oracle.born_apply(g, R, T, A, f[mine], dc, nthreads=1)
+    d_all = shard.allgather_frequencies(torch.from_numpy(d_loc.copy()), len(f))
+    adj = torch.from_numpy(oracle.born_adjoint(g, R, T, A, f[mine], d[mine], nthreads=1).copy())
+    shard.allreduce_sum(adj)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "born_apply.npy"), d_all.numpy())
+        np.save(os.path.join(out_dir, "born_adjoint.npy"), adj.numpy())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_born_frequency_sharding_equals_unsharded(tmp_path, orc, world):
+    """Ray-Born over ranks: each rank applies the Born map for its block of the
+    5 frequencies (3 ranks: blocks of 1, 2, 2), one all-gather assembles the
+    data, and the adjoint of each rank's block summed by one all-reduce equals
+    the unsharded adjoint."""
+    mp.start_processes(_born_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    g, R, T, A, f, dc, d = _born_case()
+    full = orc.born_apply(g, R, T, A, f, dc)
+    got = np.load(tmp_path / "born_apply.npy")
+    assert got.shape == full.shape
+    np.testing.assert_array_equal(got, full)
+    adj = orc.born_adjoint(g, R, T, A, f, d)
+    got_adj = np.load(tmp_path / "born_adjoint.npy")
+    assert np.abs(got_adj - adj).max() <= 1e-13 * np.abs(adj).max()
