@@ -97,9 +97,13 @@ typedef struct {
     double tol_mm;       /* linking tolerance on |x_hit - x_r| > 0 */
     int32_t fan_rays;    /* cold starts: 0 = straight line to the receiver (paper
                             Sec. 3.4.1) with a near-tangent orientation probe; K >= 2 =
-                            a fan of K rays per emitter predicts the first angle
-                            and a bracket (256 is the usual); ignored by the calls
-                            that take fixed angles */
+                            a fan of K rays per emitter predicts a bracket, the
+                            first angle (inverse interpolation through the eight,
+                            else four, fan rays around the root) and, when the
+                            first trace misses, the second (inverse quartic through
+                            that trace and four fan rays); 256 is the binding's
+                            default, 768 suits the 512-element ring at 95 mm;
+                            ignored by the calls that take fixed angles */
     int32_t block_threads; /* rt_batch_run only: rays (threads) per block of the
                             persistent kernel, 0 (= 128), 64, 128 or 256 */
     int32_t step_unroll;   /* rt_batch_run only: RK4 steps per work-queue check,
