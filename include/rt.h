@@ -328,11 +328,21 @@ int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* opt, const 
  * amplitude choice of rtborn_maps. */
 #define RTBORN_ETA_US 1e-2f
 
-/* GEMM arithmetic of rtborn_apply / rtborn_adjoint (complex64 in and out). */
+/* Contraction arithmetic of rtborn_apply / rtborn_adjoint (complex64 in and
+ * out). Both are this library's kernels. */
 enum rtborn_gemm {
-    RTBORN_GEMM_FP32 = 0,    /* FP32 multiply-add (SIMT) */
-    RTBORN_GEMM_BF16X9 = 1   /* FP32 emulated on the BF16 tensor cores (each
-                                operand split into three BF16 parts) */
+    RTBORN_GEMM_FP32 = 0,    /* FP32 multiply-add on the CUDA cores: E and W formed
+                                in workspace (2 x 8 n_tx n_in bytes), then a tiled
+                                complex GEMM per frequency */
+    RTBORN_GEMM_TF32X3 = 1   /* tensor cores (tcgen05, kind::tf32, accumulators in
+                                tensor memory): every operand value split into two
+                                TF32 terms, hi = tf32(v), lo = tf32(v - hi), and each
+                                product formed as hi*hi + hi*lo + lo*hi (~2^-21
+                                relative error per product, FP32 accumulation); E is
+                                formed inside the kernels from the maps, d's symmetry
+                                d[e][r] = d[r][e] halves the work (only blocks of
+                                128 x 128 transducers with e-block <= r-block are
+                                contracted). The default. */
 };
 
 /*
@@ -389,8 +399,12 @@ int rtborn_maps(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, int3
  *   gemm_mode enum rtborn_gemm.
  *   d_out     [n_freq][n_tx][n_tx] complex64 out, interleaved (re, im) floats.
  * The first call for a grid and ring builds the list of inside nodes on the
- * host and synchronises the stream once. Workspace: 2 x 8 bytes x n_tx x
- * (inside nodes), reused over frequencies and calls.
+ * host and synchronises the stream once. Workspace (reused over calls):
+ * RTBORN_GEMM_TF32X3 128 KB per frequency and 128 x 128 block pair (10 MB
+ * for 512 transducers and 8 frequencies); RTBORN_GEMM_FP32 2 x 8 bytes x
+ * n_tx x (inside nodes). A tensor-core launch whose bounded device wait
+ * expires (2 s without progress) writes NaN to every output of the call
+ * instead of hanging.
  */
 int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
                  const float* A, int32_t n_freq, const double* f_mhz, const float* dc_mps,
@@ -403,6 +417,10 @@ int rtborn_apply(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_
  * for nodes inside the ring, 0 elsewhere (the diagonal of d is ignored).
  *   d_in      [n_freq][n_tx][n_tx] complex64, interleaved.
  *   dc_out    [ny*nx] float out.
+ * Only the symmetric part of d contributes (E_e E_r is symmetric in e, r).
+ * Workspace with RTBORN_GEMM_TF32X3: 512 KB per frequency and 128 x 128
+ * block pair (the split, pre-swizzled operand tiles of d; 40 MB for 512
+ * transducers and 8 frequencies) plus 4 bytes per inside node and frequency.
  * Other arguments as for rtborn_apply.
  */
 int rtborn_adjoint(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
@@ -440,6 +458,28 @@ int rtborn_apply_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, in
 int rtborn_adjoint_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, int32_t n_tx, const float* T,
                        const float* A, const float* L, double y, int32_t n_freq, const double* f_mhz,
                        const float* d_in, int32_t gemm_mode, float* dc_out, void* stream);
+
+/* ------------------------------------------------------- measurement service
+ * Microbenchmarks of the hardware rates that the kernels above are measured
+ * against (the paper reports no timing and has no counterpart). Each call
+ * enqueues one kernel of `blocks` x 256 threads on `stream`; the caller times
+ * it with events on that stream and divides the work stated here by the time.
+ * Every pointer is device memory; `sink` receives one value per thread
+ * (blocks * 256 elements of the stated type) so that no work is elided.
+ * Returns RT_OK, RT_EINVAL (bad argument, nothing enqueued) or RT_ECUDA.
+ *
+ * rt_peak_fma — dtype 0: FP32, 1: FP64 (sink of that type); iters a positive
+ *   multiple of 8; 8 independent fused multiply-add chains per thread and
+ *   iteration: FLOPs = blocks * 256 * iters * 16.
+ * rt_peak_gather — iters x 8 random 16-byte loads per thread from buf
+ *   (n_vec float4, n_vec a power of two <= 2^28; 16 MiB = 2^20 float4 stays
+ *   resident in L2): useful bytes = blocks * 256 * iters * 128.
+ * rt_peak_read — `passes` coalesced sweeps of the whole grid over buf (n_vec
+ *   float4): bytes = passes * n_vec * 16.
+ */
+int rt_peak_fma(int32_t dtype, int32_t blocks, int32_t iters, void* sink, void* stream);
+int rt_peak_gather(const void* buf, int64_t n_vec, int32_t blocks, int32_t iters, float* sink, void* stream);
+int rt_peak_read(const void* buf, int64_t n_vec, int32_t blocks, int32_t passes, float* sink, void* stream);
 
 #ifdef __cplusplus
 }

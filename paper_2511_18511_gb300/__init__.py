@@ -335,7 +335,7 @@ def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, pr
 
 # ---------------------------------------------------------------- ray-Born
 
-GEMM_MODES = {"fp32": _L.RTBORN_GEMM_FP32, "bf16x9": _L.RTBORN_GEMM_BF16X9}
+GEMM_MODES = {"fp32": _L.RTBORN_GEMM_FP32, "tf32x3": _L.RTBORN_GEMM_TF32X3}
 
 
 @dataclasses.dataclass
@@ -406,7 +406,7 @@ def _check_maps(maps: BornMaps):
             raise ValueError("maps have the wrong shape")
 
 
-def rtborn_apply(maps: BornMaps, f_mhz, dc: torch.Tensor, gemm: str = "bf16x9", ctx: Optional[Context] = None,
+def rtborn_apply(maps: BornMaps, f_mhz, dc: torch.Tensor, gemm: str = "tf32x3", ctx: Optional[Context] = None,
                  stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Born data d[f, e, r] (complex64) of the perturbation dc (m/s, float32
     [ny, nx]) at frequencies f_mhz."""
@@ -425,7 +425,7 @@ def rtborn_apply(maps: BornMaps, f_mhz, dc: torch.Tensor, gemm: str = "bf16x9", 
     return out
 
 
-def rtborn_adjoint(maps: BornMaps, f_mhz, d: torch.Tensor, gemm: str = "bf16x9", ctx: Optional[Context] = None,
+def rtborn_adjoint(maps: BornMaps, f_mhz, d: torch.Tensor, gemm: str = "tf32x3", ctx: Optional[Context] = None,
                    stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Adjoint of rtborn_apply: float32 [ny, nx] from complex64 d[f, e, r]."""
     _check_maps(maps)
@@ -458,6 +458,6 @@ class Born(torch.autograd.Function):
         return rtborn_adjoint(fctx.maps, fctx.f, g, gemm=fctx.gemm), None, None, None
 
 
-def born(dc: torch.Tensor, maps: BornMaps, f_mhz, gemm: str = "bf16x9") -> torch.Tensor:
+def born(dc: torch.Tensor, maps: BornMaps, f_mhz, gemm: str = "tf32x3") -> torch.Tensor:
     """Differentiable Born data of dc (float32 [ny, nx])."""
     return Born.apply(dc, maps, f_mhz, gemm)

@@ -37,7 +37,7 @@ def up_to_date() -> bool:
 
 
 def _rpath():
-    """Run path to the toolkit's lib64 (cuBLAS), found from nvcc's location."""
+    """Run path to the toolkit's lib64, found from nvcc's location."""
     import shutil
     nv = shutil.which(NVCC)
     if not nv:
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", *_rpath()]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, *_rpath()]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

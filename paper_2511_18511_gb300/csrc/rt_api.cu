@@ -214,9 +214,8 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (ctx->batch_desc) cudaFree(ctx->batch_desc);
     if (ctx->batch_desc_host) cudaFreeHost(ctx->batch_desc_host);
     for (void* p : {ctx->born_field, ctx->born_bsf, ctx->born_keys, (void*)ctx->born_idx, ctx->born_E, ctx->born_W, ctx->born_aux,
-                    ctx->born_acc})
+                    ctx->born_acc, ctx->born_err})
         if (p) cudaFree(p);
-    if (ctx->cublas) rt::destroy_blas(ctx->cublas);
     delete ctx;
 }
 

@@ -43,14 +43,14 @@
 //
 // Born map (rtborn_apply), per frequency f (omega = 2 pi f rad/us):
 //     d[f][e][r] = omega^2 h^2 sum_{|x| < R} E_e(x) E_r(x) dc(x),  e != r,
-// E_t = A_t exp(i omega T_t) over the nodes inside the ring (a compact list).
-// E and W = omega^2 h^2 dc E are formed per frequency by one kernel (the phase
-// reduced as 2 pi frac(f T) with a compensated product, then sincospi), and
-// d = W^T E is a dense complex GEMM (cuBLAS, complex64, FP32 or the
-// BF16x9-emulated FP32 tensor-core mode). The adjoint (rtborn_adjoint) is
-//     dc~(x) = Re sum_f omega^2 h^2 sum_{e != r} conj(E_e E_r) d[f][e][r]
-//            = Re sum_f omega^2 h^2 sum_e E_e(x) V(x, e),  V = E conj(D_f)
-// (diagonal of D zeroed): one GEMM and one column reduction per frequency.
+// E_t = A_t exp(i omega T_t) over the nodes inside the ring (a compact list),
+// the phase reduced as 2 pi frac(f T) with a compensated product. The adjoint
+// (rtborn_adjoint) is
+//     dc~(x) = Re sum_f omega^2 h^2 sum_{e != r} conj(E_e E_r) d[f][e][r].
+// Both contractions run in rt_born_tc.cu: on the tensor cores (tcgen05,
+// two-term TF32 split, E formed in the kernels' operand producers; the
+// default, RTBORN_GEMM_TF32X3) or as FP32 SIMT complex GEMMs over E and
+// W = omega^2 h^2 dc E formed by k_born_efield below (RTBORN_GEMM_FP32).
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -58,7 +58,6 @@
 #include <string>
 #include <vector>
 
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include "rt_internal.h"
@@ -589,8 +588,6 @@ __global__ void k_born_scatter(int n_in, const int* __restrict__ idx, const doub
 
 }  // namespace
 
-void destroy_blas(void* handle) { cublasDestroy((cublasHandle_t)handle); }
-
 }  // namespace rt
 
 // ------------------------------------------------------------------ host side
@@ -644,6 +641,10 @@ int inside_list(rt_ctx* ctx, const rt_grid& g, double R, cudaStream_t s, int* n_
             if (x * x + y * y < R * R) idx.push_back(j * g.nx + i);
         }
     if (idx.empty()) return bfail(ctx, RT_EINVAL, "no grid node inside the ring");
+    const int n_inside = (int)idx.size();
+    // padded with node 0 to a multiple of 128 plus 128, so that whole tiles of
+    // the contraction kernels read valid nodes
+    idx.resize(((idx.size() + 127) / 128 + 1) * 128, 0);
     size_t have = ctx->born_idx_bytes;
     int rc = grow(ctx, (void**)&ctx->born_idx, &have, idx.size() * sizeof(int), s, "inside-node");
     if (rc) return rc;
@@ -657,33 +658,8 @@ int inside_list(rt_ctx* ctx, const rt_grid& g, double R, cudaStream_t s, int* n_
     ctx->born_idx_geo[1] = g.x0_mm;
     ctx->born_idx_geo[2] = g.y0_mm;
     ctx->born_idx_geo[3] = R;
-    ctx->born_n_in = (int)idx.size();
+    ctx->born_n_in = n_inside;
     *n_in = ctx->born_n_in;
-    return RT_OK;
-}
-
-int blas(rt_ctx* ctx, cudaStream_t s, cublasHandle_t* h) {
-    if (!ctx->cublas) {
-        cublasHandle_t hh = nullptr;
-        if (cublasCreate(&hh) != CUBLAS_STATUS_SUCCESS) return bfail(ctx, RT_ECUDA, "cublasCreate failed");
-        ctx->cublas = hh;
-    }
-    *h = (cublasHandle_t)ctx->cublas;
-    if (cublasSetStream(*h, s) != CUBLAS_STATUS_SUCCESS) return bfail(ctx, RT_ECUDA, "cublasSetStream failed");
-    return RT_OK;
-}
-
-int gemm(rt_ctx* ctx, cublasHandle_t h, int mode, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-         const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc) {
-    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-    cublasComputeType_t ct = CUBLAS_COMPUTE_32F_PEDANTIC;
-    if (mode == RTBORN_GEMM_BF16X9) {
-        ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
-        cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER);
-    }
-    const cublasStatus_t st = cublasGemmEx(h, ta, tb, m, n, k, &one, A, CUDA_C_32F, lda, B, CUDA_C_32F, ldb, &zero, C,
-                                           CUDA_C_32F, ldc, ct, CUBLAS_GEMM_DEFAULT);
-    if (st != CUBLAS_STATUS_SUCCESS) return bfail(ctx, RT_ECUDA, "cublasGemmEx failed (status " + std::to_string((int)st) + ")");
     return RT_OK;
 }
 
@@ -696,18 +672,32 @@ int check_born_args(rt_ctx* ctx, const rt_grid* grid, double R, int32_t n_tx, co
     if (n_freq < 0 || (n_freq > 0 && !f_mhz)) return bfail(ctx, RT_EINVAL, "frequencies invalid");
     for (int f = 0; f < n_freq; ++f)
         if (!std::isfinite(f_mhz[f])) return bfail(ctx, RT_EINVAL, "frequency not finite");
-    if (mode != RTBORN_GEMM_FP32 && mode != RTBORN_GEMM_BF16X9) return bfail(ctx, RT_EINVAL, "unknown GEMM mode");
+    if (mode != RTBORN_GEMM_FP32 && mode != RTBORN_GEMM_TF32X3) return bfail(ctx, RT_EINVAL, "unknown GEMM mode");
     return RT_OK;
 }
 
-// per-frequency workspace: E and W (or V) [n_tx][n_in] complex64
-int born_ws(rt_ctx* ctx, int n_tx, int n_in, cudaStream_t s) {
+// SIMT path: per-frequency E and W (or V) [n_tx][n_in] complex64, d^H or the
+// adjoint's FP64 accumulator
+int born_ws_simt(rt_ctx* ctx, int n_tx, int n_in, cudaStream_t s) {
     const size_t eb = sizeof(float2) * (size_t)n_tx * (size_t)n_in;
     int rc = grow(ctx, &ctx->born_E, &ctx->born_E_bytes, eb, s, "Born E");
     if (!rc) rc = grow(ctx, &ctx->born_W, &ctx->born_W_bytes, eb, s, "Born W");
     if (!rc) rc = grow(ctx, &ctx->born_aux, &ctx->born_aux_bytes,
                        std::max(sizeof(float2) * (size_t)n_tx * n_tx, sizeof(double) * (size_t)n_in), s, "Born aux");
     if (!rc) rc = grow(ctx, &ctx->born_acc, &ctx->born_acc_bytes, sizeof(double) * (size_t)n_in, s, "Born acc");
+    return rc;
+}
+
+// tensor-core path: the error word and, per launch of up to kBornFreqMax
+// frequencies, the apply's partial sums or the adjoint's D' tiles and
+// per-frequency node sums
+int born_ws_tc(rt_ctx* ctx, int n_tx, int n_in, int n_freq, bool adjoint, cudaStream_t s) {
+    const int nf = std::min(n_freq, rt::kBornFreqMax);
+    int rc = grow(ctx, &ctx->born_err, &ctx->born_err_bytes, 256, s, "Born error word");
+    if (rc) return rc;
+    if (!adjoint) return grow(ctx, &ctx->born_acc, &ctx->born_acc_bytes, rt::born_tc_acc_bytes(n_tx, nf), s, "Born sums");
+    rc = grow(ctx, &ctx->born_E, &ctx->born_E_bytes, rt::born_tc_bd_bytes(n_tx, nf), s, "Born D' tiles");
+    if (!rc) rc = grow(ctx, &ctx->born_aux, &ctx->born_aux_bytes, sizeof(float) * (size_t)nf * n_in, s, "Born sums");
     return rc;
 }
 
@@ -723,9 +713,16 @@ int check_power_law(rt_ctx* ctx, double y, int32_t n_freq, const double* f_mhz) 
     return RT_OK;
 }
 
-void split_freq(double f, float* hi, float* lo) {
-    *hi = (float)f;
-    *lo = (float)(f - (double)*hi);
+// per-frequency constants: f = fh + fl (MHz), omega_s^y (y < 0: no
+// absorption), omega^2 h^2
+rt::BornFreq born_freq(double f_mhz, double h_mm, double y) {
+    rt::BornFreq q;
+    q.fh = (float)f_mhz;
+    q.fl = (float)(f_mhz - (double)q.fh);
+    q.wy = y >= 0.0 ? (float)std::pow(2.0 * rt::kPiB * f_mhz * 1e6, y) : 0.f;
+    const double om = 2.0 * rt::kPiB * f_mhz;
+    q.scale = (float)(om * om * h_mm * h_mm);
+    return q;
 }
 
 }  // namespace
@@ -852,29 +849,39 @@ int rtborn_apply_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, in
     if (n_freq == 0) return RT_OK;
     int n_in = 0;
     rc = inside_list(ctx, *grid, ring_radius_mm, s, &n_in);
-    if (!rc) rc = born_ws(ctx, n_tx, n_in, s);
-    cublasHandle_t h = nullptr;
-    if (!rc) rc = blas(ctx, s, &h);
     if (rc) return rc;
     const long long nn = (long long)grid->nx * grid->ny;
+    float2* d = (float2*)d_out;
+    if (gemm_mode == RTBORN_GEMM_TF32X3) {
+        if ((rc = born_ws_tc(ctx, n_tx, n_in, n_freq, false, s))) return rc;
+        e = cudaMemsetAsync(ctx->born_err, 0, sizeof(int), s);
+        for (int f0 = 0; e == cudaSuccess && f0 < n_freq; f0 += rt::kBornFreqMax) {
+            const int nf = std::min(n_freq - f0, rt::kBornFreqMax);
+            rt::BornFreq fq[rt::kBornFreqMax];
+            for (int f = 0; f < nf; ++f) fq[f] = born_freq(f_mhz[f0 + f], grid->h_mm, L ? y : -1.0);
+            const rt::BornTCJob job{n_tx, nf, n_in, nn, ctx->born_idx, T, A, L, dc_mps, fq, 0};
+            e = rt::launch_born_apply_tc(ctx->device, job, (float*)ctx->born_acc, d + (size_t)f0 * n_tx * n_tx,
+                                         (int*)ctx->born_err, s);
+        }
+        ctx->last_stream = s;
+        return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "Born apply kernels");
+    }
+    if ((rc = born_ws_simt(ctx, n_tx, n_in, s))) return rc;
     float2* E = (float2*)ctx->born_E;
     float2* W = (float2*)ctx->born_W;
-    float2* d = (float2*)d_out;
     const dim3 eg((n_in + 255) / 256, n_tx);
-    for (int f = 0; f < n_freq; ++f) {
-        float fh, fl;
-        split_freq(f_mhz[f], &fh, &fl);
-        const double om = 2.0 * rt::kPiB * f_mhz[f];
-        const float scale = (float)(om * om * grid->h_mm * grid->h_mm);
-        const float wy = L ? (float)std::pow(2.0 * rt::kPiB * f_mhz[f] * 1e6, y) : 0.f;
-        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, L, wy, fh, fl, scale, dc_mps, E, W);
-        // d(r, e) = sum_p W(p, r) E(p, e): column-major D = W^T E, stored at r + e n = d[e][r]
-        rc = gemm(ctx, h, gemm_mode, CUBLAS_OP_T, CUBLAS_OP_N, n_tx, n_tx, n_in, W, n_in, E, n_in,
-                  d + (size_t)f * n_tx * n_tx, n_tx);
-        if (rc) return rc;
+    e = cudaMemsetAsync(d, 0, sizeof(float2) * (size_t)n_freq * n_tx * n_tx, s);
+    for (int f = 0; e == cudaSuccess && f < n_freq; ++f) {
+        const rt::BornFreq q = born_freq(f_mhz[f], grid->h_mm, L ? y : -1.0);
+        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, L, q.wy, q.fh, q.fl, q.scale, dc_mps, E, W);
+        // d[e][r] = sum_p E[e][p] W[r][p]
+        e = rt::launch_cgemm(n_tx, n_tx, n_in, E, n_in, 1, W, n_in, 1, d + (size_t)f * n_tx * n_tx, n_tx, 1,
+                             ctx->device, s);
     }
-    rt::k_zero_diag<<<(n_tx * n_freq + 255) / 256, 256, 0, s>>>(d, n_tx, n_freq);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        rt::k_zero_diag<<<(n_tx * n_freq + 255) / 256, 256, 0, s>>>(d, n_tx, n_freq);
+        e = cudaGetLastError();
+    }
     ctx->last_stream = s;
     return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "Born apply kernels");
 }
@@ -904,31 +911,46 @@ int rtborn_adjoint_abs(rt_ctx* ctx, const rt_grid* grid, double ring_radius_mm, 
     if (n_freq == 0) return RT_OK;
     int n_in = 0;
     rc = inside_list(ctx, *grid, ring_radius_mm, s, &n_in);
-    if (!rc) rc = born_ws(ctx, n_tx, n_in, s);
-    cublasHandle_t h = nullptr;
-    if (!rc) rc = blas(ctx, s, &h);
     if (rc) return rc;
+    const float2* d = (const float2*)d_in;
+    if (gemm_mode == RTBORN_GEMM_TF32X3) {
+        if ((rc = born_ws_tc(ctx, n_tx, n_in, n_freq, true, s))) return rc;
+        e = cudaMemsetAsync(ctx->born_err, 0, sizeof(int), s);
+        for (int f0 = 0; e == cudaSuccess && f0 < n_freq; f0 += rt::kBornFreqMax) {
+            const int nf = std::min(n_freq - f0, rt::kBornFreqMax);
+            rt::BornFreq fq[rt::kBornFreqMax];
+            for (int f = 0; f < nf; ++f) fq[f] = born_freq(f_mhz[f0 + f], grid->h_mm, L ? y : -1.0);
+            const rt::BornTCJob job{n_tx, nf, n_in, nn, ctx->born_idx, T, A, L, nullptr, fq, 0};
+            e = rt::launch_born_adjoint_tc(ctx->device, job, d + (size_t)f0 * n_tx * n_tx, (float*)ctx->born_E,
+                                           (float*)ctx->born_aux, dc_out, f0 > 0, (int*)ctx->born_err, s);
+        }
+        ctx->last_stream = s;
+        return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "Born adjoint kernels");
+    }
+    if ((rc = born_ws_simt(ctx, n_tx, n_in, s))) return rc;
     float2* E = (float2*)ctx->born_E;
     float2* V = (float2*)ctx->born_W;
     float2* Dc = (float2*)ctx->born_aux;
     double* acc = (double*)ctx->born_acc;
-    const float2* d = (const float2*)d_in;
     const dim3 eg((n_in + 255) / 256, n_tx);
-    for (int f = 0; f < n_freq; ++f) {
-        float fh, fl;
-        split_freq(f_mhz[f], &fh, &fl);
-        const double om = 2.0 * rt::kPiB * f_mhz[f];
-        const float scale = (float)(om * om * grid->h_mm * grid->h_mm);
-        const float wy = L ? (float)std::pow(2.0 * rt::kPiB * f_mhz[f] * 1e6, y) : 0.f;
-        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, L, wy, fh, fl, 0.f, nullptr, E, nullptr);
+    for (int f = 0; e == cudaSuccess && f < n_freq; ++f) {
+        const rt::BornFreq q = born_freq(f_mhz[f], grid->h_mm, L ? y : -1.0);
+        rt::k_born_efield<<<eg, 256, 0, s>>>(n_in, ctx->born_idx, nn, T, A, L, q.wy, q.fh, q.fl, 0.f, nullptr, E,
+                                             nullptr);
         rt::k_conj_nodiag<<<(n_tx * n_tx + 255) / 256, 256, 0, s>>>(d + (size_t)f * n_tx * n_tx, Dc, n_tx);
-        // V(p, e) = sum_r E(p, r) Dc(r, e)
-        rc = gemm(ctx, h, gemm_mode, CUBLAS_OP_N, CUBLAS_OP_N, n_in, n_tx, n_tx, E, n_in, Dc, n_tx, V, n_in);
-        if (rc) return rc;
-        rt::k_born_reduce<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, n_tx, E, V, scale, acc, f == 0);
+        // V[e][p] = sum_r E[r][p] conj(d[e][r]), conj(d[e][r]) at Dc[e n_tx + r]
+        e = cudaMemsetAsync(V, 0, sizeof(float2) * (size_t)n_tx * n_in, s);
+        if (e == cudaSuccess)
+            e = rt::launch_cgemm(n_in, n_tx, n_tx, E, 1, n_in, Dc, n_tx, 1, V, 1, n_in, ctx->device, s);
+        if (e == cudaSuccess) {
+            rt::k_born_reduce<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, n_tx, E, V, q.scale, acc, f == 0);
+            e = cudaGetLastError();
+        }
     }
-    rt::k_born_scatter<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, ctx->born_idx, acc, dc_out);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        rt::k_born_scatter<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, ctx->born_idx, acc, dc_out);
+        e = cudaGetLastError();
+    }
     ctx->last_stream = s;
     return e == cudaSuccess ? RT_OK : bcuda(ctx, e, "Born adjoint kernels");
 }

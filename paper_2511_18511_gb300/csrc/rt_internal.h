@@ -33,7 +33,8 @@ struct rt_ctx {
     size_t scan_bytes = 0;
     cudaStream_t last_stream = nullptr;
     // ray-Born workspace (rtborn_*): packed field with Hessian, fan-map keys,
-    // inside-ring node list, per-frequency E / W(V) and small buffers, cuBLAS
+    // inside-ring node list, contraction workspace (partial sums, D' tiles;
+    // E / W(V) of the SIMT path) and small buffers
     void* born_field = nullptr;
     size_t born_field_bytes = 0;
     void* born_bsf = nullptr;       // per-cell bicubics of c and s (B-spline fans)
@@ -53,7 +54,8 @@ struct rt_ctx {
     size_t born_aux_bytes = 0;
     void* born_acc = nullptr;
     size_t born_acc_bytes = 0;
-    void* cublas = nullptr;         // cublasHandle_t, created on first Born call
+    void* born_err = nullptr;       // device word: a contraction kernel's bounded wait expired
+    size_t born_err_bytes = 0;
 };
 
 namespace rt {
@@ -94,7 +96,37 @@ cudaError_t launch_scan(int64_t* row_ptr, int n, void* tmp, size_t* tmp_bytes, c
 // bytes per packed cell for a precision and interpolator
 size_t node_bytes(int prec, int interp = RT_BILINEAR);
 
-// Releases the context's cuBLAS handle (rt_born.cu).
-void destroy_blas(void* handle);
+// Born contractions (rt_born_tc.cu). Per-frequency constants: f = fh + fl
+// (MHz), the absorption exponent factor wy = omega_s^y and the weight
+// scale = omega^2 h^2.
+struct BornFreq {
+    float fh, fl, wy, scale;
+};
+constexpr int kBornFreqMax = 64;   // frequencies per contraction launch
+struct BornTCJob {
+    int n_tx, n_freq, n_in;           // n_freq <= kBornFreqMax
+    long long nn;             // nodes per map
+    const int* idx;           // inside-ring nodes, padded to a multiple of 128 (+128) with node 0
+    const float* T;
+    const float* A;
+    const float* L;           // maps [n_tx][nn]; L NULL without absorption
+    const float* dc;          // [nn] (apply only)
+    const BornFreq* fq;       // HOST [n_freq], passed to the kernels as parameters
+    int chunk;                // apply: K-tiles per accumulation run (0 = the default)
+};
+// workspace of the tensor-core apply (partial sums) and adjoint (D' tiles)
+size_t born_tc_acc_bytes(int n_tx, int n_freq);
+size_t born_tc_bd_bytes(int n_tx, int n_freq);
+// apply: d [n_freq][n_tx][n_tx] complex64; adjoint: dc_out[idx[p]] (=, or +=
+// with accumulate) for the inside nodes (part: [n_freq][n_in] floats of
+// workspace); err: device word that a kernel whose bounded wait expired sets,
+// after which the finishing kernel writes NaN to the outputs.
+cudaError_t launch_born_apply_tc(int device, const BornTCJob& j, float* acc, float2* d, int* err, cudaStream_t s);
+cudaError_t launch_born_adjoint_tc(int device, const BornTCJob& j, const float2* d, float* bd, float* part,
+                                   float* dc_out, bool accumulate, int* err, cudaStream_t s);
+// FP32 SIMT complex GEMM C(m, n) += sum_k A(m, k) B(n, k) (element strides; C pre-zeroed)
+cudaError_t launch_cgemm(int M, int N, int K, const float2* A, long long sam, long long sak, const float2* B,
+                         long long sbn, long long sbk, float2* C, long long scm, long long scn, int device,
+                         cudaStream_t s);
 
 }  // namespace rt

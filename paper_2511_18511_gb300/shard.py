@@ -25,15 +25,24 @@ def emitters_of(rank: int, world: int, n_tx: int) -> np.ndarray:
     return np.arange(lo, hi)
 
 
-def shard_pairs(rank: int, world: int, n_tx: int) -> np.ndarray:
-    """(e, r) pairs with e in this rank's emitter block, emitter-major, int32 [P, 2]."""
+def shard_pairs(rank: int, world: int, n_tx: int, longest_first: bool = False) -> np.ndarray:
+    """(e, r) pairs with e in this rank's emitter block, int32 [P, 2]:
+    emitter-major, or with longest_first ordered by ring offset from the
+    diameter outwards (the longest chords first, as the library's queue serves
+    the implicit all-pairs list), so that a linking launch ends on its
+    shortest rays."""
     e = emitters_of(rank, world, n_tx)
     if e.size == 0:
         return np.zeros((0, 2), np.int32)
     ee = np.repeat(e, n_tx - 1)
     rr = np.tile(np.arange(n_tx - 1), e.size)
     rr = rr + (rr >= ee)
-    return np.stack([ee, rr], 1).astype(np.int32)
+    pairs = np.stack([ee, rr], 1).astype(np.int32)
+    if longest_first:
+        off = (pairs[:, 1] - pairs[:, 0]) % n_tx
+        far = np.minimum(off, n_tx - off)          # ring distance: n_tx / 2 is the diameter
+        pairs = pairs[np.lexsort((pairs[:, 0], -far))]
+    return pairs
 
 
 def global_index(pairs: np.ndarray, n_tx: int) -> np.ndarray:
@@ -78,3 +87,25 @@ def allgather_frequencies(local, n_freq: int, group=None):
     full = torch.cat([p[:n] for p, n in zip(parts, sizes)])
     return torch.view_as_complex(full.contiguous()) if local.is_complex() else full
 
+
+
+class ShardedToF:
+    """One ToF inversion step (link + misfit adjoint) of a single problem
+    split over ranks by emitter: every rank links and back-projects its own
+    pairs, and one all-reduce (sum) of the grid gradient completes the step.
+
+    link(pairs, c) -> (theta, tof) and adjoint(pairs, c, theta, residual) -> g
+    are the per-rank operators (the CUDA library's on GPUs, the oracle's in
+    the CPU tests), so that both run this same step."""
+
+    def __init__(self, rank: int, world: int, n_tx: int, link, adjoint, allreduce=allreduce_sum):
+        self.rank, self.world, self.n_tx = rank, world, n_tx
+        self.pairs = shard_pairs(rank, world, n_tx, longest_first=True)
+        self.link, self.adjoint, self.allreduce = link, adjoint, allreduce
+
+    def step(self, c, tof_meas):
+        """tof_meas: measured times of this rank's pairs (in self.pairs order);
+        returns (g summed over ranks, theta, tof) of the misfit 0.5 |T - T_meas|^2."""
+        theta, tof = self.link(self.pairs, c)
+        g = self.adjoint(self.pairs, c, theta, tof - tof_meas)
+        return self.allreduce(g), theta, tof

@@ -88,7 +88,7 @@ def test_maps_small_vs_oracle(small, P):
 
 # --------------------------------------------------------- Born map, adjoint
 
-@pytest.mark.parametrize("gemm", ["fp32", "bf16x9"])
+@pytest.mark.parametrize("gemm", ["fp32", "tf32x3"])
 def test_apply_adjoint_synthetic_maps_vs_oracle(rt, P, orc, gemm):
     """Born map and adjoint of the same float32 maps on both sides (128^2,
     64-ring, 8 frequencies): complex64 data within 1e-4 relative L2 of the
@@ -128,7 +128,7 @@ def test_chain_maps_apply_vs_oracle(small, rt, orc):
     assert e <= 2e-3
 
 
-@pytest.mark.parametrize("gemm", ["fp32", "bf16x9"])
+@pytest.mark.parametrize("gemm", ["fp32", "tf32x3"])
 def test_dot_product_identity_gpu(small, rt, P, gemm):
     """Re<F dc, d> = <dc, F* d> through the GPU calls (maps from the GPU)."""
     w, prob, maps, _, _ = small
@@ -264,10 +264,10 @@ def test_full_size_apply_adjoint_sampled(full, rt, P, orc):
     w, prob, maps, sel, T_o, A_o = full
     amb = _ambiguous(A_o, w.grid.h)
     dcm = np.where(amb, 0.0, w.dc).astype(np.float32)
-    d_all = rt.rtborn_apply(maps, w.f_mhz, torch.as_tensor(w.dc, dtype=torch.float32, device="cuda"), gemm="bf16x9")
+    d_all = rt.rtborn_apply(maps, w.f_mhz, torch.as_tensor(w.dc, dtype=torch.float32, device="cuda"), gemm="tf32x3")
     want_all = orc.born_apply(w.grid, w.ring_radius, T_o, A_o, w.f_mhz, w.dc.astype(np.float32).astype(np.float64))
     e_all = _rel_l2(_np(d_all)[:, sel][:, :, sel], want_all)
-    d = rt.rtborn_apply(maps, w.f_mhz, torch.as_tensor(dcm, device="cuda"), gemm="bf16x9")
+    d = rt.rtborn_apply(maps, w.f_mhz, torch.as_tensor(dcm, device="cuda"), gemm="tf32x3")
     want = orc.born_apply(w.grid, w.ring_radius, T_o, A_o, w.f_mhz, dcm.astype(np.float64))
     e = _rel_l2(_np(d)[:, sel][:, :, sel], want)
     print(f"full-size apply at the oracle-mapped pairs: rel L2 {e:.2e} away from caustic zones "
@@ -279,7 +279,7 @@ def test_full_size_apply_adjoint_sampled(full, rt, P, orc):
     full_d = torch.zeros((len(w.f_mhz), w.n_tx, w.n_tx), dtype=torch.complex64, device="cuda")
     idx = torch.as_tensor(sel, device="cuda")
     full_d[:, idx[:, None], idx[None, :]] = torch.as_tensor(ds_, dtype=torch.complex64, device="cuda")
-    g = _np(rt.rtborn_adjoint(maps, w.f_mhz, full_d, gemm="bf16x9"))
+    g = _np(rt.rtborn_adjoint(maps, w.f_mhz, full_d, gemm="tf32x3"))
     want_g = orc.born_adjoint(w.grid, w.ring_radius, T_o, A_o, w.f_mhz, ds_)
     e_g = _rel_l2(np.where(amb, 0, g), np.where(amb, 0, want_g))
     print(f"full-size adjoint of data on the oracle-mapped pairs: rel L2 {e_g:.2e} away from caustic zones")
@@ -287,7 +287,7 @@ def test_full_size_apply_adjoint_sampled(full, rt, P, orc):
     dc = torch.as_tensor(w.dc, dtype=torch.float32, device="cuda")
     dd = torch.as_tensor((rng.normal(len(w.f_mhz) * w.n_tx ** 2) + 1j * rng.normal(len(w.f_mhz) * w.n_tx ** 2))
                          .reshape(len(w.f_mhz), w.n_tx, w.n_tx), dtype=torch.complex64, device="cuda")
-    Fad = rt.rtborn_adjoint(maps, w.f_mhz, dd, gemm="bf16x9")
+    Fad = rt.rtborn_adjoint(maps, w.f_mhz, dd, gemm="tf32x3")
     lhs = float((torch.conj(d_all).to(torch.complex128) * dd.to(torch.complex128)).real.sum())
     rhs = float((dc.double() * Fad.double()).sum())
     scale = float((d_all.abs().double() * dd.abs().double()).sum())

@@ -117,3 +117,57 @@ def test_born_frequency_sharding_equals_unsharded(tmp_path, orc, world):
     adj = orc.born_adjoint(g, R, T, A, f, d)
     got_adj = np.load(tmp_path / "born_adjoint.npy")
     assert np.abs(got_adj - adj).max() <= 1e-13 * np.abs(adj).max()
+
+
+def test_longest_first_shards_partition_all_pairs():
+    """The longest-first order of a shard is a permutation of its pairs, with
+    ring distances non-increasing."""
+    for n_tx, world in ((64, 2), (64, 3), (512, 8)):
+        for r in range(world):
+            a = shard.shard_pairs(r, world, n_tx)
+            b = shard.shard_pairs(r, world, n_tx, longest_first=True)
+            assert {tuple(p) for p in a} == {tuple(p) for p in b} and len(a) == len(b)
+            off = (b[:, 1] - b[:, 0]) % n_tx
+            far = np.minimum(off, n_tx - off)
+            assert (np.diff(far) <= 0).all()
+
+
+def _step_worker(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from paper_2511_18511_gb300 import phantoms as P
+    w = P.cfg_small(n_tx=16)
+
+    def link(pairs, c):
+        r = oracle.link(w.grid, c, w.tx, w.ring_radius, w.ds, pairs=pairs, nthreads=1, fan_rays=64)
+        return r["theta"], r["tof"]
+
+    def adjoint(pairs, c, theta, res):
+        return torch.from_numpy(oracle.adjoint(w.grid, c, w.tx, w.ring_radius, w.ds, theta, res, pairs=pairs,
+                                               nthreads=1).copy())
+
+    step = shard.ShardedToF(rank, world, w.n_tx, link, adjoint)
+    _, t_meas = link(step.pairs, w.c * 1.005)
+    g, _, _ = step.step(w.c, t_meas)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "step.npy"), g.numpy())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_tof_step_equals_unsharded(tmp_path, orc, world):
+    """The step the bench runs on N GPUs (ShardedToF: link and misfit adjoint
+    of each rank's longest-first emitter block, then one all-reduce), run with
+    the oracle's operators on gloo ranks: the summed gradient equals the
+    unsharded step's."""
+    from paper_2511_18511_gb300 import phantoms as P
+    mp.start_processes(_step_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    got = np.load(tmp_path / "step.npy")
+    w = P.cfg_small(n_tx=16)
+    meas = orc.link(w.grid, w.c * 1.005, w.tx, w.ring_radius, w.ds, fan_rays=64)
+    r = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, fan_rays=64)
+    full = orc.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, r["theta"], r["tof"] - meas["tof"])
+    assert np.abs(got - full).max() <= 1e-13 * np.abs(full).max()
