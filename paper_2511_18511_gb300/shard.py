@@ -94,9 +94,10 @@ class ShardedToF:
     split over ranks by emitter: every rank links and back-projects its own
     pairs, and one all-reduce (sum) of the grid gradient completes the step.
 
-    link(pairs, c) -> (theta, tof) and adjoint(pairs, c, theta, residual) -> g
-    are the per-rank operators (the CUDA library's on GPUs, the oracle's in
-    the CPU tests), so that both run this same step."""
+    link(pairs, c) -> (theta, tof) and adjoint(pairs, c, theta, tof, tof_meas)
+    -> g (the gradient of the misfit with residual tof - tof_meas) are the
+    per-rank operators (the CUDA library's on GPUs, the oracle's in the CPU
+    tests), so that both run this same step."""
 
     def __init__(self, rank: int, world: int, n_tx: int, link, adjoint, allreduce=allreduce_sum):
         self.rank, self.world, self.n_tx = rank, world, n_tx
@@ -107,5 +108,5 @@ class ShardedToF:
         """tof_meas: measured times of this rank's pairs (in self.pairs order);
         returns (g summed over ranks, theta, tof) of the misfit 0.5 |T - T_meas|^2."""
         theta, tof = self.link(self.pairs, c)
-        g = self.adjoint(self.pairs, c, theta, tof - tof_meas)
+        g = self.adjoint(self.pairs, c, theta, tof, tof_meas)
         return self.allreduce(g), theta, tof

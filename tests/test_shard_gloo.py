@@ -144,9 +144,9 @@ def _step_worker(rank, world, port, out_dir):
         r = oracle.link(w.grid, c, w.tx, w.ring_radius, w.ds, pairs=pairs, nthreads=1, fan_rays=64)
         return r["theta"], r["tof"]
 
-    def adjoint(pairs, c, theta, res):
-        return torch.from_numpy(oracle.adjoint(w.grid, c, w.tx, w.ring_radius, w.ds, theta, res, pairs=pairs,
-                                               nthreads=1).copy())
+    def adjoint(pairs, c, theta, tof, tof_meas):
+        return torch.from_numpy(oracle.adjoint(w.grid, c, w.tx, w.ring_radius, w.ds, theta, tof - tof_meas,
+                                               pairs=pairs, nthreads=1).copy())
 
     step = shard.ShardedToF(rank, world, w.n_tx, link, adjoint)
     _, t_meas = link(step.pairs, w.c * 1.005)
