@@ -71,7 +71,7 @@ def load(path: str):
                             C.c_double, C.c_double, C.c_double, C.c_int64, _dp, _dp,
                             _lp, _dp, _ip]
     L.orc_link.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
-                           C.c_double, C.c_double, C.c_int32, C.c_int32, _dp, _dp, _dp, _ip, _ip,
+                           C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp, _ip, _ip,
                            C.c_int32]
     L.orc_tof.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip, C.c_double,
                           _dp, _dp, _dp, C.c_int32]
@@ -260,9 +260,11 @@ def _pairs_arg(pairs, n_tx):
     return p, p.shape[0]
 
 
-def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None, nthreads=0, fan_rays=0):
+def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None, nthreads=0, fan_rays=0,
+         fan_ds=0.0):
     """Link all pairs; returns dict(theta, tof, hit, status, iters). fan_rays = 0:
-    straight-line cold start; >= 2: fan-predicted cold start."""
+    straight-line cold start; >= 2: fan-predicted cold start, the fan's rays
+    traced at step fan_ds (0 = ds)."""
     c = _f64(c_mps)
     tx = _f64(tx).reshape(-1, 2)
     p, n_pairs = _pairs_arg(pairs, tx.shape[0])
@@ -273,7 +275,8 @@ def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None,
     iters = np.empty(n_pairs, np.int32)
     g = _grid(grid)
     rc = lib().orc_link(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds, tol,
-                        max_iter, fan_rays, _d(theta), _d(tof), _d(hit), _i(status), _i(iters), nthreads)
+                        max_iter, fan_rays, float(fan_ds), _d(theta), _d(tof), _d(hit), _i(status), _i(iters),
+                        nthreads)
     _check(rc, "link")
     return dict(theta=theta, tof=tof, hit=hit, status=status, iters=iters)
 

@@ -6,8 +6,7 @@
  * the CUDA path. Written for clarity, not speed: plain FP64, absolute
  * coordinates, one ray per OpenMP iteration, every sample interpolated afresh.
  *
- * Where the paper (arXiv:2511.18511) is silent, the readings below are used
- * (each is also listed in the design notes):
+ * Where the paper (arXiv:2511.18511) is silent, the readings below are used:
  *   R1 gradient: dc/dx, dc/dy from grid values by central differences (one-sided
  *      at edges), then interpolated bilinearly like c itself (Sec. 3.3.1: the
  *      gradient is obtained by interpolating grid values, not by differentiating
@@ -579,7 +578,11 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
  * that trace and the four fan rays (when those were usable and the trace
  * reached the ring), else the secant of the first trace and the interval end
  * with the smaller |misfit|; from there on the secant of the last two traces.
- * Either candidate outside the bracket gives way to the Regula-Falsi point. */
+ * Either candidate outside the bracket gives way to the Regula-Falsi point.
+ * The fan only predicts: its rays may be traced at their own step fan_ds
+ * (0 = the linking step ds), while their launch angles, the fan margin ds/R
+ * and every linking trace keep ds, so the bracket rule and the predictions
+ * are the same functions of the fan's interceptions. */
 static double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
 
 /* Value at m = 0 of the polynomial theta(m) through the n points (m_q, t_q),
@@ -613,7 +616,8 @@ static int fan_points(const double* psi, int K, int k_first, int n, double a_min
     return 1;
 }
 
-static void fan_for_emitter(const Field* F, double R, const double* xe, double ds, int K, double* psi) {
+static void fan_for_emitter(const Field* F, double R, const double* xe, double ds, double fan_ds, int K,
+                            double* psi) {
     const double phi_e = atan2(xe[1], xe[0]);
     const double th_lo = phi_e + 0.5 * M_PI, th_hi = phi_e + 1.5 * M_PI;
     double margin = ds / R;
@@ -622,7 +626,7 @@ static void fan_for_emitter(const Field* F, double R, const double* xe, double d
     const double step = (a_max - a_min) / (K - 1);
     for (int k = 0; k < K; ++k) {
         TraceRes tr;
-        trace(F, R, xe[0], xe[1], xe[0], xe[1], fan_theta(a_min, step, k), ds, NULL, NULL, 0, &tr);
+        trace(F, R, xe[0], xe[1], xe[0], xe[1], fan_theta(a_min, step, k), fan_ds, NULL, NULL, 0, &tr);
         psi[k] = (tr.flags & 3) ? NAN : mod_2pi(atan2(tr.hit[1], tr.hit[0]) - phi_e);
     }
 }
@@ -812,11 +816,13 @@ static int check_common(const orc_grid* g, int32_t n_tx, const double* tx, doubl
 
 int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
              double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
-             int32_t max_iter, int32_t fan_rays, double* theta_io, double* tof, double* hit_xy,
-             int32_t* status, int32_t* iters, int32_t nthreads) {
+             int32_t max_iter, int32_t fan_rays, double fan_ds, double* theta_io, double* tof,
+             double* hit_xy, int32_t* status, int32_t* iters, int32_t nthreads) {
     int rc = check_common(g, n_tx, tx, R, ds, n_pairs, pairs);
     if (rc) return rc;
     if (!theta_io || !(tol > 0) || fan_rays == 1 || fan_rays < 0) return ORC_EINVAL;
+    if (fan_ds == 0.0) fan_ds = ds;
+    if (!(fan_ds > 0) || !isfinite(fan_ds) || (fan_rays > 0 && !ring_ok(g, R, fan_ds))) return ORC_EINVAL;
     Field F;
     rc = field_make(&F, g, c_mps);
     if (rc) return rc;
@@ -831,7 +837,7 @@ int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double*
         }
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads_of(nthreads))
         for (int32_t t = 0; t < n_tx; ++t)
-            if (need[t]) fan_for_emitter(&F, R, tx + 2 * t, ds, fan_rays, fan + (size_t)t * fan_rays);
+            if (need[t]) fan_for_emitter(&F, R, tx + 2 * t, ds, fan_ds, fan_rays, fan + (size_t)t * fan_rays);
         free(need);
     }
     int bad = 0;

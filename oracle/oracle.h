@@ -67,11 +67,12 @@ int orc_trace(const orc_grid* g, const double* c_mps, double R, double xe, doubl
  * emitter-major. theta_io: NaN = cold start, else warm start; on return the
  * linked angle. Cold starts use the straight line to the receiver when
  * fan_rays == 0, else a fan of fan_rays (>= 2) rays per emitter predicts the
- * first angle and a bracket. Outputs may be NULL. */
+ * first angle and a bracket; the fan's rays are traced at step fan_ds (0 = ds;
+ * their launch angles follow ds). Outputs may be NULL. */
 int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
              double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
-             int32_t max_iter, int32_t fan_rays, double* theta_io, double* tof, double* hit_xy,
-             int32_t* status, int32_t* iters, int32_t nthreads);
+             int32_t max_iter, int32_t fan_rays, double fan_ds, double* theta_io, double* tof,
+             double* hit_xy, int32_t* status, int32_t* iters, int32_t nthreads);
 
 /* Travel time (and hit) of every pair at the given angles, no linking. */
 int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,

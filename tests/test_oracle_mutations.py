@@ -50,6 +50,14 @@ MUTANTS = {
                                       "if (b != a && b != n - 1) l *= (0.0 - m[b]) / (m[a] - m[b]);"),
     "fan_second_angle_without_trace": ("const double m5[5] = {cur.m, m4[0], m4[1], m4[2], m4[3]};",
                                        "const double m5[5] = {prev.m, m4[0], m4[1], m4[2], m4[3]};"),
+    "fan_margin_from_fan_step": ("    double margin = ds / R;\n    if (margin < 1e-9) margin = 1e-9;\n"
+                                 "    const double a_min = th_lo + margin, a_max = th_hi - margin;\n"
+                                 "    const double step = (a_max - a_min) / (K - 1);\n    for (int k = 0; k < K; ++k) {",
+                                 "    double margin = fan_ds / R;\n    if (margin < 1e-9) margin = 1e-9;\n"
+                                 "    const double a_min = th_lo + margin, a_max = th_hi - margin;\n"
+                                 "    const double step = (a_max - a_min) / (K - 1);\n    for (int k = 0; k < K; ++k) {"),
+    "fan_traced_at_link_step": ("fan_theta(a_min, step, k), fan_ds, NULL, NULL, 0, &tr);",
+                                "fan_theta(a_min, step, k), ds, NULL, NULL, 0, &tr);"),
 }
 
 # fast pins first; a mutant is killed by the first pin that fails
@@ -67,6 +75,7 @@ PINS = [
     pins.test_fisheye_ring_closed_form_converges_h2,
     pins.test_adjoint_matches_central_differences,
     pins.test_fan_start_prediction_accuracy,
+    pins.test_fan_step_changes_only_the_predictions,
 ]
 
 

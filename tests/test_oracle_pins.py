@@ -497,3 +497,29 @@ def test_fan_start_prediction_accuracy(orc):
     assert (r64["iters"] >= 3).mean() <= 0.01, np.bincount(r64["iters"])
     r0 = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=0)
     np.testing.assert_allclose(r["tof"], r0["tof"], rtol=1e-8)
+
+
+def test_fan_step_changes_only_the_predictions(orc):
+    """The fan may be traced at its own step (fan_ds): fan_ds = ds is the
+    default exactly; a coarse fan (h/2 = 5 ds) links the same rays as the
+    straight-line start and keeps the predictions high order (>= 85 % of the
+    pairs in one trace with 128 rays); in a homogeneous medium (straight rays,
+    exact for any step) every pair still links in one trace from a fan traced
+    at 10 ds, which holds only while the fan's launch angles follow ds, the
+    step the predictions assume."""
+    w = P.cfg_small()
+    a = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=128)
+    b = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=128, fan_ds=w.ds)
+    for k in ("theta", "tof", "iters"):
+        np.testing.assert_array_equal(a[k], b[k])
+    c = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=128, fan_ds=0.5 * w.grid.h)
+    assert (c["status"] == 0).all()
+    r0 = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=0)
+    np.testing.assert_allclose(c["tof"], r0["tof"], rtol=1e-8)
+    assert (c["iters"] == 1).mean() >= 0.85, np.bincount(c["iters"])
+    assert not np.array_equal(c["theta"], a["theta"])   # the coarse fan is traced: other first angles
+    g, tx, R = _small_ring(32)
+    h = orc.link(g, P.homogeneous(g), tx, R, 0.05, fan_rays=64, fan_ds=0.5)
+    assert (h["iters"] == 1).all()
+    with pytest.raises(Exception):
+        orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, fan_rays=64, fan_ds=-1.0)
