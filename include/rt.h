@@ -39,7 +39,8 @@
 extern "C" {
 #endif
 
-#define RT_ABI_VERSION 2   /* 2: rt_options.interpolator, rt_bspline_coef, rtborn_*_abs */
+#define RT_ABI_VERSION 3   /* 2: rt_options.interpolator, rt_bspline_coef, rtborn_*_abs;
+                              3: rt_options.fan_ds_mm */
 
 enum rt_code {
     RT_OK = 0,
@@ -119,6 +120,14 @@ typedef struct {
                             rt_tof_forward, rt_tof_adjoint, rt_path_matrix and
                             rtborn_maps (rt_batch_run and rt_tof_forward_noalloc
                             require RT_BILINEAR) */
+    double fan_ds_mm;      /* step of the fan start's rays (rt_link, rt_batch_run),
+                            0 = ds_mm. The fan only predicts first angles and
+                            brackets: its launch angles follow ds_mm and every
+                            linking trace uses ds_mm, so a coarser fan (e.g. h/2)
+                            links the same rays in about as many traces for a
+                            fraction of the fan's cost. With fan_rays >= 2 the
+                            ring plus max(ds_mm, fan_ds_mm) and one cell must lie
+                            inside the grid. */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
@@ -282,8 +291,9 @@ typedef struct {
  * (summed over instances) are read with rt_status_counts. The call sizes the
  * context's batch workspace on first use: make one call outside stream
  * capture, after which the same batch (sizes unchanged) can be captured into
- * a CUDA graph and replayed (the descriptor copy reads a pinned staging buffer
- * that the call fills and that later calls overwrite).
+ * a CUDA graph and replayed (the instance descriptors travel as a kernel
+ * parameter, so a captured launch keeps the descriptors of the call that was
+ * captured).
  */
 int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst, const rt_options* opt, void* stream);
 
@@ -304,7 +314,12 @@ int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst, const rt_
  * device current (make that first call before any stream capture). All calls
  * share the one array, which keeps the last call's contents: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. Arguments and outputs are as for rt_tof_forward;
+ * serialised by the caller. The first calls on one device may come from
+ * several host threads at once. `stream` (NULL = the legacy default stream)
+ * must belong to the current device; a stream of another device returns
+ * RT_EINVAL. Arguments and outputs are as for rt_tof_forward, except that only
+ * opt->interpolator = RT_BILINEAR is served (RT_BSPLINE returns RT_EINVAL:
+ * its packed field and coefficient workspace do not fit the fixed array) and
  * opt->fan_rays is ignored. Returns RT_OK, RT_EINVAL (bad argument),
  * RT_ENOMEM (grid too large) or RT_ECUDA; there is no error message.
  */

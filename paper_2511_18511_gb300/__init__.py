@@ -113,7 +113,7 @@ DEFAULT_FAN = 256
 
 
 def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, block_threads=0,
-          step_unroll=0, blocks_per_sm=0, integrator="rk4", interpolator="bilinear") -> _L.RtOptions:
+          step_unroll=0, blocks_per_sm=0, integrator="rk4", interpolator="bilinear", fan_ds=0.0) -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
     if integrator not in INTEGRATORS:
@@ -122,17 +122,19 @@ def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, bl
         raise ValueError(f"interpolator must be one of {sorted(INTERPOLATORS)}")
     return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays),
                         int(block_threads), int(step_unroll), int(blocks_per_sm), INTEGRATORS[integrator],
-                        INTERPOLATORS[interpolator])
+                        INTERPOLATORS[interpolator], float(fan_ds))
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
             theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
             ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
-            fan_rays: int = DEFAULT_FAN, integrator: str = "rk4", interpolator: str = "bilinear") -> dict:
+            fan_rays: int = DEFAULT_FAN, integrator: str = "rk4", interpolator: str = "bilinear",
+            fan_ds: float = 0.0) -> dict:
     """Link every pair (shooting method, paper Sec. 3.4) and return the linked
     angles, travel times (us), interceptions (mm), per-pair status and traces.
     Cold starts (theta0 None / NaN) use a fan of fan_rays rays per emitter, or
-    the straight line to the receiver with fan_rays = 0. integrator: "rk4" or
+    the straight line to the receiver with fan_rays = 0; the fan's rays are
+    traced at step fan_ds (0 = ds), their launch angles follow ds. integrator: "rk4" or
     "heun" (the paper's default stepper); interpolator: "bilinear" or "bspline"
     (the interpolating cubic B-spline, Sec. 3.3.1)."""
     ctx = ctx or default_context(prob.c.device.index)
@@ -149,7 +151,7 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     else:
         out["theta"].copy_(theta0)
     ps = prob.struct(c)
-    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator, interpolator=interpolator)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator, interpolator=interpolator, fan_ds=fan_ds)
     _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                     _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
     return out
@@ -318,7 +320,7 @@ class BatchInstance:
 
 
 def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
-                 fan_rays: int = DEFAULT_FAN, block_threads: int = 0, step_unroll: int = 0,
+                 fan_rays: int = DEFAULT_FAN, block_threads: int = 0, step_unroll: int = 0, fan_ds: float = 0.0,
                  blocks_per_sm: int = 0, ctx: Optional[Context] = None, stream=None,
                  reset_angles: bool = True, integrator: str = "rk4"):
     """Link (and, where tof_ref is set, adjoint-scatter) every pair of every
@@ -328,7 +330,8 @@ def rt_batch_run(instances, ds: float, tol: float = 1e-4, max_iter: int = 30, pr
         for b in instances:
             b.theta.fill_(float("nan"))
     arr = (_L.RtInstance * len(instances))(*[b.struct() for b in instances])
-    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll, blocks_per_sm, integrator)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, block_threads, step_unroll, blocks_per_sm, integrator,
+              fan_ds=fan_ds)
     _L.check(ctx.h, ctx.lib.rt_batch_run(ctx.h, len(instances), arr, C.byref(o), _stream(stream)))
     return instances
 

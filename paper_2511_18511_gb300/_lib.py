@@ -25,7 +25,7 @@ EXPORTED = [
     "rtborn_adjoint_abs", "rt_peak_fma", "rt_peak_gather", "rt_peak_read",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_TF32X3 = 0, 1
-ABI_VERSION = 2   # layout of RtOptions below
+ABI_VERSION = 3   # layout of RtOptions below
 
 
 class RtGrid(C.Structure):
@@ -37,7 +37,7 @@ class RtOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("ds_mm", C.c_double),
                 ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("block_threads", C.c_int32),
                 ("step_unroll", C.c_int32), ("blocks_per_sm", C.c_int32), ("integrator", C.c_int32),
-                ("interpolator", C.c_int32)]
+                ("interpolator", C.c_int32), ("fan_ds_mm", C.c_double)]
 
 
 class RtProblem(C.Structure):

@@ -1,5 +1,6 @@
 // rt_api.cu — the C ABI declared in include/rt.h: context, argument checks,
 // workspace and kernel launches. No exception crosses the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -126,7 +127,10 @@ int make_geom(rt_ctx* ctx, const rt_problem* p, const rt_options* o, Geom* G) {
         return fail(ctx, RT_EINVAL, "pairs == NULL requires n_pairs == n_tx*(n_tx-1)");
     const double R = p->ring_radius_mm;
     if (!(R > 0) || !std::isfinite(R)) return fail(ctx, RT_EINVAL, "ring radius must be > 0");
-    const double need = R + o->ds_mm + g.h_mm;
+    if (!(o->fan_ds_mm >= 0.0) || !std::isfinite(o->fan_ds_mm))
+        return fail(ctx, RT_EINVAL, "fan_ds_mm must be 0 (= ds_mm) or > 0");
+    // the ring plus one step (of the march or, for the fan, of the fan) and one cell
+    const double need = R + std::max(o->ds_mm, o->fan_rays >= 2 ? o->fan_ds_mm : 0.0) + g.h_mm;
     const double xl = g.x0_mm, xh = g.x0_mm + (g.nx - 1) * g.h_mm;
     const double yl = g.y0_mm, yh = g.y0_mm + (g.ny - 1) * g.h_mm;
     if (!(-need >= xl && need <= xh && -need >= yl && need <= yh))
@@ -211,8 +215,6 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (ctx->fan_need) cudaFree(ctx->fan_need);
     if (ctx->txphi) cudaFree(ctx->txphi);
     if (ctx->batch_ws) cudaFree(ctx->batch_ws);
-    if (ctx->batch_desc) cudaFree(ctx->batch_desc);
-    if (ctx->batch_desc_host) cudaFreeHost(ctx->batch_desc_host);
     for (void* p : {ctx->born_field, ctx->born_bsf, ctx->born_keys, (void*)ctx->born_idx, ctx->born_E, ctx->born_W, ctx->born_aux,
                     ctx->born_acc, ctx->born_err})
         if (p) cudaFree(p);
@@ -263,7 +265,8 @@ int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* 
     cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
     e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
-                        status, iters, ctx->counters, ctx->queue, opt->fan_rays, ctx->fan, ctx->fan_need, s);
+                        status, iters, ctx->counters, ctx->queue, opt->fan_rays, opt->fan_ds_mm, ctx->fan,
+                        ctx->fan_need, s);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
 }
 

@@ -5,6 +5,7 @@
 // forward and the adjoint share one launch and one tail.
 #include <algorithm>
 #include <climits>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -247,17 +248,22 @@ template <typename T, int BLOCK, int UNROLL, int MINB>
 cudaError_t launch_batch_kernel(const rt::BatchParams& D, long long total, double tol, int max_iter,
                                 int fan_rays, unsigned long long* counters, unsigned long long* queue,
                                 cudaStream_t s) {
-    static int blocks = 0;
+    static std::atomic<int> cache[64];   // resident blocks of this variant, per device
     const size_t smem = sizeof(rt::LinkState) * BLOCK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int blocks = cache[dev].load(std::memory_order_relaxed);
     if (!blocks) {
-        cudaError_t e = cudaFuncSetAttribute(rt::k_batch<T, BLOCK, UNROLL, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(rt::k_batch<T, BLOCK, UNROLL, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
+        int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt::k_batch<T, BLOCK, UNROLL, MINB>, BLOCK, smem);
         blocks = sms * (per_sm > 0 ? per_sm : 1);
+        cache[dev].store(blocks, std::memory_order_relaxed);
     }
     const long long need = (total + BLOCK - 1) / BLOCK;
     const int nb = (int)(need < blocks ? need : blocks);
@@ -364,7 +370,7 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
         if (e != cudaSuccess) break;
         if (opt->fan_rays >= 2 && I.prob.n_pairs > 0) {
             d.fan = reinterpret_cast<const double*>(ws + fan_off[slot]);
-            e = rt::launch_fan(d.G, d.field, opt->precision, opt->fan_rays, I.theta_io,
+            e = rt::launch_fan(d.G, opt->fan_ds_mm, d.field, opt->precision, opt->fan_rays, I.theta_io,
                                reinterpret_cast<double*>(ws + fan_off[slot]), reinterpret_cast<int*>(ws + need_off[slot]),
                                ctx->counters, s);
             if (e != cudaSuccess) break;
@@ -381,7 +387,7 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
             e = cudaMemsetAsync(I.g_c, 0, sizeof(double) * (size_t)I.prob.grid.nx * I.prob.grid.ny, s);
     }
     if (e != cudaSuccess) return rt::set_error(ctx, RT_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
-    static rt::BatchParams params;   // host staging of the kernel parameter (copied at launch)
+    rt::BatchParams params{};   // the kernel parameter, copied at launch
     params.n_inst = n_inst;
     std::memcpy(params.d, D.data(), sizeof(InstDesc) * (size_t)n_inst);
     e = cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s);

@@ -43,6 +43,7 @@
 // (k_born_efield in rt_born.cu) and runs the hand-written complex GEMM
 // k_cgemm below.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -684,14 +685,14 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const float2
 }
 
 int sm_count(int device) {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64];
     if (device < 0 || device >= 64) return 152;
-    if (!cache[device]) {
-        int v = 0;
+    int v = cache[device].load(std::memory_order_relaxed);
+    if (!v) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 152;
-        cache[device] = v;
+        cache[device].store(v, std::memory_order_relaxed);
     }
-    return cache[device];
+    return v;
 }
 
 }  // namespace

@@ -23,12 +23,9 @@ struct rt_ctx {
     size_t fan_cap = 0, need_cap = 0;
     double* txphi = nullptr;        // [n_tx] polar angles of the transducers (NaN = off the ring)
     size_t txphi_cap = 0;
-    // batch workspace (rt_batch_run): packed fields, fans, flags; descriptors
+    // batch workspace (rt_batch_run): packed fields, fans, flags
     void* batch_ws = nullptr;
     size_t batch_ws_bytes = 0;
-    void* batch_desc = nullptr;       // device copy of the instance descriptors
-    void* batch_desc_host = nullptr;  // pinned staging of the descriptors
-    size_t batch_desc_bytes = 0;
     void* scan_tmp = nullptr;       // prefix-sum workspace (path matrix)
     size_t scan_bytes = 0;
     cudaStream_t last_stream = nullptr;
@@ -72,12 +69,13 @@ bool stream_capturing(cudaStream_t s);
 // the field layout (and kernel variant) follows G.interp.
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
                         cudaStream_t s);
+// fan_ds: the fan's tracing step (0 = G.ds); its launch angles follow G.ds.
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
-                        unsigned long long* counters, int* queue, int fan_rays, double* fan,
+                        unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,
                         int* fan_need, cudaStream_t s);
-cudaError_t launch_fan(const Geom& G, const void* field, int prec, int fan_rays, const double* theta, double* fan,
-                       int* fan_need, unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_fan(const Geom& G, double fan_ds, const void* field, int prec, int fan_rays, const double* theta,
+                       double* fan, int* fan_need, unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double* theta, double* tof,
                        double* hit, cudaStream_t s);
 cudaError_t launch_adjoint(const Geom& G, const void* field, int prec, const double* theta,

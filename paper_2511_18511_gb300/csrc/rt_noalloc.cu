@@ -8,6 +8,7 @@
 // hands it only input and output buffers. For them this file keeps the
 // packed field in a fixed, file-scope device array instead. Every GPU that
 // loads the library holds that array until the process exits.
+#include <atomic>
 #include <cstdio>
 
 #include "rt_internal.h"
@@ -23,17 +24,20 @@ constexpr size_t kFlagBytes = 256;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes + kFlagBytes];
 
 constexpr int kMaxDevices = 64;
-// Device address of g_scratch per device, found once with that device current.
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+// Device address of g_scratch per device, found with that device current.
+// Host threads that make their first call on a device at the same time may
+// both look it up; they find the same address, and the atomic store makes
+// that benign.
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
 
 int scratch_on(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) return RT_EINVAL;
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
+    void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return RT_ECUDA;
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    *out = static_cast<unsigned char*>(p);
     return RT_OK;
 }
 
@@ -54,12 +58,18 @@ extern "C" int rt_tof_forward_noalloc(const rt_problem* prob, const rt_options* 
     if (need > kScratchBytes) return RT_ENOMEM;   // grid larger than the static scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RT_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s) {
+        // the scratch address is the current device's: the stream must be on it
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return RT_ECUDA;
+        if (sdev != dev) return RT_EINVAL;
+    }
     unsigned char* base = nullptr;
     rc = scratch_on(dev, &base);
     if (rc) return rc;
     void* field = base;
     int* flag = reinterpret_cast<int*>(base + kScratchBytes);
-    cudaStream_t s = (cudaStream_t)stream;
     // launch_pack clears the flag before packing
     if (rt::launch_pack(prob->grid, prob->c_mps, field, flag, opt->precision, s) != cudaSuccess) return RT_ECUDA;
     G.bad_field = flag;

@@ -1,6 +1,8 @@
 // rt_ray.cu — kernels of the ToF path: field packing, shooting-method linking
 // with the fused travel time, travel time at fixed angles, the adjoint scatter
 // and the explicit system-matrix rows.
+#include <atomic>
+#include <cmath>
 #include <cfloat>
 #include <climits>
 #include <cstdint>
@@ -145,9 +147,11 @@ __global__ void k_fan_mark(Geom G, const double* __restrict__ theta, int* need) 
 // same relative angle from consecutive emitters: nearly parallel rays of nearly
 // equal length through nearby cells, and the launch ends with the short rays
 // near the tangents.
+// G carries the fan's tracing step; margin (ds/R of the linking step) fixes
+// the fan's launch angles, which the linking predictions assume.
 template <typename T, int I>
 __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I>::Field* __restrict__ F, int K,
-                                                const int* __restrict__ need, double* fan,
+                                                double margin, const int* __restrict__ need, double* fan,
                                                 unsigned long long* counters) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     const int rank = id / G.n_tx, e = id - rank * G.n_tx;
@@ -157,7 +161,6 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I
     if (id < G.n_tx * K && need[e] && !*G.bad_field) {
         const double xe = G.tx[2 * e], ye = G.tx[2 * e + 1];
         const double phi_e = atan2(ye, xe);
-        const double margin = fmax(G.ds / G.R, 1e-9);
         const double a_min = phi_e + 0.5 * kPi + margin, a_max = phi_e + 1.5 * kPi - margin;
         const double step = (a_max - a_min) / (K - 1);
         auto C = make_cell<T, I>(G, F);
@@ -267,41 +270,58 @@ __global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, 
     }
 }
 
-// Blocks of a persistent launch: resident blocks per SM x SMs (cached per slot).
+// Blocks of a persistent launch on the current device: resident blocks per
+// SM x SMs (cached per device and kernel slot).
 template <typename K>
 static int persistent_blocks(K kernel, int slot) {
-    static int cache[16] = {0};
-    if (!cache[slot]) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
+    static std::atomic<int> cache[64][16];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int v = cache[dev][slot].load(std::memory_order_relaxed);
+    if (!v) {
+        int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLinkBlock, 0);
-        cache[slot] = sms * (per_sm > 0 ? per_sm : 1);
+        v = sms * (per_sm > 0 ? per_sm : 1);
+        cache[dev][slot].store(v, std::memory_order_relaxed);
     }
-    return cache[slot];
+    return v;
 }
 
 template <typename T, int I>
-static void fan_impl(const Geom& G, const void* field, int fan_rays, double* fan, const int* fan_need,
-                     unsigned long long* counters, cudaStream_t s) {
+static void fan_impl(const Geom& G, const void* field, int fan_rays, double margin, double* fan,
+                     const int* fan_need, unsigned long long* counters, cudaStream_t s) {
     const int nf = G.n_tx * fan_rays;
-    k_fan<T, I><<<grid_for(nf), kBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, fan_rays, fan_need, fan,
-                                                counters);
+    k_fan<T, I><<<grid_for(nf), kBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, fan_rays, margin,
+                                                fan_need, fan, counters);
 }
 
-cudaError_t launch_fan(const Geom& G, const void* field, int prec, int fan_rays, const double* theta, double* fan,
-                       int* fan_need, unsigned long long* counters, cudaStream_t s) {
+Geom with_step(const Geom& G, double ds) {
+    Geom F = G;
+    F.ds = ds;
+    F.dsf = (float)ds;
+    F.Hf = (float)(ds / G.h);
+    F.max_steps = (long long)std::ceil(8.0 * G.R / ds);
+    F.max_steps_i = (int)F.max_steps;
+    return F;
+}
+
+cudaError_t launch_fan(const Geom& G, double fan_ds, const void* field, int prec, int fan_rays, const double* theta,
+                       double* fan, int* fan_need, unsigned long long* counters, cudaStream_t s) {
     if (G.n_pairs == 0 || fan_rays < 2) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(fan_need, 0, sizeof(int) * (size_t)G.n_tx, s);
     if (e != cudaSuccess) return e;
     k_fan_mark<<<grid_for(G.n_pairs), kBlock, 0, s>>>(G, theta, fan_need);
+    const Geom F = fan_ds > 0.0 ? with_step(G, fan_ds) : G;
+    const double margin = fmax(G.ds / G.R, 1e-9);
     const bool bs = G.interp == RT_BSPLINE;
     if (prec == RT_FP64) {
-        if (bs) fan_impl<double, RT_BSPLINE>(G, field, fan_rays, fan, fan_need, counters, s);
-        else fan_impl<double, RT_BILINEAR>(G, field, fan_rays, fan, fan_need, counters, s);
+        if (bs) fan_impl<double, RT_BSPLINE>(F, field, fan_rays, margin, fan, fan_need, counters, s);
+        else fan_impl<double, RT_BILINEAR>(F, field, fan_rays, margin, fan, fan_need, counters, s);
     } else {
-        if (bs) fan_impl<float, RT_BSPLINE>(G, field, fan_rays, fan, fan_need, counters, s);
-        else fan_impl<float, RT_BILINEAR>(G, field, fan_rays, fan, fan_need, counters, s);
+        if (bs) fan_impl<float, RT_BSPLINE>(F, field, fan_rays, margin, fan, fan_need, counters, s);
+        else fan_impl<float, RT_BILINEAR>(F, field, fan_rays, margin, fan, fan_need, counters, s);
     }
     return cudaGetLastError();
 }
@@ -317,13 +337,13 @@ static void link_impl(const Geom& G, const void* field, double tol, int max_iter
 
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
-                        unsigned long long* counters, int* queue, int fan_rays, double* fan,
+                        unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,
                         int* fan_need, cudaStream_t s) {
     if (G.n_pairs == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (fan_rays >= 2) {
-        e = launch_fan(G, field, prec, fan_rays, theta, fan, fan_need, counters, s);
+        e = launch_fan(G, fan_ds, field, prec, fan_rays, theta, fan, fan_need, counters, s);
         if (e != cudaSuccess) return e;
     }
     const bool bs = G.interp == RT_BSPLINE;

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_without_gpu(lib):
     from paper_2511_18511_gb300 import _lib
-    assert lib.rt_version() == _lib.ABI_VERSION == 2
+    assert lib.rt_version() == _lib.ABI_VERSION == 3
 
 
 def test_option_checks_without_gpu(lib):
@@ -63,3 +63,19 @@ def test_null_arguments_are_rejected_without_gpu(lib):
 def test_library_built_for_sm103a_only():
     from paper_2511_18511_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_noalloc_object_references_no_allocator(lib):
+    """The allocation-free entry point's object file calls no CUDA allocator
+    (its undefined symbols, read with nm, name no cudaMalloc* or cudaFree*)."""
+    import shutil
+    import subprocess
+    from paper_2511_18511_gb300 import build
+    nm = shutil.which("nm")
+    if not nm:
+        pytest.skip("nm not available")
+    obj = os.path.join(build.OUT, "rt_noalloc.o")
+    assert os.path.exists(obj)
+    out = subprocess.run([nm, "-u", "-C", obj], capture_output=True, text=True, check=True).stdout
+    bad = [ln for ln in out.splitlines() if re.search(r"\bcuda(Malloc|Free)\w*|\bcuMem(Alloc|Free)\w*", ln)]
+    assert not bad, bad

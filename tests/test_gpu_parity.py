@@ -97,6 +97,33 @@ def test_link_matches_oracle_small(small, small_straight, rt, P, prec, fan):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_link_with_coarse_fan_matches_oracle(rt, orc, P, prec):
+    """The fan start traced at its own step (fan_ds = h/2 = 5 ds, launch
+    angles still following ds) against the oracle with the same fan step:
+    every pair links, travel times and endpoints within the linking bars, and
+    in FP64 the same number of traces per pair as the oracle."""
+    w = P.cfg_small()
+    fds = 0.5 * w.grid.h
+    ref = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, fan_rays=FAN, fan_ds=fds)
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
+    r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, fan_rays=FAN, fan_ds=fds)
+    ok, counts = rt.rt_status_counts()
+    assert ok and counts[0] == prob.n_pairs
+    rel = np.abs(_np(r["tof"]) / ref["tof"] - 1)
+    assert rel.max() <= TOF_RTOL, rel.max()
+    pairs = P.all_pairs(w.n_tx)
+    assert np.linalg.norm(_np(r["hit"]) - w.tx[pairs[:, 1]], axis=1).max() <= w.tol
+    it, it_ref = _np(r["iters"]), ref["iters"]
+    print(f"[{prec} fan_ds={fds}] linked: max ToF rel err {rel.max():.3e}, traces/pair {it.mean():.4f} "
+          f"(oracle {it_ref.mean():.4f}; fan at ds: oracle "
+          f"{orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, fan_rays=FAN)['iters'].mean():.4f})")
+    if prec == "fp64":
+        np.testing.assert_array_equal(it, it_ref)
+    else:
+        assert abs(it.mean() - it_ref.mean()) <= 0.01
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_tof_at_oracle_angles(small, rt, prec):
     """Travel time at the oracle's linked angles (same rays on both sides)."""
     w, prob, ref = small

@@ -36,6 +36,7 @@ def test_noalloc_matches_regular_call_twice(rt, orc, prec):
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
     theta = torch.as_tensor(ref["theta"], device="cuda")
     T_reg, hit_reg = rt.rt_tof_forward(prob, theta, w.ds, precision=prec)
+    T_orc, _ = orc.tof(w.grid, w.c, w.tx, w.ring_radius, w.ds, ref["theta"])
     ps = prob.struct()
     o = rt._opts(w.ds, precision=prec)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -49,6 +50,9 @@ def test_noalloc_matches_regular_call_twice(rt, orc, prec):
         rel = (T / T_reg - 1).abs().max().item()
         assert rel <= (1e-12 if prec == "fp64" else 2e-6), rel
         assert (hit - hit_reg).abs().max().item() <= (1e-9 if prec == "fp64" else 1e-4)
+        # and, independently of the regular call, against the oracle at the same angles
+        rel_o = np.abs(T.cpu().numpy() / T_orc - 1).max()
+        assert rel_o <= (1e-12 if prec == "fp64" else 2e-6), rel_o
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(rt):
@@ -59,7 +63,10 @@ def test_noalloc_rejects_grids_beyond_its_scratch(rt):
     ps = prob.struct()
     o = rt._opts(0.02, precision="fp32c")
     theta = torch.zeros(prob.n_pairs, dtype=torch.float64, device="cuda")
-    T = torch.empty_like(theta)
+    T = torch.full_like(theta, float("nan"))
+    torch.cuda.synchronize()
     rc = L.rt_tof_forward_noalloc(C.byref(ps), C.byref(o), C.c_void_p(theta.data_ptr()),
                                   C.c_void_p(T.data_ptr()), None, None)
     assert rc == rt._L.RT_ENOMEM
+    torch.cuda.synchronize()
+    assert torch.isnan(T).all()          # nothing was enqueued: the output is untouched
