@@ -81,10 +81,11 @@ def parse():
                          "the first N_EMIT emitters of the workload, then exit")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"],
                     help="precision of the --profile case")
-    ap.add_argument("--workload", default="breast", choices=["breast", "batch", "born"],
+    ap.add_argument("--workload", default="breast", choices=["breast", "batch", "born", "small", "fisheye"],
                     help="breast: the headline single problem; batch: 32 uneven instances in one persistent "
                          "launch replayed from a CUDA graph; born: ray-Born maps + apply + adjoint "
-                         "(1024^2, 512-ring, 8 frequencies)")
+                         "(1024^2, 512-ring, 8 frequencies); small: 128^2 / 64-ring; fisheye: the Maxwell "
+                         "fish-eye lens 512^2 / 256-ring")
     return ap.parse_args()
 
 
@@ -607,6 +608,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tof_config(args):
+    """The ToF step (rt_link + rt_tof_adjoint, cold fan start) on one of the smaller
+    configurations as its own line: the 128^2 / 64-ring Gaussian-inclusion
+    medium (4,032 pairs) or the fish-eye lens on 512^2 with a 256-ring (65,280
+    pairs); FP32-compensated and FP64 on the GPU, the oracle on all host cores
+    and on one thread (bounded samples of the same step)."""
+    import torch
+    import oracle
+    import paper_2511_18511_gb300 as rt
+    from paper_2511_18511_gb300 import phantoms as P
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    w = P.cfg_small() if args.workload == "small" else P.cfg_fisheye()
+    fan, fan_ds = 256, 0.5 * w.grid.h
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
+    t_meas = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp64", c=prob.c * 1.002, fan_rays=fan)["tof"].clone()
+    s = torch.cuda.current_stream()
+
+    def one(prec, out, g):
+        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, fan_rays=fan, fan_ds=fan_ds, out=out)
+        g = rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, out=g)
+        return r, g
+
+    def timed(prec, steps, warmup):
+        out, g = None, None
+        for _ in range(warmup):
+            out, g = one(prec, out, g)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            one(prec, out, g)
+            b.record(s)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        ok, counts = rt.rt_status_counts()
+        return float(np.mean([a.elapsed_time(b) for a, b in ts])), ok, counts, out
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms, ok, counts, out = timed("fp32c", args.steps, args.warmup)
+    clk = clocks.stop()
+    ms64, ok64, _, _ = timed("fp64", 1, 1)
+    n = prob.n_pairs
+    # the oracle on the same step: a bounded sample of emitters (all cores, then one thread)
+    oracle.build()
+    pairs = P.all_pairs(w.n_tx)
+
+    def cpu(n_emit, nthreads):
+        emit = np.arange(0, w.n_tx, max(1, w.n_tx // n_emit))[:n_emit]
+        sub = pairs[np.isin(pairs[:, 0], emit)]
+        tm = t_meas.cpu().numpy()[np.isin(pairs[:, 0], emit)]
+        t0 = time.perf_counter()
+        r = oracle.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=w.tol, pairs=sub, fan_rays=fan, fan_ds=fan_ds,
+                        nthreads=nthreads)
+        oracle.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, r["theta"], r["tof"] - tm, pairs=sub,
+                       nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        cores = oracle.num_threads() if nthreads == 0 else nthreads
+        return {"value": len(sub) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{len(sub)} pairs ({len(emit)} emitters x {w.n_tx - 1} receivers), cold fan start, "
+                          f"link + adjoint, {dt:.2f} s on {cores} thread(s)"}
+
+    n_all = 16 if w.n_tx >= 64 else w.n_tx
+    cb = cpu(n_all, 0)
+    cb["one_thread"] = cpu(2, 1)
+    line = {"metric": f"linked rays/s (ToF fwd+adjoint, {w.name})", "value": n / (ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": f"{w.grid.nx}x{w.grid.ny}", "h_mm": w.grid.h, "ring": w.n_tx,
+                       "ring_radius_mm": w.ring_radius, "pairs": n, "ds_mm": w.ds, "tol_mm": w.tol,
+                       "start": f"cold: fan of {fan} rays per transducer at {fan_ds} mm",
+                       "step": "rt_link + rt_tof_adjoint (L2 misfit against times in c x 1.002)"},
+            "link": {"all_linked": ok, "status_counts": counts[:7],
+                     "mean_traces_per_pair": float(out["iters"].float().mean().item())},
+            "fp64_gpu": {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "all_linked": ok64,
+                         "speedup_fp32c_over_fp64": ms64 / ms},
+            "gpu_launches": 9 * args.steps, "clocks": clk, "peaks": peaks, "cpu_baseline": cb}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -617,6 +700,8 @@ def main():
         return run_batch(args)
     if args.workload == "born":
         return run_born(args)
+    if args.workload in ("small", "fisheye"):
+        return run_tof_config(args)
     import torch
     import paper_2511_18511_gb300 as rt
     from paper_2511_18511_gb300 import shard
@@ -656,8 +741,8 @@ def main():
                     iters=torch.empty(n, dtype=torch.int32, device=dev))
 
     def step(prec, out, g, ev=None, c=None, tm=None, **kw):
-        """rt_link (cold) + rt_tof_adjoint of the misfit; with N > 1 the
-        ShardedToF step: this rank's pairs, then one all-reduce of g."""
+        """rt_link (cold) + rt_tof_adjoint of the misfit, an event between them;
+        with N > 1 the ShardedToF step: this rank's pairs, then one all-reduce of g."""
         tm = t_meas if tm is None else tm
 
         def link(_pairs, cc):

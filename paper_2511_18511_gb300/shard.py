@@ -99,14 +99,20 @@ class ShardedToF:
     per-rank operators (the CUDA library's on GPUs, the oracle's in the CPU
     tests), so that both run this same step."""
 
-    def __init__(self, rank: int, world: int, n_tx: int, link, adjoint, allreduce=allreduce_sum):
+    def __init__(self, rank: int, world: int, n_tx: int, link=None, adjoint=None, allreduce=allreduce_sum,
+                 link_adjoint=None):
         self.rank, self.world, self.n_tx = rank, world, n_tx
         self.pairs = shard_pairs(rank, world, n_tx, longest_first=True)
         self.link, self.adjoint, self.allreduce = link, adjoint, allreduce
+        # optional fused operator link_adjoint(pairs, c, tof_meas) -> (theta, tof, g)
+        self.link_adjoint = link_adjoint
 
     def step(self, c, tof_meas):
         """tof_meas: measured times of this rank's pairs (in self.pairs order);
         returns (g summed over ranks, theta, tof) of the misfit 0.5 |T - T_meas|^2."""
-        theta, tof = self.link(self.pairs, c)
-        g = self.adjoint(self.pairs, c, theta, tof, tof_meas)
+        if self.link_adjoint is not None:
+            theta, tof, g = self.link_adjoint(self.pairs, c, tof_meas)
+        else:
+            theta, tof = self.link(self.pairs, c)
+            g = self.adjoint(self.pairs, c, theta, tof, tof_meas)
         return self.allreduce(g), theta, tof

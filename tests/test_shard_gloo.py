@@ -148,11 +148,18 @@ def _step_worker(rank, world, port, out_dir):
         return torch.from_numpy(oracle.adjoint(w.grid, c, w.tx, w.ring_radius, w.ds, theta, tof - tof_meas,
                                                pairs=pairs, nthreads=1).copy())
 
+    def link_adjoint(pairs, c, tof_meas):
+        theta, tof = link(pairs, c)
+        return theta, tof, adjoint(pairs, c, theta, tof, tof_meas)
+
     step = shard.ShardedToF(rank, world, w.n_tx, link, adjoint)
     _, t_meas = link(step.pairs, w.c * 1.005)
     g, _, _ = step.step(w.c, t_meas)
+    fused = shard.ShardedToF(rank, world, w.n_tx, link_adjoint=link_adjoint)
+    g2, _, _ = fused.step(w.c, t_meas)
     if rank == 0:
         np.save(os.path.join(out_dir, "step.npy"), g.numpy())
+        np.save(os.path.join(out_dir, "step_fused.npy"), g2.numpy())
     dist.destroy_process_group()
 
 
@@ -166,6 +173,7 @@ def test_sharded_tof_step_equals_unsharded(tmp_path, orc, world):
     mp.start_processes(_step_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
                        start_method="spawn")
     got = np.load(tmp_path / "step.npy")
+    np.testing.assert_array_equal(np.load(tmp_path / "step_fused.npy"), got)
     w = P.cfg_small(n_tx=16)
     meas = orc.link(w.grid, w.c * 1.005, w.tx, w.ring_radius, w.ds, fan_rays=64)
     r = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, fan_rays=64)
