@@ -731,6 +731,7 @@ def main():
     # "measured" travel times from the true medium (outside any timed region)
     meas = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp64", c=c_true, ctx=ctx)
     t_meas = meas["tof"].clone()
+    rows = rt.Rows.create(prob)       # recorded rows of the step's linked rays
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def buffers():
@@ -741,18 +742,28 @@ def main():
                     iters=torch.empty(n, dtype=torch.int32, device=dev))
 
     def step(prec, out, g, ev=None, c=None, tm=None, **kw):
-        """rt_link (cold) + rt_tof_adjoint of the misfit, an event between them;
-        with N > 1 the ShardedToF step: this rank's pairs, then one all-reduce of g."""
+        """Link (cold) + adjoint of the misfit, an event between them: in the
+        FP32-compensated bilinear form rt_link_rows + rt_tof_adjoint_rows (the
+        link records its rays' rows, the adjoint reads them), otherwise rt_link
+        + rt_tof_adjoint; with N > 1 the ShardedToF step: this rank's pairs,
+        then one all-reduce of g."""
         tm = t_meas if tm is None else tm
+        use_rows = prec == "fp32c" and not kw
 
         def link(_pairs, cc):
-            r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, c=cc, ctx=ctx, out=out, fan_rays=BREAST_FAN,
-                           fan_ds=FAN_DS, **kw)
+            if use_rows:
+                r = rt.rt_link_rows(prob, w.ds, rows, tol=w.tol, c=cc, ctx=ctx, out=out, fan_rays=BREAST_FAN,
+                                    fan_ds=FAN_DS)
+            else:
+                r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, c=cc, ctx=ctx, out=out, fan_rays=BREAST_FAN,
+                               fan_ds=FAN_DS, **kw)
             if ev:
                 ev[1].record(stream)
             return r["theta"], r["tof"]
 
         def adjoint(_pairs, cc, theta, tof, tof_meas):
+            if use_rows:
+                return rt.rt_tof_adjoint_rows(prob, rows, theta, tof, w.ds, tof_ref=tof_meas, c=cc, ctx=ctx, out=g)
             return rt.rt_tof_adjoint(prob, theta, tof, w.ds, tof_ref=tof_meas, precision=prec, c=cc, ctx=ctx,
                                      out=g, **kw)
 
@@ -848,21 +859,22 @@ def main():
                    "ring_radius_mm": w.ring_radius, "pairs": n_all, "ds_mm": w.ds, "tol_mm": w.tol,
                    "start": f"cold: fan of {BREAST_FAN} rays per transducer traced at {FAN_DS} mm",
                    "fan_rays": BREAST_FAN, "fan_ds_mm": FAN_DS,
-                   "step": "rt_link + rt_tof_adjoint (L2 misfit)" + (
+                   "step": "rt_link_rows + rt_tof_adjoint_rows (L2 misfit; the link records its rays' rows "
+                           "of the system matrix, the adjoint reads them)" + (
                        "; pairs split over ranks by emitter block (longest chords first), NCCL all-reduce of "
                        "the gradient inside the step" if world > 1 else ""),
                    "precision": "fp32c (FP32 march, compensated direction/sums, FP64 linking)",
                    "l2": "flushed between timed steps (256 MB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32, "unit": "TFLOP/s",
                      "frac": achieved / fp32, "traffic": traffic,
-                     "kernel": "rt_link call: k_fan<float> + k_link<float> (+ field pack)",
+                     "kernel": "rt_link_rows call: k_fan<float> + k_link<float, recording> (+ field pack)",
                      "flop_per_rk4_step": FLOP_PER_STEP, "rk4_steps_per_launch": steps_per_launch,
                      "peak_basis": "FP32 FMA rate measured at start-up on this GPU (rt_peak_fma)"},
         "link": {"mean_traces_per_pair": res["iters"], "all_linked": res["ok"],
                  "status_counts": res["counts"][:7], "link_ms": link_ms, "adjoint_ms": adjoint_ms},
         "e2e": {"value": n_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # per step: rt_link = k_pack, k_tx_phi, k_fan_mark, k_fan, k_link;
-        # rt_tof_adjoint = k_pack, k_tx_phi, k_adjoint, k_adjoint_finish
+        # per step: rt_link_rows = k_pack, k_tx_phi, k_fan_mark, k_fan, k_link;
+        # rt_tof_adjoint_rows = k_pack, k_tx_phi, k_adjoint_rows, k_adjoint_finish
         "gpu_launches": 9 * args.steps,
         "clocks": res["clocks"],
         "peaks": peaks,
@@ -872,7 +884,7 @@ def main():
         line["pairs_per_rank"] = n
     if world == 1:
         line.update(single_gpu_legs(args, peaks, rt, torch, prob, w, ctx, timed, res, link_ms, adjoint_ms,
-                                    ms_per_step, steps_per_launch, dev, stream, flush, t_meas, buffers))
+                                    ms_per_step, steps_per_launch, dev, stream, flush, t_meas, buffers, rows))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, n_emit=16)
         line["cpu_baseline"]["one_thread"] = cpu_baseline(w, n_emit=2, nthreads=1)
@@ -883,7 +895,7 @@ def main():
 
 
 def single_gpu_legs(args, peaks, rt, torch, prob, w, ctx, timed, res, link_ms, adjoint_ms, ms_per_step,
-                    steps_per_launch, dev, stream, flush, t_meas, buffers) -> dict:
+                    steps_per_launch, dev, stream, flush, t_meas, buffers, rows) -> dict:
     """Sub-objects of the 1-GPU line: the adjoint kernel's roofline, the
     L2-gather comparison, the plain FP64 form, the warm start, the cubic
     B-spline sampler, the batched workload and the ray-Born step."""
@@ -921,15 +933,38 @@ def single_gpu_legs(args, peaks, rt, torch, prob, w, ctx, timed, res, link_ms, a
                           "link_ms": float(np.mean(warm_link)),
                           "mean_traces_per_pair": float(out_w["iters"].float().mean().item()),
                           "start": "the previous step's linked angles"}
-    adj_ach = retrace_steps * FLOP_PER_STEP / (adjoint_ms / 1e3) / 1e12
+    # the adjoint from recorded rows reads every pair's runs (20 B each) and
+    # adds four FP64 atomics per run into the L2-resident gradient
+    runs = int(rows.len.clamp(min=0).sum().item())
+    adj_bytes = runs * 20 + n * (4 + 8 + 8)
+    adj_gbs = adj_bytes / (adjoint_ms / 1e3) / 1e9
+    hbm = peaks["hbm_gbs"]
     legs["roofline_adjoint"] = {
-        "bound": "alu", "achieved": adj_ach, "peak": fp32, "unit": "TFLOP/s", "frac": adj_ach / fp32,
-        "traffic": _traffic(os.path.join(ROOT, "profiles", "adjoint_traffic.json"),
-                            ("rt_trace.cuh", "rt_link.cuh", "rt_bspline.cuh", "rt_ray.cu")),
-        "kernel": "rt_tof_adjoint call: k_adjoint<float> (+ pack, finish)", "flop_per_rk4_step": FLOP_PER_STEP,
-        "rk4_steps_per_launch": retrace_steps,
-        "note": "retrace FLOPs only; the scatter's FP64 atomics (4 per cell run) are not counted",
-        "peak_basis": "FP32 FMA rate measured at start-up on this GPU (rt_peak_fma)"}
+        "bound": "hbm", "achieved": adj_gbs, "peak": hbm, "unit": "GB/s", "frac": adj_gbs / hbm,
+        "traffic": None, "kernel": "rt_tof_adjoint_rows call: k_adjoint_rows (+ pack, finish)",
+        "bytes_per_launch": adj_bytes, "runs": runs, "fp64_atomics_per_s": 4.0 * runs / (adjoint_ms / 1e3),
+        "note": "algorithmic bytes = the recorded runs (20 B each) + 20 B per pair; the 4 FP64 atomics per run "
+                "go to the L2-resident gradient",
+        "peak_basis": "measured HBM copy rate (MEASURED_PEAKS.json)"}
+    # the same adjoint by retracing every ray (rt_tof_adjoint), for comparison
+    g_r = torch.empty_like(prob.c)
+    ta = []
+    for k in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rt.rt_tof_adjoint(prob, res["out"]["theta"], res["out"]["tof"], w.ds, tof_ref=t_meas, precision="fp32c",
+                          ctx=ctx, out=g_r)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            ta.append(a.elapsed_time(b))
+    retrace_ms = float(np.mean(ta))
+    adj_ach = retrace_steps * FLOP_PER_STEP / (retrace_ms / 1e3) / 1e12
+    legs["adjoint_by_retrace"] = {
+        "ms": retrace_ms, "achieved_tflops": adj_ach, "frac_of_fp32": adj_ach / fp32,
+        "rk4_steps_per_launch": retrace_steps, "kernel": "rt_tof_adjoint: k_adjoint<float> retraces every ray",
+        "max_rel_diff_of_gradient": float(((g_r - res["g"]).abs().max() / g_r.abs().max()).item())}
     gath = steps_per_launch * GATHER_BYTES_PER_STEP / (link_ms / 1e3) / 1e9
     legs["l2_gather"] = {
         "bytes_per_rk4_step": GATHER_BYTES_PER_STEP, "achieved_gbs": gath, "peak_gbs": peaks["l2_gather_gbs"],

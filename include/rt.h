@@ -208,6 +208,64 @@ int rt_tof_adjoint(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt,
                    double* g_c, void* stream);
 
 /*
+ * Recorded rows of the system matrix (paper Sec. 3.1.1: each row holds the
+ * interpolation-weighted path lengths of a pair's ray; "because of its
+ * sparsity, it can be computed and stored explicitly"). rt_link_rows writes
+ * them while it links, from the very traces it links with, so that
+ * rt_tof_adjoint_rows applies the transpose without tracing the rays again.
+ *
+ * rt_run: one run of consecutive sample points of a ray inside one cell: the
+ * index j*nx + i of the cell's lower-left node and the run's weights of the
+ * nodes (i, j), (i+1, j), (i, j+1), (i+1, j+1): the sums over its points of
+ * trapezoid weight x bilinear weight (mm), in FP32.
+ * rt_rows: caller-owned device storage; pair k's runs at runs[k*cap ..
+ * k*cap + len[k]) in the order the ray visits the cells; len[k] = -1 where no
+ * row is recorded (the pair did not link to tol, or its ray visited more than
+ * cap cells); rt_tof_adjoint_rows traces those pairs again.
+ */
+typedef struct {
+    int32_t node;
+    float w00, w10, w01, w11;
+} rt_run;
+
+typedef struct {
+    rt_run* runs;      /* device [n_pairs * cap] */
+    int32_t* len;      /* device [n_pairs] */
+    int32_t cap;       /* runs per pair, >= 1 */
+} rt_rows;
+
+/* rt_rows_cap — runs per pair that hold every linked ray of the problem with
+ * room to spare: 1.15 x the cells a straight diameter crosses diagonally, plus
+ * 16 (1561 for a 95 mm ring on a 0.2 mm grid: 8.2 GB of runs for 261,632
+ * pairs); rays that visit more cells are traced again by
+ * rt_tof_adjoint_rows. Returns 0 for an invalid problem. */
+int32_t rt_rows_cap(const rt_problem* prob);
+
+/*
+ * rt_link_rows — rt_link (same arguments and results) that also records, for
+ * every pair that links to tol, the row of its linked ray into `rows`. Every
+ * trace of a pair records into the pair's slot, so the slot holds the last
+ * trace, which is the linked one. RT_FP32_COMP and RT_BILINEAR only
+ * (RT_EINVAL otherwise). Writes about 20 bytes per cell a trace visits.
+ */
+int rt_link_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* theta_io,
+                 double* tof_us, double* hit_xy_mm, int32_t* status, int32_t* iters, const rt_rows* rows,
+                 void* stream);
+
+/*
+ * rt_tof_adjoint_rows — rt_tof_adjoint from recorded rows: g_c as written by
+ * rt_tof_adjoint with the same theta, g_tof and tof_ref, for rows recorded by
+ * rt_link_rows on the same problem and options whose linked angles are theta
+ * (pairs without a row are traced again at theta). Each run's four weights
+ * are scaled by w_i in FP32 and added to FP64 accumulators, the arithmetic of
+ * rt_tof_adjoint, so the two agree up to the order of the FP64 sums. A warp
+ * per pair reads its row (coalesced). RT_FP32_COMP and RT_BILINEAR only.
+ */
+int rt_tof_adjoint_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const rt_rows* rows,
+                        const double* theta, const double* g_tof, const double* tof_ref, double* g_c,
+                        void* stream);
+
+/*
  * rt_path_matrix — the explicit sparse system matrix (paper Sec. 3.1.1,
  * "because of its sparsity, it can be computed and stored explicitly"):
  * row i = pair i, column j = node j, L_ij = sum over the ray's sample points

@@ -18,7 +18,7 @@ import torch
 from . import _lib as _L
 from .phantoms import Grid
 
-__all__ = ["Context", "Problem", "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix",
+__all__ = ["Context", "Problem", "rt_link", "rt_link_rows", "rt_tof_adjoint_rows", "Rows", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix",
            "rt_status_counts", "rt_batch_run", "BatchInstance", "ToF", "tof", "PRECISIONS",
            "BornMaps", "rtborn_maps", "rtborn_apply", "rtborn_adjoint", "Born", "born", "GEMM_MODES"]
 
@@ -155,6 +155,77 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                     _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
     return out
+
+
+@dataclasses.dataclass
+class Rows:
+    """Recorded rows of the system matrix (rt_rows): per pair up to `cap` runs
+    of 20 bytes (node index, four FP32 node weights) and the number recorded
+    (-1 = none)."""
+    runs: torch.Tensor               # int32 [n_pairs * cap * 5] (rt_run records)
+    len: torch.Tensor                # int32 [n_pairs]
+    cap: int
+
+    @staticmethod
+    def create(prob: Problem, cap: Optional[int] = None) -> "Rows":
+        lib = _L.load()
+        ps = prob.struct()
+        cap = int(lib.rt_rows_cap(C.byref(ps))) if cap is None else int(cap)
+        if cap < 1:
+            raise ValueError("invalid problem for recorded rows")
+        dev = prob.c.device
+        return Rows(torch.empty(prob.n_pairs * cap * 5, dtype=torch.int32, device=dev),
+                    torch.empty(prob.n_pairs, dtype=torch.int32, device=dev), cap)
+
+    def struct(self) -> _L.RtRows:
+        return _L.RtRows(self.runs.data_ptr(), self.len.data_ptr(), self.cap)
+
+
+def rt_link_rows(prob: Problem, ds: float, rows: Rows, tol: float = 1e-4, max_iter: int = 30,
+                 theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
+                 ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
+                 fan_rays: int = DEFAULT_FAN, fan_ds: float = 0.0) -> dict:
+    """rt_link (FP32-compensated, bilinear) that also records the rows of the
+    linked rays into `rows` for rt_tof_adjoint_rows."""
+    ctx = ctx or default_context(prob.c.device.index)
+    dev = prob.c.device
+    n = prob.n_pairs
+    if out is None:
+        out = dict(theta=torch.empty(n, dtype=torch.float64, device=dev),
+                   tof=torch.empty(n, dtype=torch.float64, device=dev),
+                   hit=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev),
+                   iters=torch.empty(n, dtype=torch.int32, device=dev))
+    if theta0 is None:
+        out["theta"].fill_(float("nan"))
+    else:
+        out["theta"].copy_(theta0)
+    ps = prob.struct(c)
+    o = _opts(ds, tol, max_iter, "fp32c", fan_rays, fan_ds=fan_ds)
+    rs = rows.struct()
+    _L.check(ctx.h, ctx.lib.rt_link_rows(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
+                                         _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), C.byref(rs),
+                                         _stream(stream)))
+    return out
+
+
+def rt_tof_adjoint_rows(prob: Problem, rows: Rows, theta: torch.Tensor, g_tof: torch.Tensor, ds: float,
+                        tof_ref: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
+                        ctx: Optional[Context] = None, stream=None,
+                        out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """rt_tof_adjoint from the rows recorded by rt_link_rows (same problem and
+    options; theta = the linked angles)."""
+    ctx = ctx or default_context(prob.c.device.index)
+    cc = prob.c if c is None else c
+    g = torch.empty_like(cc) if out is None else out
+    ps = prob.struct(c)
+    o = _opts(ds, precision="fp32c")
+    rs = rows.struct()
+    _L.check(ctx.h, ctx.lib.rt_tof_adjoint_rows(ctx.h, C.byref(ps), C.byref(o), C.byref(rs),
+                                                _ptr(theta.contiguous()), _ptr(g_tof.contiguous()),
+                                                _ptr(None if tof_ref is None else tof_ref.contiguous()), _ptr(g),
+                                                _stream(stream)))
+    return g
 
 
 def rt_tof_forward(prob: Problem, theta: torch.Tensor, ds: float, precision: str = "fp32c",

@@ -22,7 +22,8 @@ EXPORTED = [
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
     "rt_tof_forward_noalloc", "rt_batch_run", "rtborn_maps", "rtborn_apply", "rtborn_adjoint",
     "rt_csr_matvec", "rt_csr_rmatvec", "rt_bspline_coef", "rtborn_maps_abs", "rtborn_apply_abs",
-    "rtborn_adjoint_abs", "rt_peak_fma", "rt_peak_gather", "rt_peak_read",
+    "rtborn_adjoint_abs", "rt_peak_fma", "rt_peak_gather", "rt_peak_read", "rt_rows_cap", "rt_link_rows",
+    "rt_tof_adjoint_rows",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_TF32X3 = 0, 1
 ABI_VERSION = 3   # layout of RtOptions below
@@ -44,6 +45,13 @@ class RtProblem(C.Structure):
     _fields_ = [("grid", RtGrid), ("c_mps", C.c_void_p), ("n_tx", C.c_int32),
                 ("tx_xy_mm", C.c_void_p), ("ring_radius_mm", C.c_double), ("n_pairs", C.c_int32),
                 ("pairs", C.c_void_p)]
+
+
+class RtRows(C.Structure):
+    _fields_ = [("runs", C.c_void_p), ("len", C.c_void_p), ("cap", C.c_int32)]
+
+
+RUN_BYTES = 20   # rt_run: int32 node + 4 float weights
 
 
 class RtInstance(C.Structure):
@@ -88,6 +96,10 @@ def load():
         L.rt_ctx_reserve.argtypes = [vp, C.c_int64]
         L.rt_link.argtypes = [vp, P(RtProblem), P(RtOptions), vp, vp, vp, vp, vp, vp]
         L.rt_tof_forward.argtypes = [vp, P(RtProblem), P(RtOptions), vp, vp, vp, vp]
+        L.rt_rows_cap.argtypes = [P(RtProblem)]
+        L.rt_rows_cap.restype = C.c_int32
+        L.rt_link_rows.argtypes = [vp, P(RtProblem), P(RtOptions), vp, vp, vp, vp, vp, P(RtRows), vp]
+        L.rt_tof_adjoint_rows.argtypes = [vp, P(RtProblem), P(RtOptions), P(RtRows), vp, vp, vp, vp, vp]
         L.rt_tof_adjoint.argtypes = [vp, P(RtProblem), P(RtOptions), vp, vp, vp, vp, vp]
         L.rt_path_matrix.argtypes = [vp, P(RtProblem), P(RtOptions), vp, vp, vp, vp, C.c_int64,
                                      P(C.c_int64), vp]

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "rt_internal.h"
+#include "rt_link.cuh"
 #include "rt_trace.cuh"
 
 namespace {
@@ -103,6 +104,32 @@ int prepare(rt_ctx* ctx, const rt_problem* p, const rt_options* o, bool need_lin
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transducer table kernel");
     G->tx_phi = ctx->txphi;
     ctx->last_stream = s;
+    return RT_OK;
+}
+
+// Fan workspace of a cold-start link (sized outside stream capture).
+int ensure_fan(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, cudaStream_t s) {
+    if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536)
+        return fail(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
+    if (opt->fan_rays < 2) return RT_OK;
+    const size_t fan_bytes = sizeof(double) * (size_t)prob->n_tx * (size_t)opt->fan_rays;
+    const size_t need_bytes = sizeof(int) * (size_t)prob->n_tx;
+    if (ctx->fan_cap >= fan_bytes && ctx->need_cap >= need_bytes) return RT_OK;
+    if (capturing(s)) return fail(ctx, RT_EINVAL, "fan workspace too small during stream capture");
+    if (ctx->fan_cap < fan_bytes) {
+        if (ctx->fan) cudaFree(ctx->fan);
+        ctx->fan = nullptr;
+        ctx->fan_cap = 0;
+        if (cudaMalloc(&ctx->fan, fan_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "fan workspace");
+        ctx->fan_cap = fan_bytes;
+    }
+    if (ctx->need_cap < need_bytes) {
+        if (ctx->fan_need) cudaFree(ctx->fan_need);
+        ctx->fan_need = nullptr;
+        ctx->need_cap = 0;
+        if (cudaMalloc(&ctx->fan_need, need_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "fan workspace");
+        ctx->need_cap = need_bytes;
+    }
     return RT_OK;
 }
 
@@ -239,35 +266,67 @@ int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* 
     rt::Geom G;
     int rc = prepare(ctx, prob, opt, true, s, &G);
     if (rc) return rc;
-    if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536)
-        return fail(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
-    if (opt->fan_rays >= 2) {
-        const size_t fan_bytes = sizeof(double) * (size_t)prob->n_tx * (size_t)opt->fan_rays;
-        const size_t need_bytes = sizeof(int) * (size_t)prob->n_tx;
-        if (ctx->fan_cap < fan_bytes || ctx->need_cap < need_bytes) {
-            if (capturing(s)) return fail(ctx, RT_EINVAL, "fan workspace too small during stream capture");
-            if (ctx->fan_cap < fan_bytes) {
-                if (ctx->fan) cudaFree(ctx->fan);
-                ctx->fan = nullptr;
-                ctx->fan_cap = 0;
-                if (cudaMalloc(&ctx->fan, fan_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "fan workspace");
-                ctx->fan_cap = fan_bytes;
-            }
-            if (ctx->need_cap < need_bytes) {
-                if (ctx->fan_need) cudaFree(ctx->fan_need);
-                ctx->fan_need = nullptr;
-                ctx->need_cap = 0;
-                if (cudaMalloc(&ctx->fan_need, need_bytes) != cudaSuccess) return fail(ctx, RT_ENOMEM, "fan workspace");
-                ctx->need_cap = need_bytes;
-            }
-        }
-    }
+    rc = ensure_fan(ctx, prob, opt, s);
+    if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
     e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
                         status, iters, ctx->counters, ctx->queue, opt->fan_rays, opt->fan_ds_mm, ctx->fan,
                         ctx->fan_need, s);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
+}
+
+int32_t rt_rows_cap(const rt_problem* prob) {
+    if (!prob || !(prob->grid.h_mm > 0) || !(prob->ring_radius_mm > 0)) return 0;
+    const double cells = 1.15 * std::sqrt(2.0) * 2.0 * prob->ring_radius_mm / prob->grid.h_mm + 16.0;
+    if (!(cells < 1e9)) return 0;
+    return (int32_t)std::ceil(cells);
+}
+
+static int check_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const rt_rows* rows) {
+    if (!opt) return fail(ctx, RT_EINVAL, "options pointer is NULL");
+    if (opt->precision != RT_FP32_COMP || opt->interpolator != RT_BILINEAR)
+        return fail(ctx, RT_EINVAL, "recorded rows need RT_FP32_COMP and RT_BILINEAR");
+    if (!rows || rows->cap < 1 || (prob && prob->n_pairs > 0 && (!rows->runs || !rows->len)))
+        return fail(ctx, RT_EINVAL, "rows: runs, len and cap >= 1 are required");
+    return RT_OK;
+}
+
+int rt_link_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* theta_io, double* tof_us,
+                 double* hit_xy_mm, int32_t* status, int32_t* iters, const rt_rows* rows, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx) return RT_EINVAL;
+    int rc = check_rows(ctx, prob, opt, rows);
+    if (rc) return rc;
+    if (!theta_io && prob && prob->n_pairs > 0) return fail(ctx, RT_EINVAL, "theta_io is NULL");
+    rt::Geom G;
+    rc = prepare(ctx, prob, opt, true, s, &G);
+    if (rc) return rc;
+    rc = ensure_fan(ctx, prob, opt, s);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
+    const rt::RowRec rec{rows->runs, rows->len, rows->cap};
+    e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
+                        status, iters, ctx->counters, ctx->queue, opt->fan_rays, opt->fan_ds_mm, ctx->fan,
+                        ctx->fan_need, s, &rec);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
+}
+
+int rt_tof_adjoint_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const rt_rows* rows,
+                        const double* theta, const double* g_tof, const double* tof_ref, double* g_c, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx) return RT_EINVAL;
+    int rc = check_rows(ctx, prob, opt, rows);
+    if (rc) return rc;
+    if (!g_c) return fail(ctx, RT_EINVAL, "g_c is required");
+    if ((!theta || !g_tof) && prob && prob->n_pairs > 0) return fail(ctx, RT_EINVAL, "theta and g_tof are required");
+    rt::Geom G;
+    rc = prepare(ctx, prob, opt, false, s, &G);
+    if (rc) return rc;
+    const rt::RowRec rec{rows->runs, rows->len, rows->cap};
+    cudaError_t e = rt::launch_adjoint_rows(G, ctx->field, theta, g_tof, tof_ref, prob->c_mps, rec, g_c, s);
+    return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "adjoint kernel");
 }
 
 int rt_tof_forward(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const double* theta,

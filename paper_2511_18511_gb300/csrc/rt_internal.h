@@ -69,11 +69,17 @@ bool stream_capturing(cudaStream_t s);
 // the field layout (and kernel variant) follows G.interp.
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
                         cudaStream_t s);
+struct RowRec;
 // fan_ds: the fan's tracing step (0 = G.ds); its launch angles follow G.ds.
+// rec: record the rows of the system matrix (FP32-compensated bilinear only).
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
                         unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,
-                        int* fan_need, cudaStream_t s);
+                        int* fan_need, cudaStream_t s, const RowRec* rec = nullptr);
+// adjoint from recorded rows (pairs without one traced again), then the chain rule
+cudaError_t launch_adjoint_rows(const Geom& G, const void* field, const double* theta, const double* g_tof,
+                                const double* tof_ref, const double* c_mps, const RowRec& rec, double* g_c,
+                                cudaStream_t s);
 cudaError_t launch_fan(const Geom& G, double fan_ds, const void* field, int prec, int fan_rays, const double* theta,
                        double* fan, int* fan_need, unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_tof(const Geom& G, const void* field, int prec, const double* theta, double* tof,

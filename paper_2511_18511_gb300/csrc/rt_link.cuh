@@ -436,4 +436,57 @@ struct AdjSink {
     }
 };
 
+// Records a trace's runs (rt_run: the cell's lower-left node and its four
+// node weights, formed exactly as AdjSink::flush forms them before scaling)
+// into the pair's slot; runs beyond cap are counted but not stored.
+template <typename T>
+struct RecSink {
+    rt_run* base;
+    int n, cap, nx, ny;
+    CellAcc<T> acc;
+    __device__ __forceinline__ void emit(const CellAcc<T>& a) {
+        if (n < cap) {
+            const T w11 = a.Wxy, w10 = a.Wx - a.Wxy, w01 = a.Wy - a.Wxy;
+            const T w00 = (a.W - a.Wx) - w01;
+            const int i = min(max(a.ai, 0), nx - 2), j = min(max(a.aj, 0), ny - 2);
+            rt_run r;
+            r.node = j * nx + i;
+            r.w00 = (float)w00;
+            r.w10 = (float)w10;
+            r.w01 = (float)w01;
+            r.w11 = (float)w11;
+            base[n] = r;
+        }
+        ++n;
+    }
+    __device__ __forceinline__ void add(int ci, int cj, T tx, T ty, T a) {
+        if (ci != acc.ai || cj != acc.aj) {
+            if (acc.ai != INT_MIN) emit(acc);
+            acc.reset();
+            acc.ai = ci;
+            acc.aj = cj;
+        }
+        acc.W += a;
+        acc.Wx += a * tx;
+        acc.Wy += a * ty;
+        acc.Wxy += a * tx * ty;
+    }
+    __device__ __forceinline__ void finish() {
+        if (acc.ai != INT_MIN) emit(acc);
+        acc.reset();
+    }
+    __device__ __forceinline__ void begin(rt_run* slot) {
+        base = slot;
+        n = 0;
+        acc.reset();
+    }
+};
+
+// Recording target of a linking launch (rt_link_rows); runs == null: none.
+struct RowRec {
+    rt_run* runs;
+    int32_t* len;
+    int cap;
+};
+
 }  // namespace rt

@@ -6,6 +6,7 @@
 #include <cfloat>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include <cub/device/device_scan.cuh>
 #include <math_constants.h>
@@ -179,17 +180,28 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I
 // Persistent linking kernel: each lane takes pairs from the queue, advances
 // its own trace one RK4 step per loop iteration, and updates the linking
 // state when a trace ends, so lanes never wait for other lanes' pairs.
-template <typename T, int I>
-__global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, const typename Samp<T, I>::Field* __restrict__ F,
+// The recording variant keeps a run accumulator per lane: compiled for 5
+// resident blocks per SM (102 registers) instead of 6.
+template <typename T, int I, bool REC> struct LinkBlocks { static constexpr int v = Occ<T, I>::blocks; };
+template <typename T, int I> struct LinkBlocks<T, I, true> { static constexpr int v = 5; };
+
+template <typename T, int I, bool REC>
+__global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(Geom G, const typename Samp<T, I>::Field* __restrict__ F,
                                                      double tol, int max_iter, double* theta, double* tof,
                                                      double* hit, int32_t* status, int32_t* iters,
                                                      unsigned long long* counters, int* queue, int fan_rays,
-                                                     const double* __restrict__ fan) {
+                                                     const double* __restrict__ fan, RowRec rec) {
     __shared__ LinkState sh[kLinkBlock];
     LinkState& L = sh[threadIdx.x];
     auto C = make_cell<T, I>(G, F);
     TraceState<T> ts;
-    NoSink ns;
+    typename std::conditional<REC, RecSink<T>, NoSink>::type ns;
+    if constexpr (REC) {
+        ns.cap = rec.cap;
+        ns.nx = G.nx;
+        ns.ny = G.ny;
+        ns.begin(rec.runs);
+    }
     long long steps = 0;
     unsigned n_ok = 0, n_max = 0, n_cap = 0, n_bad = 0;
     bool active = false;
@@ -230,6 +242,7 @@ __global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, 
                 pair_of(G, k, e, r);
                 fan_start(G, L, fan + (size_t)e * fan_rays, fan_rays);
             }
+            if constexpr (REC) ns.begin(rec.runs + (size_t)k * rec.cap);
             trace_begin(ts, G, L.xe, L.ye, L.next);
             active = true;
         }
@@ -245,11 +258,18 @@ __global__ void __launch_bounds__(kLinkBlock, Occ<T, I>::blocks) k_link(Geom G, 
                 if (hit) { hit[2 * k] = L.best_hx; hit[2 * k + 1] = L.best_hy; }
                 if (iters) iters[k] = L.n_eval;
                 if (status) status[k] = st;
+                if constexpr (REC) {
+                    // the slot holds the last trace: the linked ray when it reached tol
+                    const bool last_is_best = st == RT_RAY_OK && ns.n <= rec.cap &&
+                                              L.best_th == L.next && o.flags == 0;
+                    rec.len[k] = last_is_best ? ns.n : -1;
+                }
                 n_ok += st == RT_RAY_OK;
                 n_max += st == RT_RAY_MAXITER;
                 n_cap += st == RT_RAY_STEPCAP;
                 active = false;
             } else {
+                if constexpr (REC) ns.begin(rec.runs + (size_t)L.k * rec.cap);
                 trace_begin(ts, G, L.xe, L.ye, L.next);
             }
         }
@@ -326,25 +346,30 @@ cudaError_t launch_fan(const Geom& G, double fan_ds, const void* field, int prec
     return cudaGetLastError();
 }
 
-template <typename T, int I>
+template <typename T, int I, bool REC = false>
 static void link_impl(const Geom& G, const void* field, double tol, int max_iter, double* theta, double* tof,
                       double* hit, int32_t* status, int32_t* iters, unsigned long long* counters, int* queue,
-                      int fan_rays, double* fan, int slot, cudaStream_t s) {
-    const int nb = min(persistent_blocks(k_link<T, I>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-    k_link<T, I><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, tol, max_iter, theta, tof,
-                                           hit, status, iters, counters, queue, fan_rays, fan);
+                      int fan_rays, double* fan, int slot, cudaStream_t s, const RowRec& rec = RowRec{}) {
+    const int nb = min(persistent_blocks(k_link<T, I, REC>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+    k_link<T, I, REC><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, tol, max_iter, theta,
+                                                tof, hit, status, iters, counters, queue, fan_rays, fan, rec);
 }
 
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
                         unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,
-                        int* fan_need, cudaStream_t s) {
+                        int* fan_need, cudaStream_t s, const RowRec* rec) {
     if (G.n_pairs == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (fan_rays >= 2) {
         e = launch_fan(G, fan_ds, field, prec, fan_rays, theta, fan, fan_need, counters, s);
         if (e != cudaSuccess) return e;
+    }
+    if (rec) {   // recording: FP32-compensated, bilinear (checked by the caller)
+        link_impl<float, RT_BILINEAR, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, queue,
+                                            fan_rays, fan, 11, s, *rec);
+        return cudaGetLastError();
     }
     const bool bs = G.interp == RT_BSPLINE;
     if (prec == RT_FP64) {
@@ -432,6 +457,62 @@ __global__ void k_adjoint_finish(double* g, const double* __restrict__ c_mps, in
         const double c = c_mps[k];
         g[k] = -1000.0 * g[k] / (c * c);
     }
+}
+
+// Adjoint from recorded rows: a warp per pair (in the work-queue order), its
+// lanes striding over the pair's runs, each run's four weights scaled by w in
+// FP32 and added with FP64 atomics exactly as AdjSink::flush adds them; pairs
+// without a row are traced again by lane 0.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_adjoint_rows(Geom G, const typename Samp<T, RT_BILINEAR>::Field* __restrict__ F,
+                                                         const double* theta, const double* g_tof,
+                                                         const double* tof_ref, double* g, RowRec rec) {
+    const long long wid = (blockIdx.x * (long long)kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= G.n_pairs) return;
+    const int k = queue_pair(G, (int)wid);
+    const double wd = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
+    if (wd == 0.0 || !isfinite(wd)) return;
+    const T w = (T)wd;
+    const int n = rec.len[k];
+    if (n >= 0) {
+        const rt_run* row = rec.runs + (size_t)k * rec.cap;
+        for (int r = lane; r < n; r += 32) {
+            const rt_run u = row[r];
+            double* p = g + u.node;
+            atomicAdd(p, to_double(w * (T)u.w00));
+            atomicAdd(p + 1, to_double(w * (T)u.w10));
+            atomicAdd(p + G.nx, to_double(w * (T)u.w01));
+            atomicAdd(p + G.nx + 1, to_double(w * (T)u.w11));
+        }
+    } else if (lane == 0) {
+        LinkCtx X;
+        if (!setup_pair(G, k, X)) return;
+        auto C = make_cell<T, RT_BILINEAR>(G, F);
+        AdjSink<T> sink;
+        sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
+        sink.init();
+        sink.w = w;
+        trace_ray<T>(C, G, X.xe, X.ye, theta[k], X.xr, X.yr, sink);
+    }
+}
+
+cudaError_t launch_adjoint_rows(const Geom& G, const void* field, const double* theta, const double* g_tof,
+                                const double* tof_ref, const double* c_mps, const RowRec& rec, double* g_c,
+                                cudaStream_t s) {
+    const int n = G.nx * G.ny;
+    cudaError_t e = cudaMemsetAsync(g_c, 0, sizeof(double) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    if (G.n_pairs > 0) {
+        const long long threads = (long long)G.n_pairs * 32;
+        k_adjoint_rows<float><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+            G, (const typename Samp<float, RT_BILINEAR>::Field*)field, theta, g_tof, tof_ref, g_c, rec);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int blocks = (n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8;
+    k_adjoint_finish<<<blocks, 256, 0, s>>>(g_c, c_mps, n);
+    return cudaGetLastError();
 }
 
 template <typename T, int I>

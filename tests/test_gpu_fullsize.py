@@ -199,3 +199,27 @@ def test_breast_finite_differences_autograd(breast, rt, P):
     print(f"finite differences ({len(fd)} pixels, h = 0.01 m/s, {skipped} skipped at caustics): rel L2 {err:.3e}")
     assert len(fd) == 64 and skipped <= 16
     assert err <= 1e-2
+
+
+def test_recorded_rows_breast(breast, rt):
+    """The bench's step with recorded rows (rt_link_rows + rt_tof_adjoint_rows,
+    cold fan of 768 rays at h/2) against rt_link + rt_tof_adjoint on the
+    breast workload: identical links, every pair's row recorded, and the
+    gradient equal up to the order of its FP64 sums."""
+    w, prob = breast
+    t_ref = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp64", fan_rays=768)["tof"].clone() * 0.999
+    sep = rt.rt_link(prob, w.ds, tol=w.tol, fan_rays=768, fan_ds=0.1)
+    g_sep = rt.rt_tof_adjoint(prob, sep["theta"], sep["tof"], w.ds, tof_ref=t_ref)
+    rows = rt.Rows.create(prob)
+    out = rt.rt_link_rows(prob, w.ds, rows, tol=w.tol, fan_rays=768, fan_ds=0.1)
+    g = rt.rt_tof_adjoint_rows(prob, rows, out["theta"], out["tof"], w.ds, tof_ref=t_ref)
+    torch.cuda.synchronize()
+    for k in ("theta", "tof", "hit", "status", "iters"):
+        assert torch.equal(out[k], sep[k]), k
+    ln = _np(rows.len)
+    gs = _np(g_sep)
+    rel = np.abs(_np(g) - gs).max() / np.abs(gs).max()
+    print(f"breast recorded rows: runs per ray {ln.mean():.0f} (max {ln.max()}, cap {rows.cap}), "
+          f"rows missing {(ln < 0).sum()}, gradient vs rt_tof_adjoint max rel {rel:.2e}")
+    assert (ln > 0).all()
+    assert rel <= 1e-11

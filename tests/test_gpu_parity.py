@@ -123,6 +123,43 @@ def test_link_with_coarse_fan_matches_oracle(rt, orc, P, prec):
         assert abs(it.mean() - it_ref.mean()) <= 0.01
 
 
+@pytest.mark.parametrize("fan", [FAN, 0])
+def test_recorded_rows_small(rt, orc, P, fan):
+    """rt_link_rows links exactly as rt_link and records the linked rays' rows;
+    rt_tof_adjoint_rows from them equals rt_tof_adjoint up to the order of the
+    FP64 sums and the oracle's adjoint within the adjoint bar; with a cap of 8
+    runs all but the shortest rows overflow and those pairs are traced again,
+    with the same gradient (128^2 / 64-ring, fan and straight starts)."""
+    w = P.cfg_small()
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
+    g_ref = torch.as_tensor(P.SplitMix64(5).normal(prob.n_pairs), device="cuda")
+    sep = rt.rt_link(prob, w.ds, tol=w.tol, fan_rays=fan)
+    g_sep = rt.rt_tof_adjoint(prob, sep["theta"], sep["tof"], w.ds, tof_ref=g_ref)
+    rows = rt.Rows.create(prob)
+    out = rt.rt_link_rows(prob, w.ds, rows, tol=w.tol, fan_rays=fan)
+    g = rt.rt_tof_adjoint_rows(prob, rows, out["theta"], out["tof"], w.ds, tof_ref=g_ref)
+    torch.cuda.synchronize()
+    for k in ("theta", "tof", "status", "iters"):
+        assert torch.equal(out[k], sep[k]), k
+    ln = _np(rows.len)
+    assert (ln > 0).all() and ln.max() <= rows.cap
+    ref = orc.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, _np(out["theta"]), _np(out["tof"]) - _np(g_ref))
+    gf, gs = _np(g), _np(g_sep)
+    rel = np.linalg.norm(gf - ref) / np.linalg.norm(ref)
+    same = np.abs(gf - gs).max() / np.abs(gs).max()
+    tiny = rt.Rows.create(prob, cap=8)
+    out2 = rt.rt_link_rows(prob, w.ds, tiny, tol=w.tol, fan_rays=fan)
+    g2 = rt.rt_tof_adjoint_rows(prob, tiny, out2["theta"], out2["tof"], w.ds, tof_ref=g_ref)
+    torch.cuda.synchronize()
+    ln2 = _np(tiny.len)
+    assert ((ln2 == -1) | ((ln2 >= 1) & (ln2 <= 8))).all() and (ln2 == -1).mean() > 0.9
+    same2 = np.abs(_np(g2) - gs).max() / np.abs(gs).max()
+    print(f"[fan={fan}] recorded rows: runs per ray {ln.mean():.0f} (max {ln.max()}, cap {rows.cap}), adjoint vs "
+          f"oracle rel L2 {rel:.2e}, vs rt_tof_adjoint {same:.2e}, {(ln2 == -1).mean():.3f} of the rows "
+          f"overflowing a cap of 8: {same2:.2e}")
+    assert rel <= ADJ_RTOL and same <= 1e-11 and same2 <= 1e-11
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_tof_at_oracle_angles(small, rt, prec):
     """Travel time at the oracle's linked angles (same rays on both sides)."""
