@@ -168,7 +168,8 @@ class BornInversionResult:
 
 def born_frequency_marching(maps, d_meas: torch.Tensor, f_mhz, levels, n_inner: int = 10,
                             tol_update: float = 1e-3, gemm: str = "fp32",
-                            dc0: Optional[torch.Tensor] = None, ops=None) -> BornInversionResult:
+                            dc0: Optional[torch.Tensor] = None, ops=None,
+                            update_rays: Optional[Callable] = None) -> BornInversionResult:
     """Ray-Born linearisations by frequency (arXiv:2511.18511 Sec. 3.1): the
     levels (lists of indices into f_mhz, ordered from low to high frequency)
     are solved in turn, each with the Hessian-based iterative solver (linear
@@ -176,9 +177,16 @@ def born_frequency_marching(maps, d_meas: torch.Tensor, f_mhz, levels, n_inner: 
     Sec. 3.1 item 1), warm-started from the previous level's estimate, until the
     relative l2 norm of the update falls below tol_update.
 
-    The Green's functions are the given maps (one background medium); the
-    paper's per-level ray update, and its Hessian-free single step whose data-
-    and solution-space weights it does not specify, are not part of this loop.
+    The paper updates the ray trajectories for each linearised subproblem from
+    the current estimate (Sec. 3.1). With update_rays, a callable dc ->
+    (apply(f_list, x), adjoint(f_list, d)) giving the Born operators whose
+    Green's functions are traced in the background plus dc, every level after
+    the first rebuilds its operators F_k from the current estimate dc_k; the
+    level's equation is F_k dc = d_level, solved from dc_k, so its first
+    residual is d_level - F_k dc_k (the data stay the Born data relative to the
+    background). Without it the Green's functions are the given maps (or ops)
+    throughout. The paper's Hessian-free single step, whose data- and
+    solution-space weights it does not specify, is not part of this loop.
     d_meas: complex [n_freq, n_tx, n_tx] data at the frequencies f_mhz.
     ops: optional (apply(f_list, dc), adjoint(f_list, d)) in place of the
     library's rtborn_apply / rtborn_adjoint on the maps (the GPU operators)."""
@@ -191,7 +199,9 @@ def born_frequency_marching(maps, d_meas: torch.Tensor, f_mhz, levels, n_inner: 
         dc = dc0.clone()
     misfit, update = [], []
     run = 0
-    for lev in levels:
+    for li, lev in enumerate(levels):
+        if update_rays is not None and li > 0:
+            ops = update_rays(dc)
         idx = list(lev)
         f = [float(f_mhz[i]) for i in idx]
         b = d_meas[idx].contiguous()
@@ -209,3 +219,19 @@ def born_frequency_marching(maps, d_meas: torch.Tensor, f_mhz, levels, n_inner: 
         if du < tol_update:
             break
     return BornInversionResult(dc, misfit, update, run)
+
+
+def gpu_ray_update(prob, ds: float, fan_rays: int, gemm: str = "tf32x3", **maps_kw) -> Callable:
+    """update_rays for born_frequency_marching on the GPU: dc (float32 [ny, nx],
+    m/s) -> the library's Born operators on maps traced (rtborn_maps) in
+    prob.c + dc."""
+    from . import rtborn_adjoint, rtborn_apply, rtborn_maps
+    state = {"maps": None}
+
+    def rebuild(dc):
+        c = (prob.c + dc.to(torch.float64)).contiguous()
+        state["maps"] = rtborn_maps(prob, ds, fan_rays, c=c, out=state["maps"], **maps_kw)
+        m = state["maps"]
+        return (lambda f, x: rtborn_apply(m, f, x, gemm=gemm), lambda f, d: rtborn_adjoint(m, f, d, gemm=gemm))
+
+    return rebuild
