@@ -480,9 +480,14 @@ def run_profile_case(args):
     pairs = pairs[pairs[:, 0] < args.profile]
     # all emitters: the implicit all-pairs list, served in the bench's queue order
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius, pairs=None if args.profile >= w.n_tx else pairs)
+    rows = rt.Rows.create(prob) if args.precision == "fp32c" else None
     for _ in range(2):
-        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision, fan_rays=BREAST_FAN, fan_ds=FAN_DS)
-        rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=r["tof"] * 0.999, precision=args.precision)
+        if rows is not None:       # the bench's step: recorded rows
+            r = rt.rt_link_rows(prob, w.ds, rows, tol=w.tol, fan_rays=BREAST_FAN, fan_ds=FAN_DS)
+            rt.rt_tof_adjoint_rows(prob, rows, r["theta"], r["tof"], w.ds, tof_ref=r["tof"] * 0.999)
+        else:
+            r = rt.rt_link(prob, w.ds, tol=w.tol, precision=args.precision, fan_rays=BREAST_FAN, fan_ds=FAN_DS)
+            rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=r["tof"] * 0.999, precision=args.precision)
     torch.cuda.synchronize()
     ok, counts = rt.rt_status_counts()
     print(json.dumps({"profile_case": w.name, "pairs": int(len(pairs)), "precision": args.precision,
@@ -946,6 +951,19 @@ def single_gpu_legs(args, peaks, rt, torch, prob, w, ctx, timed, res, link_ms, a
         "note": "algorithmic bytes = the recorded runs (20 B each) + 20 B per pair; the 4 FP64 atomics per run "
                 "go to the L2-resident gradient",
         "peak_basis": "measured HBM copy rate (MEASURED_PEAKS.json)"}
+    # the link without recording (rt_link), for the cost of the recording
+    out_p = buffers()
+    tl = []
+    for k in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rt.rt_link(prob, w.ds, tol=w.tol, precision="fp32c", ctx=ctx, out=out_p, fan_rays=BREAST_FAN, fan_ds=FAN_DS)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            tl.append(a.elapsed_time(b))
+    legs["link_without_rows_ms"] = float(np.mean(tl))
     # the same adjoint by retracing every ray (rt_tof_adjoint), for comparison
     g_r = torch.empty_like(prob.c)
     ta = []
