@@ -149,7 +149,8 @@ struct BornCell {
     // Fields at fractions (u, v) of cell (ci, cj), as Cell::at of the ToF path.
     __device__ __forceinline__ void at(int ci, int cj, float u, float v, float& c, float& gx, float& gy, float& hxx,
                                        float& hxy, float& hyy, float& tx, float& ty) {
-        if (ci == pi && cj == pj && u >= 0.f && u < 1.f && v >= 0.f && v < 1.f) {
+        // 0 <= u < 1 on the float bits (-0 takes the general path, to the same result)
+        if (ci == pi && cj == pj && __float_as_uint(u) < 0x3f800000u && __float_as_uint(v) < 0x3f800000u) {
             tx = u;
             ty = v;
         } else {
@@ -377,35 +378,58 @@ __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, co
     const float ac0 = dx * D0y - dy * D0x;
     const int ic = B.S.ci + (oi ? 1 : 0), jc = B.S.cj + (oj ? 1 : 0);
     const float cP = c * B.P;
+    // Which of the nine nodes take a candidate (bit 3 (b + 1) + a + 1), then
+    // one pass per taken node: the warp runs the candidate body as often as its
+    // busiest lane has nodes (about once per sample at ds = h/10) instead of
+    // once per block position that any of its lanes takes.
+    // The window -ds/2 <= a < ds/2 as 0 <= a + ds/2 < ds on the float bits: a
+    // non-negative float below ds has smaller bits than ds, and a negative one
+    // (or NaN) larger. The whole block inside the grid is the rule (a ring at
+    // least a cell and a step inside the grid); the per-node test is the
+    // exception.
+    unsigned take = 0;
+    const unsigned wbits = __float_as_uint(2.f * A.Hhalf);
+    const float sh = al0 + A.Hhalf;
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
+        const float t = sh + (float)b * dy;
 #pragma unroll
-        for (int a = -1; a <= 1; ++a) {
-            const float al = al0 + (float)a * dx + (float)b * dy;
-            if (al >= -A.Hhalf && al < A.Hhalf) {
-                const int ni = ic + a, nj = jc + b;
-                if (ni >= 0 && ni < G.nx && nj >= 0 && nj < G.ny) {
-                    const float ac = ac0 + (float)b * dx - (float)a * dy;
-                    // paraxial Q carried to the foot of the node (dQ~/ds~ = c P)
-                    const float Qf = B.Q + al * cP;
-                    const float aQ = fabsf(Qf);
-                    const float Qc = aQ >= 1.f ? aQ : 1.f;
-                    float M = B.P / Qf;
-                    if (!(M >= 0.f)) M = B.P / copysignf(Qc, Qf);
-                    const float ext = A.hf * (s * al + 0.5f * M * ac * ac) - Tc;
-                    const size_t node = (size_t)nj * G.nx + ni;
-                    atomicMin(tfirst + node, f2ord(T + ext));
-                    const float ux = (float)ni - F.xt, uy = (float)nj - F.yt;
-                    const float Tref = F.h_ct * sqrtf(ux * ux + uy * uy);
-                    const float score = ((T - Tref) + ext) + A.eta * ac * ac;
-                    const float amp = sqrtf(c * inv_ct_h / Qc);
-                    const unsigned long long sk = (unsigned long long)f2ord(score) << 32;
-                    atomicMin(near + node, sk | __float_as_uint(amp));
-                    // Lambda >= 0: its float bits order like its value
-                    if (ABS) atomicMin(lam + node, sk | __float_as_uint(fmaxf(Lm + al_h * al, 0.f)));
-                }
-            }
+        for (int a = -1; a <= 1; ++a)
+            if (__float_as_uint(t + (float)a * dx) < wbits) take |= 1u << (3 * (b + 1) + (a + 1));
+    }
+    if (ic < 1 || ic >= G.nx - 1 || jc < 1 || jc >= G.ny - 1) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int ni = ic + q % 3 - 1, nj = jc + q / 3 - 1;
+            if (ni < 0 || ni >= G.nx || nj < 0 || nj >= G.ny) take &= ~(1u << q);
         }
+    }
+    while (take) {
+        const int q = __ffs(take) - 1;
+        take &= take - 1;
+        const int b = (q >= 6) ? 1 : ((q >= 3) ? 0 : -1);
+        const int a = q - 3 * (b + 1) - 1;
+        const float fa = (float)a, fb = (float)b;
+        const float al = al0 + fa * dx + fb * dy;
+        const float ac = ac0 + fb * dx - fa * dy;
+        const int ni = ic + a, nj = jc + b;
+        // paraxial Q carried to the foot of the node (dQ~/ds~ = c P)
+        const float Qf = B.Q + al * cP;
+        const float aQ = fabsf(Qf);
+        const float Qc = aQ >= 1.f ? aQ : 1.f;
+        float M = B.P / Qf;
+        if (!(M >= 0.f)) M = B.P / copysignf(Qc, Qf);
+        const float ext = A.hf * (s * al + 0.5f * M * ac * ac) - Tc;
+        const size_t node = (size_t)nj * G.nx + ni;
+        atomicMin(tfirst + node, f2ord(T + ext));
+        const float ux = (float)ni - F.xt, uy = (float)nj - F.yt;
+        const float Tref = F.h_ct * sqrtf(ux * ux + uy * uy);
+        const float score = ((T - Tref) + ext) + A.eta * ac * ac;
+        const float amp = sqrtf(c * inv_ct_h / Qc);
+        const unsigned long long sk = (unsigned long long)f2ord(score) << 32;
+        atomicMin(near + node, sk | __float_as_uint(amp));
+        // Lambda >= 0: its float bits order like its value
+        if (ABS) atomicMin(lam + node, sk | __float_as_uint(fmaxf(Lm + al_h * al, 0.f)));
     }
 }
 
