@@ -130,8 +130,9 @@ def batch_leg(args, peaks, steps: int = 3, warmup: int = 3, fp64_every: int = 4)
         b.tof_ref = b.tof.clone()
         b.g_c = torch.empty_like(b.prob.c)
     total = sum(b.prob.n_pairs for b in insts)
-    best, times = autotune.tune_batch(insts, ds, reps=1)
-    kw = dict(block_threads=best[0], step_unroll=best[1], blocks_per_sm=best[2])
+    fan_ds = 0.5 * ws[0].grid.h           # every instance has h = 0.2 mm: the fan traced at 0.1 mm
+    best, times = autotune.tune_batch(insts, ds, reps=1, fan_ds=fan_ds)
+    kw = dict(block_threads=best[0], step_unroll=best[1], blocks_per_sm=best[2], fan_ds=fan_ds)
     rt.rt_batch_run(insts, ds, **kw)
     torch.cuda.synchronize()
     s = torch.cuda.Stream()
@@ -180,13 +181,13 @@ def batch_leg(args, peaks, steps: int = 3, warmup: int = 3, fp64_every: int = 4)
         return a.elapsed_time(b)
 
     ms_sub32 = timed_sub("fp32c", kw)
-    ms_sub64 = timed_sub("fp64", dict(block_threads=128, step_unroll=1, blocks_per_sm=1))
+    ms_sub64 = timed_sub("fp64", dict(block_threads=128, step_unroll=1, blocks_per_sm=1, fan_ds=fan_ds))
     fp32 = peaks["fp32_tflops"]
     return {"metric": "linked rays/s (batched link+adjoint, 32 uneven instances, one persistent launch, CUDA graph)",
             "value": total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
             "config": {"workload": "batch32_uneven", "instances": len(insts), "pairs": total, "ds_mm": ds,
                        "grids": sorted({int(b.prob.grid.nx) for b in insts}),
-                       "rings": sorted({b.prob.n_tx for b in insts}), "fan_rays": rt.DEFAULT_FAN,
+                       "rings": sorted({b.prob.n_tx for b in insts}), "fan_rays": rt.DEFAULT_FAN, "fan_ds_mm": fan_ds,
                        "autotuned": {"rays_per_block": best[0], "step_unroll": best[1], "blocks_per_sm": best[2]},
                        "autotune_ms": {",".join(map(str, k)): round(v, 2) for k, v in times.items()},
                        "l2": "flushed between timed replays (256 MB write)"},
@@ -457,7 +458,8 @@ def run_born(args):
 
 def run_profile_case(args):
     """One rt_link on a subset of pairs of the full-size workload (ncu captures);
-    with --workload born, rtborn_maps on the first N_EMIT transducers."""
+    with --workload born, rtborn_maps on the first N_EMIT transducers, then the
+    Born apply and adjoint (tensor-core path) of those maps at two frequencies."""
     import torch
     if args.workload == "born":
         import paper_2511_18511_gb300 as rt
@@ -470,8 +472,14 @@ def run_profile_case(args):
             maps = rt.rtborn_maps(prob, w.ds, w.fan_rays, out=maps)
         torch.cuda.synchronize()
         _, counts = rt.rt_status_counts()
+        dc = torch.as_tensor(w.dc, dtype=torch.float32, device="cuda")
+        f = list(w.f_mhz[:2])
+        d = rt.rtborn_apply(maps, f, dc)
+        g = rt.rtborn_adjoint(maps, f, d)
+        torch.cuda.synchronize()
         print(json.dumps({"profile_case": w.name, "transducers": n, "fan_rays": w.fan_rays,
-                          "rk4_steps_both_passes": counts[7]}))
+                          "rk4_steps_both_passes": counts[7], "born_frequencies": f,
+                          "finite": bool(torch.isfinite(d).all()) and bool(torch.isfinite(g).all())}))
         return
     import paper_2511_18511_gb300 as rt
     from paper_2511_18511_gb300 import phantoms as P
@@ -946,10 +954,12 @@ def single_gpu_legs(args, peaks, rt, torch, prob, w, ctx, timed, res, link_ms, a
     hbm = peaks["hbm_gbs"]
     legs["roofline_adjoint"] = {
         "bound": "hbm", "achieved": adj_gbs, "peak": hbm, "unit": "GB/s", "frac": adj_gbs / hbm,
-        "traffic": None, "kernel": "rt_tof_adjoint_rows call: k_adjoint_rows (+ pack, finish)",
-        "bytes_per_launch": adj_bytes, "runs": runs, "fp64_atomics_per_s": 4.0 * runs / (adjoint_ms / 1e3),
-        "note": "algorithmic bytes = the recorded runs (20 B each) + 20 B per pair; the 4 FP64 atomics per run "
-                "go to the L2-resident gradient",
+        "traffic": _traffic(os.path.join(ROOT, "profiles", "adjoint_traffic.json"), ("rt_ray.cu", "rt_link.cuh")),
+        "kernel": "rt_tof_adjoint_rows call: k_adjoint_rows (+ pack, finish)",
+        "bytes_per_launch": adj_bytes, "runs": runs, "runs_per_s": runs / (adjoint_ms / 1e3),
+        "note": "algorithmic bytes = the recorded runs (20 B each) + 20 B per pair; the gradient stays in L2 and "
+                "takes FP64 atomics, up to four per run (a lane first sums the nodes that consecutive cells of "
+                "its ray share)",
         "peak_basis": "measured HBM copy rate (MEASURED_PEAKS.json)"}
     # the link without recording (rt_link), for the cost of the recording
     out_p = buffers()

@@ -20,9 +20,9 @@ CANDIDATES = [(64, 1, 8), (64, 1, 12), (128, 1, 4), (128, 1, 5), (128, 1, 6), (1
 CACHE = os.path.join(_build.OUT, "autotune.json")
 
 
-def signature(instances, precision: str, fan_rays: int) -> str:
+def signature(instances, precision: str, fan_rays: int, fan_ds: float = 0.0) -> str:
     parts = [f"{b.prob.grid.nx}x{b.prob.grid.ny}:{b.prob.n_tx}:{int(b.tof_ref is not None)}" for b in instances]
-    return f"{precision}|fan{fan_rays}|" + ",".join(sorted(parts))
+    return f"{precision}|fan{fan_rays}@{fan_ds:g}|" + ",".join(sorted(parts))
 
 
 def _load():
@@ -34,10 +34,10 @@ def _load():
 
 
 def tune_batch(instances, ds: float, tol: float = 1e-4, precision: str = "fp32c", fan_rays: int = 256,
-               reps: int = 2, use_cache: bool = True, verbose: bool = False):
+               reps: int = 2, use_cache: bool = True, verbose: bool = False, fan_ds: float = 0.0):
     """Returns ((block_threads, step_unroll, blocks_per_sm), {candidate: ms}) for this batch."""
     from . import rt_batch_run
-    key = f"{torch.cuda.get_device_name()}|{signature(instances, precision, fan_rays)}"
+    key = f"{torch.cuda.get_device_name()}|{signature(instances, precision, fan_rays, fan_ds)}"
     cache = _load()
     if use_cache and key in cache:
         c = cache[key]
@@ -46,14 +46,14 @@ def tune_batch(instances, ds: float, tol: float = 1e-4, precision: str = "fp32c"
     times = {}
     for blk, unr, occ in cands:
         rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk, step_unroll=unr,
-                     blocks_per_sm=occ)
+                     blocks_per_sm=occ, fan_ds=fan_ds)
         torch.cuda.synchronize()
         best = None
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk,
-                         step_unroll=unr, blocks_per_sm=occ)
+                         step_unroll=unr, blocks_per_sm=occ, fan_ds=fan_ds)
             b.record()
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
