@@ -71,8 +71,10 @@ def load(path: str):
                             C.c_double, C.c_double, C.c_double, C.c_int64, _dp, _dp,
                             _lp, _dp, _ip]
     L.orc_link.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
-                           C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp, _ip, _ip,
-                           C.c_int32]
+                           C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32, _dp, _dp, _dp, _ip,
+                           _ip, C.c_int32]
+    L.orc_subfan_angles.argtypes = [C.c_double, C.c_double, C.c_int32, _dp]
+    L.orc_subfan_predict.argtypes = [C.c_int32, _dp, _dp, _ip, _dp]
     L.orc_tof.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip, C.c_double,
                           _dp, _dp, _dp, C.c_int32]
     L.orc_path_matrix.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
@@ -261,10 +263,11 @@ def _pairs_arg(pairs, n_tx):
 
 
 def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None, nthreads=0, fan_rays=0,
-         fan_ds=0.0):
+         fan_ds=0.0, subfan=0):
     """Link all pairs; returns dict(theta, tof, hit, status, iters). fan_rays = 0:
     straight-line cold start; >= 2: fan-predicted cold start, the fan's rays
-    traced at step fan_ds (0 = ds)."""
+    traced at step fan_ds (0 = ds); subfan > 0: a fan-started pair whose second
+    trace misses is refined by subfan rays inside its bracket (reading R12)."""
     c = _f64(c_mps)
     tx = _f64(tx).reshape(-1, 2)
     p, n_pairs = _pairs_arg(pairs, tx.shape[0])
@@ -275,10 +278,28 @@ def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None,
     iters = np.empty(n_pairs, np.int32)
     g = _grid(grid)
     rc = lib().orc_link(C.byref(g), _d(c), tx.shape[0], _d(tx), R, n_pairs, _i(p), ds, tol,
-                        max_iter, fan_rays, float(fan_ds), _d(theta), _d(tof), _d(hit), _i(status), _i(iters),
-                        nthreads)
+                        max_iter, fan_rays, float(fan_ds), int(subfan), _d(theta), _d(tof), _d(hit), _i(status),
+                        _i(iters), nthreads)
     _check(rc, "link")
     return dict(theta=theta, tof=tof, hit=hit, status=status, iters=iters)
+
+
+def subfan_angles(ta, tb, M):
+    """R12: the M sub-fan ray angles strictly inside the bracket (ta, tb)."""
+    out = np.empty(int(M))
+    _check(lib().orc_subfan_angles(float(ta), float(tb), int(M), _d(out)), "subfan_angles")
+    return out
+
+
+def subfan_predict(theta, m, interior):
+    """R12 prediction from the sequence (bracket end of negative misfit,
+    sub-fan rays, other end) -> dict(theta3, ta, tb, start_theta, start_m,
+    changes_sign)."""
+    t, mm = _f64(theta).ravel(), _f64(m).ravel()
+    it = np.ascontiguousarray(interior, dtype=np.int32).ravel()
+    out = np.empty(6)
+    _check(lib().orc_subfan_predict(len(t), _d(t), _d(mm), _i(it), _d(out)), "subfan_predict")
+    return dict(theta3=out[0], ta=out[1], tb=out[2], start_theta=out[3], start_m=out[4], changes_sign=bool(out[5]))
 
 
 def tof(grid, c_mps, tx, R, ds, theta, pairs=None, nthreads=0):

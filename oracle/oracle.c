@@ -582,7 +582,20 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
  * The fan only predicts: its rays may be traced at their own step fan_ds
  * (0 = the linking step ds), while their launch angles, the fan margin ds/R
  * and every linking trace keep ds, so the bracket rule and the predictions
- * are the same functions of the fan's interceptions. */
+ * are the same functions of the fan's interceptions.
+ *
+ * R12 sub-fan (an option, subfan = M > 0): when the second trace of a
+ * fan-started pair misses too, M more rays at fan_ds, evenly spaced strictly
+ * inside the bracket, theta_q = ta + (tb - ta) q / (M + 1), q = 1..M (ta the
+ * end of negative misfit), refine it before the third trace. In the sequence
+ * (ta, the sub-fan rays that reach the ring, tb) the first entry of
+ * non-negative misfit and the one before it become the bracket (the Illinois
+ * state restarts); the third angle is the root of the inverse cubic through
+ * the four sub-fan rays around that interval (when all four are sub-fan rays,
+ * their misfits increase strictly along the sequence and the root falls
+ * inside), else the Regula-Falsi point of the interval; the secant then
+ * starts from the interval end of smaller |misfit|. Like the fan, the
+ * sub-fan only predicts; the linking traces keep ds. */
 static double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
 
 /* Value at m = 0 of the polynomial theta(m) through the n points (m_q, t_q),
@@ -631,9 +644,78 @@ static void fan_for_emitter(const Field* F, double R, const double* xe, double d
     }
 }
 
+/* R12 prediction from the sequence (st[i], sm[i]), i = 0..n-1, of the
+ * bracket end of negative misfit, the sub-fan rays that reached the ring (in
+ * angle order, interior[i] = 1) and the other bracket end: the first entry of
+ * non-negative misfit and the one before it become the bracket B (Illinois
+ * state restarted); returns the third angle (the inverse cubic through the
+ * four sub-fan rays around the interval when they are all sub-fan rays with
+ * strictly increasing misfits and the root falls inside, else the
+ * Regula-Falsi point) and sets *start to the interval end of smaller
+ * |misfit|, where the secant starts. */
+static double subfan_predict(const double* st, const double* sm, const int* interior, int n, Bracket* B,
+                             double* start_theta, double* start_m) {
+    int j = 1;
+    while (j < n - 1 && sm[j] < 0) ++j;
+    B->ta = st[j - 1]; B->fa = sm[j - 1];
+    B->tb = st[j]; B->fb = sm[j];
+    B->last = 0;
+    double th = B->ta - B->fa * (B->tb - B->ta) / (B->fb - B->fa);
+    if (j - 2 >= 0 && j + 1 < n && interior[j - 2] && interior[j - 1] && interior[j] && interior[j + 1] &&
+        sm[j - 2] < sm[j - 1] && sm[j - 1] < sm[j] && sm[j] < sm[j + 1]) {
+        const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);
+        if (v > fmin(B->ta, B->tb) && v < fmax(B->ta, B->tb)) th = v;
+    }
+    const int lo = fabs(B->fa) <= fabs(B->fb);
+    *start_theta = lo ? B->ta : B->tb;
+    *start_m = lo ? B->fa : B->fb;
+    return th;
+}
+
+/* Angle of sub-fan ray q = 1..M inside the bracket (ta, tb). */
+static double subfan_angle(double ta, double tb, int q, int M) { return ta + (tb - ta) * q / (M + 1); }
+
+/* R12: trace the M sub-fan rays of bracket B at fan_ds and predict. */
+static double subfan_refine(const Field* F, double R, const double* xe, double phi_e, double psi_r,
+                            double fan_ds, int M, Bracket* B, Eval* start) {
+    double st[ORC_SUBFAN_MAX + 2], sm[ORC_SUBFAN_MAX + 2];
+    int interior[ORC_SUBFAN_MAX + 2];
+    int n = 0;
+    st[n] = B->ta; sm[n] = B->fa; interior[n++] = 0;
+    for (int q = 1; q <= M; ++q) {
+        const double th = subfan_angle(B->ta, B->tb, q, M);
+        TraceRes tr;
+        trace(F, R, xe[0], xe[1], xe[0], xe[1], th, fan_ds, NULL, NULL, 0, &tr);
+        if (tr.flags & 3) continue;
+        st[n] = th;
+        sm[n] = R * (mod_2pi(atan2(tr.hit[1], tr.hit[0]) - phi_e) - psi_r);
+        interior[n++] = 1;
+    }
+    st[n] = B->tb; sm[n] = B->fb; interior[n++] = 0;
+    return subfan_predict(st, sm, interior, n, B, &start->theta, &start->m);
+}
+
+int orc_subfan_angles(double ta, double tb, int32_t M, double* theta) {
+    if (M < 1 || M > ORC_SUBFAN_MAX || !theta) return ORC_EINVAL;
+    for (int q = 1; q <= M; ++q) theta[q - 1] = subfan_angle(ta, tb, q, M);
+    return ORC_OK;
+}
+
+int orc_subfan_predict(int32_t n, const double* st, const double* sm, const int32_t* interior, double* out6) {
+    if (n < 2 || n > ORC_SUBFAN_MAX + 2 || !st || !sm || !interior || !out6) return ORC_EINVAL;
+    int in[ORC_SUBFAN_MAX + 2];
+    for (int i = 0; i < n; ++i) in[i] = interior[i] != 0;
+    Bracket B;
+    double s_th, s_m;
+    out6[0] = subfan_predict(st, sm, in, n, &B, &s_th, &s_m);
+    out6[1] = B.ta; out6[2] = B.tb; out6[3] = s_th; out6[4] = s_m;
+    out6[5] = (B.fa < 0 && B.fb >= 0) ? 1.0 : 0.0;
+    return ORC_OK;
+}
+
 static void link_pair_fan(const Field* F, double R, const double* xe, const double* xr, double ds,
-                          double tol, int max_iter, const double* psi, int K, Eval* best, int* status,
-                          int* n_eval_out) {
+                          double tol, int max_iter, const double* psi, int K, double fan_ds, int subfan,
+                          Eval* best, int* status, int* n_eval_out) {
     const double phi_e = atan2(xe[1], xe[0]);
     const double psi_r = mod_2pi(atan2(xr[1], xr[0]) - phi_e);
     const double th_lo = phi_e + 0.5 * M_PI, th_hi = phi_e + 1.5 * M_PI;
@@ -706,7 +788,12 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
     int n_eval = 0, conv = 0;
     double next = th0;
     while (n_eval < max_iter) {
-        if (n_eval > 0) {
+        if (n_eval == 2 && subfan > 0) {
+            Eval s0;
+            next = subfan_refine(F, R, xe, phi_e, psi_r, fan_ds, subfan, &B, &s0);
+            prev = s0;
+            cur = s0;
+        } else if (n_eval > 0) {
             if (n_eval == 1 && ok4 && !(cur.tr.flags & 3)) {
                 const double t5[5] = {cur.theta, t4[0], t4[1], t4[2], t4[3]};
                 const double m5[5] = {cur.m, m4[0], m4[1], m4[2], m4[3]};
@@ -816,11 +903,12 @@ static int check_common(const orc_grid* g, int32_t n_tx, const double* tx, doubl
 
 int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
              double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
-             int32_t max_iter, int32_t fan_rays, double fan_ds, double* theta_io, double* tof,
+             int32_t max_iter, int32_t fan_rays, double fan_ds, int32_t subfan, double* theta_io, double* tof,
              double* hit_xy, int32_t* status, int32_t* iters, int32_t nthreads) {
     int rc = check_common(g, n_tx, tx, R, ds, n_pairs, pairs);
     if (rc) return rc;
     if (!theta_io || !(tol > 0) || fan_rays == 1 || fan_rays < 0) return ORC_EINVAL;
+    if (subfan < 0 || subfan > ORC_SUBFAN_MAX) return ORC_EINVAL;
     if (fan_ds == 0.0) fan_ds = ds;
     if (!(fan_ds > 0) || !isfinite(fan_ds) || (fan_rays > 0 && !ring_ok(g, R, fan_ds))) return ORC_EINVAL;
     Field F;
@@ -854,7 +942,7 @@ int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double*
         int st, ne;
         if (fan && isnan(theta_io[k]))
             link_pair_fan(&F, R, tx + 2 * e, tx + 2 * r, ds, tol, max_iter, fan + (size_t)e * fan_rays, fan_rays,
-                          &best, &st, &ne);
+                          fan_ds, subfan, &best, &st, &ne);
         else
             link_pair(&F, R, tx + 2 * e, tx + 2 * r, ds, tol, max_iter, theta_io[k], &best, &st, &ne);
         theta_io[k] = best.theta;

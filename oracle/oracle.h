@@ -68,11 +68,22 @@ int orc_trace(const orc_grid* g, const double* c_mps, double R, double xe, doubl
  * linked angle. Cold starts use the straight line to the receiver when
  * fan_rays == 0, else a fan of fan_rays (>= 2) rays per emitter predicts the
  * first angle and a bracket; the fan's rays are traced at step fan_ds (0 = ds;
- * their launch angles follow ds). Outputs may be NULL. */
+ * their launch angles follow ds). subfan (0..ORC_SUBFAN_MAX, fan starts only):
+ * after a second missed trace, subfan rays at fan_ds inside the bracket refine
+ * it before the third (reading R12). Outputs may be NULL. */
+#define ORC_SUBFAN_MAX 32
 int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,
              double R, int32_t n_pairs, const int32_t* pairs, double ds, double tol,
-             int32_t max_iter, int32_t fan_rays, double fan_ds, double* theta_io, double* tof,
+             int32_t max_iter, int32_t fan_rays, double fan_ds, int32_t subfan, double* theta_io, double* tof,
              double* hit_xy, int32_t* status, int32_t* iters, int32_t nthreads);
+
+/* R12 sub-fan pieces, for tests: the M ray angles inside a bracket (ta, tb),
+ * and the prediction from a sequence of n (angle, misfit, interior flag)
+ * entries (bracket end of negative misfit, sub-fan rays, other bracket end):
+ * out6 = {third angle, new ta, new tb, secant start angle and misfit, 1 when
+ * the new bracket changes sign}. */
+int orc_subfan_angles(double ta, double tb, int32_t M, double* theta);
+int orc_subfan_predict(int32_t n, const double* st, const double* sm, const int32_t* interior, double* out6);
 
 /* Travel time (and hit) of every pair at the given angles, no linking. */
 int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,

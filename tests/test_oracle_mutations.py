@@ -58,10 +58,28 @@ MUTANTS = {
                                  "    const double step = (a_max - a_min) / (K - 1);\n    for (int k = 0; k < K; ++k) {"),
     "fan_traced_at_link_step": ("fan_theta(a_min, step, k), fan_ds, NULL, NULL, 0, &tr);",
                                 "fan_theta(a_min, step, k), ds, NULL, NULL, 0, &tr);"),
+    "subfan_angles_shifted": ("{ return ta + (tb - ta) * q / (M + 1); }",
+                              "{ return ta + (tb - ta) * (q - 1) / (M + 1); }"),
+    "subfan_interval_from_far_side": ("B->ta = st[j - 1]; B->fa = sm[j - 1];\n    B->tb = st[j]; B->fb = sm[j];",
+                                      "B->ta = st[j]; B->fa = sm[j];\n    B->tb = st[j + 1 < n ? j + 1 : j]; "
+                                      "B->fb = sm[j + 1 < n ? j + 1 : j];"),
+    "subfan_window_with_ends": ("interior[j - 2] && interior[j - 1] && interior[j] && interior[j + 1] &&",
+                                "1 &&"),
+    "subfan_cubic_point_dropped": ("const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);",
+                                   "const double v = inverse_poly_root(st + j - 2, sm + j - 2, 3);"),
+    "subfan_cubic_shifted": ("const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);",
+                             "const double v = inverse_poly_root(st + j - 1, sm + j - 1, 4);"),
+    "subfan_start_from_far_end": ("const int lo = fabs(B->fa) <= fabs(B->fb);",
+                                  "const int lo = fabs(B->fa) > fabs(B->fb);"),
+    "subfan_misfit_sign": ("sm[n] = R * (mod_2pi(atan2(tr.hit[1], tr.hit[0]) - phi_e) - psi_r);",
+                           "sm[n] = R * (psi_r - mod_2pi(atan2(tr.hit[1], tr.hit[0]) - phi_e));"),
 }
 
 # fast pins first; a mutant is killed by the first pin that fails
 PINS = [
+    pins.test_subfan_angles_evenly_inside,
+    pins.test_subfan_prediction_exact_for_cubic_inverse,
+    pins.test_subfan_picks_first_sign_change_and_nearer_end,
     pins.test_bilinear_exact_for_bilinear_field,
     pins.test_homogeneous_straight_rays,
     pins.test_path_matrix_invariants,
@@ -76,6 +94,7 @@ PINS = [
     pins.test_adjoint_matches_central_differences,
     pins.test_fan_start_prediction_accuracy,
     pins.test_fan_step_changes_only_the_predictions,
+    pins.test_subfan_refines_only_the_third_angle,
 ]
 
 

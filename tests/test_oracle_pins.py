@@ -523,3 +523,104 @@ def test_fan_step_changes_only_the_predictions(orc):
     assert (h["iters"] == 1).all()
     with pytest.raises(Exception):
         orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, fan_rays=64, fan_ds=-1.0)
+
+
+def test_subfan_refines_only_the_third_angle(orc):
+    """R12: after a second missed trace, a sub-fan inside the bracket predicts
+    the third angle. subfan = 0 is the plain rule exactly. On the 128^2 /
+    64-ring case with a coarse 16-ray fan (many pairs reach a third trace) the
+    sub-fan links the same rays as the straight-line start (ToF within 1e-8),
+    changes nothing before the third trace, and with 16 rays links at least
+    90 % of the pairs that make a third trace at that trace (79 % without it,
+    where the third angle is a secant step), halving the pairs that need four
+    or more."""
+    w = P.cfg_small()
+    kw = dict(tol=1e-4, fan_rays=16, fan_ds=0.5 * w.grid.h)
+    r0 = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, tol=1e-4, fan_rays=0)
+    a = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, subfan=0, **kw)
+    b = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, **kw)
+    for k in ("theta", "tof", "iters"):
+        np.testing.assert_array_equal(a[k], b[k])
+    s = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, subfan=16, **kw)
+    assert (s["status"] == 0).all()
+    np.testing.assert_allclose(s["tof"], r0["tof"], rtol=1e-8)
+    early = a["iters"] <= 2
+    np.testing.assert_array_equal(s["theta"][early], a["theta"][early])
+    np.testing.assert_array_equal(s["iters"][early], a["iters"][early])
+    third = s["iters"] >= 3
+    assert third.sum() > 1000
+    at3 = float(np.mean(s["iters"][third] == 3))
+    assert at3 >= 0.90, (at3, np.bincount(s["iters"]))
+    assert (s["iters"] >= 4).sum() <= 0.5 * (a["iters"] >= 4).sum(), (np.bincount(s["iters"]), np.bincount(a["iters"]))
+    with pytest.raises(Exception):
+        orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, subfan=-1, **kw)
+
+
+def test_subfan_angles_evenly_inside(orc):
+    """R12's sub-fan: M rays evenly spaced strictly inside the bracket, in the
+    direction from the end of negative misfit (either orientation)."""
+    for ta, tb, M in ((0.2, 1.0, 8), (3.0, 2.5, 4), (-1.0, 1.0, 1)):
+        th = orc.subfan_angles(ta, tb, M)
+        step = (tb - ta) / (M + 1)
+        np.testing.assert_allclose(np.diff(np.r_[ta, th, tb]), step, rtol=0, atol=1e-14)
+
+
+def _cubic_inverse(coef, theta):
+    """m with theta(m) = coef[0] + coef[1] m + coef[2] m^2 + coef[3] m^3 (the
+    real root; theta(m) monotone)."""
+    out = []
+    for t in np.atleast_1d(theta):
+        r = np.roots([coef[3], coef[2], coef[1], coef[0] - t])
+        out.append(r[np.argmin(np.abs(r.imag))].real)
+    return np.array(out)
+
+
+def test_subfan_prediction_exact_for_cubic_inverse(orc):
+    """The third angle is the root of the inverse cubic through the four
+    sub-fan rays around the interval: exact (to rounding) when the angle is a
+    cubic polynomial of the misfit, in both orientations. The bracket ends,
+    whose misfits may carry the Illinois halving, never enter it: here they
+    are set off the curve, and a root next to an end gives the Regula-Falsi
+    point of its interval instead."""
+    for coef, ta_m, tb_m in (((0.3, 0.8, 0.2, 0.05), -1.6, 1.2), ((0.3, -0.8, 0.2, -0.05), -1.0, 1.6)):
+        ta, tb = np.polyval(coef[::-1], ta_m), np.polyval(coef[::-1], tb_m)
+        for M in (4, 8):
+            th = orc.subfan_angles(ta, tb, M)
+            m = _cubic_inverse(coef, th)
+            seq_t = np.r_[ta, th, tb]
+            seq_m = np.r_[0.5 * ta_m, m, 0.5 * tb_m]        # ends off the curve
+            j = int(np.argmax(seq_m >= 0))
+            assert 3 <= j <= M - 1                            # four sub-fan rays around the root
+            p = orc.subfan_predict(seq_t, seq_m, np.r_[0, np.ones(M, int), 0])
+            assert p["changes_sign"]
+            assert (p["ta"], p["tb"]) == (seq_t[j - 1], seq_t[j])
+            assert abs(p["theta3"] - coef[0]) <= 1e-12, (M, p["theta3"])
+    # the root between the last sub-fan ray and the far end: linear
+    coef = (0.3, 0.8, 0.2, 0.05)
+    ta_m, tb_m = -2.0, 0.05
+    ta, tb = np.polyval(coef[::-1], ta_m), np.polyval(coef[::-1], tb_m)
+    th = orc.subfan_angles(ta, tb, 4)
+    m = _cubic_inverse(coef, th)
+    assert (m < 0).all()
+    seq_t, seq_m = np.r_[ta, th, tb], np.r_[0.5 * ta_m, m, 0.5 * tb_m]
+    p = orc.subfan_predict(seq_t, seq_m, [0, 1, 1, 1, 1, 0])
+    rf = seq_t[4] - seq_m[4] * (seq_t[5] - seq_t[4]) / (seq_m[5] - seq_m[4])
+    assert (p["ta"], p["tb"]) == (seq_t[4], seq_t[5]) and abs(p["theta3"] - rf) <= 1e-15
+
+
+def test_subfan_picks_first_sign_change_and_nearer_end(orc):
+    """Several sign changes in the sequence: the bracket is the first entry of
+    non-negative misfit from the negative end and the one before; without four
+    sub-fan rays around it the third angle is its Regula-Falsi point; the
+    secant starts from its end of smaller |misfit|; rays that did not reach the
+    ring are simply absent from the sequence."""
+    t = np.array([0.0, 0.1, 0.2, 0.3, 0.4, 0.5])
+    m = np.array([-1.0, -0.5, 0.3, -0.2, 0.6, 1.0])
+    p = orc.subfan_predict(t, m, [0, 1, 1, 1, 1, 0])
+    assert (p["ta"], p["tb"]) == (0.1, 0.2)
+    assert abs(p["theta3"] - (0.1 + 0.5 * 0.1 / 0.8)) <= 1e-15
+    assert (p["start_theta"], p["start_m"]) == (0.2, 0.3)
+    m2 = np.array([-1.0, -0.5, -0.05, 0.4, 1.0])
+    p2 = orc.subfan_predict([0.0, 0.1, 0.2, 0.3, 0.4], m2, [0, 1, 1, 1, 0])
+    assert (p2["ta"], p2["tb"]) == (0.2, 0.3) and (p2["start_theta"], p2["start_m"]) == (0.2, -0.05)
+    assert abs(p2["theta3"] - (0.2 + 0.05 * 0.1 / 0.45)) <= 1e-15    # window 1..4 reaches the end: linear
