@@ -331,6 +331,14 @@ __device__ __forceinline__ void born_heun(CellB& C, const BornRay& B, float H, f
     N.S.fy = nfy;
 }
 
+// square root by the hardware approximation (sqrt.approx.ftz.f32), for values
+// whose last bits only need to be reproducible
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // order-preserving map of float bits to unsigned (negative values included)
 __device__ __forceinline__ unsigned f2ord(float f) {
     const unsigned u = __float_as_uint(f);
@@ -377,6 +385,7 @@ __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, co
     const float al0 = dx * D0x + dy * D0y;
     const float ac0 = dx * D0y - dy * D0x;
     const int ic = B.S.ci + (oi ? 1 : 0), jc = B.S.cj + (oj ? 1 : 0);
+    const float fic = (float)ic, fjc = (float)jc;
     const float cP = c * B.P;
     // Which of the nine nodes take a candidate (bit 3 (b + 1) + a + 1), then
     // one pass per taken node: the warp runs the candidate body as often as its
@@ -417,15 +426,16 @@ __device__ __forceinline__ void born_deposit(const Geom& G, const FanArgs& A, co
         const float Qf = B.Q + al * cP;
         const float aQ = fabsf(Qf);
         const float Qc = aQ >= 1.f ? aQ : 1.f;
-        float M = B.P / Qf;
-        if (!(M >= 0.f)) M = B.P / copysignf(Qc, Qf);
+        float M = B.P * rcp_approx(Qf);
+        if (!(M >= 0.f)) M = B.P * rcp_approx(copysignf(Qc, Qf));
         const float ext = A.hf * (s * al + 0.5f * M * ac * ac) - Tc;
         const size_t node = (size_t)nj * G.nx + ni;
         atomicMin(tfirst + node, f2ord(T + ext));
-        const float ux = (float)ni - F.xt, uy = (float)nj - F.yt;
-        const float Tref = F.h_ct * sqrtf(ux * ux + uy * uy);
+        const float ux = (fic + fa) - F.xt, uy = (fjc + fb) - F.yt;   // node index sums are exact
+        // the same value for every candidate of the node from this transducer's fan
+        const float Tref = F.h_ct * sqrt_approx(ux * ux + uy * uy);
         const float score = ((T - Tref) + ext) + A.eta * ac * ac;
-        const float amp = sqrtf(c * inv_ct_h / Qc);
+        const float amp = sqrtf(c * inv_ct_h * rcp_approx(Qc));
         const unsigned long long sk = (unsigned long long)f2ord(score) << 32;
         atomicMin(near + node, sk | __float_as_uint(amp));
         // Lambda >= 0: its float bits order like its value
