@@ -39,8 +39,9 @@
 extern "C" {
 #endif
 
-#define RT_ABI_VERSION 3   /* 2: rt_options.interpolator, rt_bspline_coef, rtborn_*_abs;
-                              3: rt_options.fan_ds_mm */
+#define RT_ABI_VERSION 4   /* 2: rt_options.interpolator, rt_bspline_coef, rtborn_*_abs;
+                              3: rt_options.fan_ds_mm; 4: rt_options.subfan_rays */
+#define RT_SUBFAN_MAX 32
 
 enum rt_code {
     RT_OK = 0,
@@ -128,6 +129,23 @@ typedef struct {
                             fraction of the fan's cost. With fan_rays >= 2 the
                             ring plus max(ds_mm, fan_ds_mm) and one cell must lie
                             inside the grid. */
+    int32_t subfan_rays;   /* rt_link, rt_link_rows: 0 = off; M in [1, RT_SUBFAN_MAX]:
+                            when the second trace of a fan-started pair misses, M
+                            rays at fan_ds_mm evenly spaced inside its bracket
+                            predict the third angle (inverse cubic through the four
+                            around the root, else Regula Falsi in the narrowed
+                            bracket; reading R12, the oracle's subfan) and the link
+                            runs in rounds: one trace per pair, the second traces,
+                            the sub-fan, the rest. Only predictions change: the
+                            linked rays stay those of the straight start. On the
+                            1024^2 / 512-ring breast workload the rounds cost more
+                            than they save (77.9 against 60.7 ms with 8 rays): a
+                            round of a few hundred traces lasts as long as one ray
+                            marched by warps whose 32 lanes hold unrelated rays,
+                            while the single launch runs those chains beside the
+                            bulk. Workspace: about 0.55 KB + 8 M bytes per pair.
+                            RT_FP32_COMP and RT_BILINEAR only; rt_batch_run
+                            requires 0. */
 } rt_options;
 
 /* One ToF problem: grid, sound speed and ring (paper Sec. 3.1.1: the system
@@ -236,9 +254,12 @@ typedef struct {
 
 /* rt_rows_cap — runs per pair that hold every linked ray of the problem with
  * room to spare: 1.15 x the cells a straight diameter crosses diagonally, plus
- * 16 (1561 for a 95 mm ring on a 0.2 mm grid: 8.2 GB of runs for 261,632
- * pairs); rays that visit more cells are traced again by
- * rt_tof_adjoint_rows. Returns 0 for an invalid problem. */
+ * 16, rounded up to a multiple of 4 (1564 for a 95 mm ring on a 0.2 mm grid:
+ * 8.2 GB of runs for 261,632 pairs); rays that visit more cells are traced
+ * again by rt_tof_adjoint_rows. With a multiple of 4 and a 16-byte aligned
+ * runs array every row starts on a 16-byte boundary, which lets
+ * rt_tof_adjoint_rows read the rows with 16-byte loads (any other capacity
+ * works, with narrower loads). Returns 0 for an invalid problem. */
 int32_t rt_rows_cap(const rt_problem* prob);
 
 /*

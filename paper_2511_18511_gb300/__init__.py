@@ -113,7 +113,8 @@ DEFAULT_FAN = 256
 
 
 def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, block_threads=0,
-          step_unroll=0, blocks_per_sm=0, integrator="rk4", interpolator="bilinear", fan_ds=0.0) -> _L.RtOptions:
+          step_unroll=0, blocks_per_sm=0, integrator="rk4", interpolator="bilinear", fan_ds=0.0,
+          subfan_rays=0) -> _L.RtOptions:
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
     if integrator not in INTEGRATORS:
@@ -122,21 +123,23 @@ def _opts(ds, tol=1e-4, max_iter=30, precision="fp32c", fan_rays=DEFAULT_FAN, bl
         raise ValueError(f"interpolator must be one of {sorted(INTERPOLATORS)}")
     return _L.RtOptions(PRECISIONS[precision], int(max_iter), float(ds), float(tol), int(fan_rays),
                         int(block_threads), int(step_unroll), int(blocks_per_sm), INTEGRATORS[integrator],
-                        INTERPOLATORS[interpolator], float(fan_ds))
+                        INTERPOLATORS[interpolator], float(fan_ds), int(subfan_rays))
 
 
 def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, precision: str = "fp32c",
             theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
             ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
             fan_rays: int = DEFAULT_FAN, integrator: str = "rk4", interpolator: str = "bilinear",
-            fan_ds: float = 0.0) -> dict:
+            fan_ds: float = 0.0, subfan_rays: int = 0) -> dict:
     """Link every pair (shooting method, paper Sec. 3.4) and return the linked
     angles, travel times (us), interceptions (mm), per-pair status and traces.
     Cold starts (theta0 None / NaN) use a fan of fan_rays rays per emitter, or
     the straight line to the receiver with fan_rays = 0; the fan's rays are
     traced at step fan_ds (0 = ds), their launch angles follow ds. integrator: "rk4" or
     "heun" (the paper's default stepper); interpolator: "bilinear" or "bspline"
-    (the interpolating cubic B-spline, Sec. 3.3.1)."""
+    (the interpolating cubic B-spline, Sec. 3.3.1). subfan_rays > 0: link in
+    rounds, with that many rays refining the third angle of a fan-started pair
+    whose second trace missed."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     n = prob.n_pairs
@@ -151,7 +154,8 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     else:
         out["theta"].copy_(theta0)
     ps = prob.struct(c)
-    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator, interpolator=interpolator, fan_ds=fan_ds)
+    o = _opts(ds, tol, max_iter, precision, fan_rays, integrator=integrator, interpolator=interpolator, fan_ds=fan_ds,
+              subfan_rays=subfan_rays)
     _L.check(ctx.h, ctx.lib.rt_link(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                     _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), _stream(stream)))
     return out
@@ -184,7 +188,7 @@ class Rows:
 def rt_link_rows(prob: Problem, ds: float, rows: Rows, tol: float = 1e-4, max_iter: int = 30,
                  theta0: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
                  ctx: Optional[Context] = None, stream=None, out: Optional[dict] = None,
-                 fan_rays: int = DEFAULT_FAN, fan_ds: float = 0.0) -> dict:
+                 fan_rays: int = DEFAULT_FAN, fan_ds: float = 0.0, subfan_rays: int = 0) -> dict:
     """rt_link (FP32-compensated, bilinear) that also records the rows of the
     linked rays into `rows` for rt_tof_adjoint_rows."""
     ctx = ctx or default_context(prob.c.device.index)
@@ -201,7 +205,7 @@ def rt_link_rows(prob: Problem, ds: float, rows: Rows, tol: float = 1e-4, max_it
     else:
         out["theta"].copy_(theta0)
     ps = prob.struct(c)
-    o = _opts(ds, tol, max_iter, "fp32c", fan_rays, fan_ds=fan_ds)
+    o = _opts(ds, tol, max_iter, "fp32c", fan_rays, fan_ds=fan_ds, subfan_rays=subfan_rays)
     rs = rows.struct()
     _L.check(ctx.h, ctx.lib.rt_link_rows(ctx.h, C.byref(ps), C.byref(o), _ptr(out["theta"]), _ptr(out["tof"]),
                                          _ptr(out["hit"]), _ptr(out["status"]), _ptr(out["iters"]), C.byref(rs),

@@ -26,7 +26,7 @@ EXPORTED = [
     "rt_tof_adjoint_rows",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_TF32X3 = 0, 1
-ABI_VERSION = 3   # layout of RtOptions below
+ABI_VERSION = 4   # layout of RtOptions below
 
 
 class RtGrid(C.Structure):
@@ -38,7 +38,7 @@ class RtOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("ds_mm", C.c_double),
                 ("tol_mm", C.c_double), ("fan_rays", C.c_int32), ("block_threads", C.c_int32),
                 ("step_unroll", C.c_int32), ("blocks_per_sm", C.c_int32), ("integrator", C.c_int32),
-                ("interpolator", C.c_int32), ("fan_ds_mm", C.c_double)]
+                ("interpolator", C.c_int32), ("fan_ds_mm", C.c_double), ("subfan_rays", C.c_int32)]
 
 
 class RtProblem(C.Structure):

@@ -133,6 +133,37 @@ int ensure_fan(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, cudaS
     return RT_OK;
 }
 
+// Workspace of the R12 rounds (opt->subfan_rays > 0): two set-aside state
+// arrays, the sub-fan misfits and the round counters, 256-byte aligned parts.
+static int ensure_link_ws(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, cudaStream_t s,
+                          rt::LinkWork* W) {
+    W->subfan = 0;
+    if (opt->subfan_rays < 0 || opt->subfan_rays > RT_SUBFAN_MAX)
+        return fail(ctx, RT_EINVAL, "subfan_rays must be in [0, RT_SUBFAN_MAX]");
+    if (opt->subfan_rays == 0 || prob->n_pairs == 0) return RT_OK;
+    if (opt->precision != RT_FP32_COMP || opt->interpolator != RT_BILINEAR)
+        return fail(ctx, RT_EINVAL, "subfan_rays needs RT_FP32_COMP and RT_BILINEAR");
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t np = (size_t)prob->n_pairs;
+    const size_t st = al(rt::link_state_bytes() * np), sb = al(sizeof(double) * np * (size_t)opt->subfan_rays);
+    const size_t need = 2 * st + sb + 256;
+    if (ctx->link_ws_bytes < need) {
+        if (capturing(s)) return fail(ctx, RT_EINVAL, "link workspace too small during stream capture");
+        if (ctx->link_ws) cudaFree(ctx->link_ws);
+        ctx->link_ws = nullptr;
+        ctx->link_ws_bytes = 0;
+        if (cudaMalloc(&ctx->link_ws, need) != cudaSuccess) return fail(ctx, RT_ENOMEM, "link workspace");
+        ctx->link_ws_bytes = need;
+    }
+    char* b = (char*)ctx->link_ws;
+    W->subfan = opt->subfan_rays;
+    W->aside_a = (rt::LinkState*)b;
+    W->aside_b = (rt::LinkState*)(b + st);
+    W->sub = (double*)(b + 2 * st);
+    W->ctr = (int*)(b + 2 * st + sb);
+    return RT_OK;
+}
+
 }  // namespace
 
 namespace rt {
@@ -240,6 +271,7 @@ void rt_ctx_destroy(rt_ctx* ctx) {
     if (ctx->scan_tmp) cudaFree(ctx->scan_tmp);
     if (ctx->fan) cudaFree(ctx->fan);
     if (ctx->fan_need) cudaFree(ctx->fan_need);
+    if (ctx->link_ws) cudaFree(ctx->link_ws);
     if (ctx->txphi) cudaFree(ctx->txphi);
     if (ctx->batch_ws) cudaFree(ctx->batch_ws);
     for (void* p : {ctx->born_field, ctx->born_bsf, ctx->born_keys, (void*)ctx->born_idx, ctx->born_E, ctx->born_W, ctx->born_aux,
@@ -268,11 +300,14 @@ int rt_link(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, double* 
     if (rc) return rc;
     rc = ensure_fan(ctx, prob, opt, s);
     if (rc) return rc;
+    rt::LinkWork W;
+    rc = ensure_link_ws(ctx, prob, opt, s, &W);
+    if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
     e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
                         status, iters, ctx->counters, ctx->queue, opt->fan_rays, opt->fan_ds_mm, ctx->fan,
-                        ctx->fan_need, s);
+                        ctx->fan_need, s, nullptr, W.subfan ? &W : nullptr);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
 }
 
@@ -280,7 +315,7 @@ int32_t rt_rows_cap(const rt_problem* prob) {
     if (!prob || !(prob->grid.h_mm > 0) || !(prob->ring_radius_mm > 0)) return 0;
     const double cells = 1.15 * std::sqrt(2.0) * 2.0 * prob->ring_radius_mm / prob->grid.h_mm + 16.0;
     if (!(cells < 1e9)) return 0;
-    return (int32_t)std::ceil(cells);
+    return ((int32_t)std::ceil(cells) + 3) & ~3;   // a multiple of 4: rows start on 16-byte boundaries
 }
 
 static int check_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, const rt_rows* rows) {
@@ -304,12 +339,15 @@ int rt_link_rows(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, dou
     if (rc) return rc;
     rc = ensure_fan(ctx, prob, opt, s);
     if (rc) return rc;
+    rt::LinkWork W;
+    rc = ensure_link_ws(ctx, prob, opt, s, &W);
+    if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(ctx->counters, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
     const rt::RowRec rec{rows->runs, rows->len, rows->cap};
     e = rt::launch_link(G, ctx->field, opt->precision, opt->tol_mm, opt->max_iter, theta_io, tof_us, hit_xy_mm,
                         status, iters, ctx->counters, ctx->queue, opt->fan_rays, opt->fan_ds_mm, ctx->fan,
-                        ctx->fan_need, s, &rec);
+                        ctx->fan_need, s, &rec, W.subfan ? &W : nullptr);
     return e == cudaSuccess ? RT_OK : cuda_fail(ctx, e, "link kernel");
 }
 

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             L.phase = 0;
             L.psi_at_lo = 0.0;
             L.best_d2 = CUDART_INF;
-            L.fan_k0 = -1;
+            L.fan_k0 = -2;
             if (fan_rays >= 2 && d.fan && isnan(tin)) {
                 int e, r;
                 pair_of(G, k, e, r);
@@ -309,6 +309,7 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
         return rt::set_error(ctx, RT_EINVAL, "rt_batch_run samples bilinearly (interpolator RT_BILINEAR)");
     if (opt->fan_rays == 1 || opt->fan_rays < 0 || opt->fan_rays > 65536)
         return rt::set_error(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
+    if (opt->subfan_rays != 0) return rt::set_error(ctx, RT_EINVAL, "rt_batch_run links in one launch: subfan_rays must be 0");
     const int block = opt->block_threads ? opt->block_threads : 128;
     const int unroll = opt->step_unroll ? opt->step_unroll : 1;
     const int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm

@@ -21,6 +21,8 @@ struct rt_ctx {
     double* fan = nullptr;          // [n_tx * fan_rays] interception angles of the emitter fans
     int* fan_need = nullptr;        // [n_tx] emitters with at least one cold-start pair
     size_t fan_cap = 0, need_cap = 0;
+    void* link_ws = nullptr;        // link rounds with the R12 sub-fan (rt::LinkWork)
+    size_t link_ws_bytes = 0;
     double* txphi = nullptr;        // [n_tx] polar angles of the transducers (NaN = off the ring)
     size_t txphi_cap = 0;
     // batch workspace (rt_batch_run): packed fields, fans, flags
@@ -70,12 +72,25 @@ bool stream_capturing(cudaStream_t s);
 cudaError_t launch_pack(const rt_grid& g, const double* c_mps, void* field, int* dflag, int prec,
                         cudaStream_t s);
 struct RowRec;
+struct LinkState;
+// Workspace of a link split into rounds with the R12 sub-fan (subfan rays per
+// pair, > 0): two set-aside state arrays of n_pairs entries, the sub-fan
+// misfits [n_pairs * subfan] and five int counters.
+struct LinkWork {
+    int subfan;
+    LinkState* aside_a;
+    LinkState* aside_b;
+    double* sub;
+    int* ctr;
+};
+size_t link_state_bytes();
 // fan_ds: the fan's tracing step (0 = G.ds); its launch angles follow G.ds.
 // rec: record the rows of the system matrix (FP32-compensated bilinear only).
+// W (subfan > 0): link in rounds (one trace, a second, the sub-fan, the rest).
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
                         unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,
-                        int* fan_need, cudaStream_t s, const RowRec* rec = nullptr);
+                        int* fan_need, cudaStream_t s, const RowRec* rec = nullptr, const LinkWork* W = nullptr);
 // adjoint from recorded rows (pairs without one traced again), then the chain rule
 cudaError_t launch_adjoint_rows(const Geom& G, const void* field, const double* theta, const double* g_tof,
                                 const double* tof_ref, const double* c_mps, const RowRec& rec, double* g_c,

@@ -70,7 +70,8 @@ struct LinkState {
     double psi_at_lo, next;
     int k, n_eval, phase, last, e0_flagged;
     int fan_k0;                      // fan start: interval between rays fan_k0, fan_k0 + 1 whose
-                                     // four surrounding rays are usable for the second angle; else -1
+                                     // four surrounding rays are usable for the second angle; else -1;
+                                     // -2: the pair did not start from the fan
     // adjoint retrace of the batched kernel (read on flushes only)
     double* adj_g;
     double adj_w;
@@ -346,6 +347,73 @@ __device__ inline void fan_start(const Geom& G, LinkState& L, const double* __re
     L.th0 = th0;
     L.next = th0;
     L.phase = 2;
+}
+
+// ---------------------------------------------------------------- R12 sub-fan
+
+constexpr int kSubfanMax = 32;   // RT_SUBFAN_MAX
+
+// One round of a linking launch split into rounds (R12 schedule): pairs from
+// the work queue or resumed from the states the previous round set aside;
+// with stop_after > 0 a pair that has made that many traces without finishing
+// is set aside (its state saved, its next angle already chosen).
+struct LinkRound {
+    int stop_after;
+    LinkState* aside_out;
+    int* n_out;
+    const LinkState* aside_in;   // non-null: resume these states instead of the queue
+    const int* n_in;
+    const double* sub;           // R12 sub-fan misfits of the resumed pairs [slot][sub_m], or null
+    int sub_m;
+};
+
+// Angle of sub-fan ray q = 1..M, evenly spaced strictly inside the bracket
+// from its end of negative misfit.
+__device__ __forceinline__ double subfan_theta(const LinkState& L, int q, int M) {
+    return L.ta + (L.tb - L.ta) * q / (M + 1);
+}
+
+// R12: a fan-started pair whose second trace missed, with the misfits m[q-1]
+// of its M sub-fan rays (NaN: the ray did not reach the ring). In the
+// sequence (ta, the sub-fan rays that reached the ring, tb) the first entry of
+// non-negative misfit and the one before it become the bracket (Illinois
+// state restarted); the third angle is the root of the inverse cubic through
+// the four sub-fan rays around that interval (all four sub-fan rays, misfits
+// strictly increasing, root inside), else its Regula-Falsi point; the secant
+// starts from the interval end of smaller |misfit|.
+static __device__ __noinline__ void subfan_apply(LinkState& L, const double* __restrict__ m, int M) {
+    double st[kSubfanMax + 2], sm[kSubfanMax + 2];
+    bool in[kSubfanMax + 2];
+    int n = 0;
+    st[n] = L.ta; sm[n] = L.fa; in[n++] = false;
+    for (int q = 1; q <= M; ++q) {
+        const double v = m[q - 1];
+        if (isnan(v)) continue;
+        st[n] = subfan_theta(L, q, M); sm[n] = v; in[n++] = true;
+    }
+    st[n] = L.tb; sm[n] = L.fb; in[n++] = false;
+    int j = 1;
+    while (j < n - 1 && sm[j] < 0) ++j;
+    L.ta = st[j - 1]; L.fa = sm[j - 1];
+    L.tb = st[j]; L.fb = sm[j];
+    L.last = 0;
+    double th = L.ta - L.fa * (L.tb - L.ta) / (L.fb - L.fa);
+    if (j - 2 >= 0 && j + 1 < n && in[j - 2] && in[j - 1] && in[j] && in[j + 1] && sm[j - 2] < sm[j - 1] &&
+        sm[j - 1] < sm[j] && sm[j] < sm[j + 1]) {
+        // inverse cubic through the four rays, Lagrange form at misfit 0
+        double v = 0.0;
+        for (int a = 0; a < 4; ++a) {
+            double l = 1.0;
+            for (int b = 0; b < 4; ++b)
+                if (b != a) l *= (0.0 - sm[j - 2 + b]) / (sm[j - 2 + a] - sm[j - 2 + b]);
+            v += l * st[j - 2 + a];
+        }
+        if (v > fmin(L.ta, L.tb) && v < fmax(L.ta, L.tb)) th = v;
+    }
+    const bool lo = fabs(L.fa) <= fabs(L.fb);
+    L.cur_th = L.prev_th = lo ? L.ta : L.tb;
+    L.cur_m = L.prev_m = lo ? L.fa : L.fb;
+    L.next = th;
 }
 
 // Work order of the persistent kernel. For the all-pairs list, queue slot q

@@ -185,13 +185,14 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I
 template <typename T, int I, bool REC> struct LinkBlocks { static constexpr int v = Occ<T, I>::blocks; };
 template <typename T, int I> struct LinkBlocks<T, I, true> { static constexpr int v = 5; };
 
-template <typename T, int I, bool REC>
+template <typename T, int I, bool REC, bool ROUNDS = false>
 __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(Geom G, const typename Samp<T, I>::Field* __restrict__ F,
                                                      double tol, int max_iter, double* theta, double* tof,
                                                      double* hit, int32_t* status, int32_t* iters,
                                                      unsigned long long* counters, int* queue, int fan_rays,
-                                                     const double* __restrict__ fan, RowRec rec) {
+                                                     const double* __restrict__ fan, RowRec rec, LinkRound rd) {
     __shared__ LinkState sh[kLinkBlock];
+    const int n_in = (ROUNDS && rd.aside_in) ? *rd.n_in : 0;
     LinkState& L = sh[threadIdx.x];
     auto C = make_cell<T, I>(G, F);
     TraceState<T> ts;
@@ -206,6 +207,16 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
     unsigned n_ok = 0, n_max = 0, n_cap = 0, n_bad = 0;
     bool active = false;
     for (;;) {
+        if (ROUNDS && !active && rd.aside_in) {
+            // resume a pair set aside by the previous round (R12: refined first)
+            const int slot = fetch_pair(queue);
+            if (slot >= n_in) break;
+            L = rd.aside_in[slot];
+            if (rd.sub && L.fan_k0 >= -1 && L.n_eval == 2) subfan_apply(L, rd.sub + (size_t)slot * rd.sub_m, rd.sub_m);
+            if constexpr (REC) ns.begin(rec.runs + (size_t)L.k * rec.cap);
+            trace_begin(ts, G, L.xe, L.ye, L.next);
+            active = true;
+        }
         if (!active) {
             const int qslot = fetch_pair(queue);
             if (qslot >= G.n_pairs) break;
@@ -236,7 +247,7 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
             L.phase = 0;
             L.psi_at_lo = 0.0;
             L.best_d2 = CUDART_INF;
-            L.fan_k0 = -1;
+            L.fan_k0 = -2;
             if (fan_rays >= 2 && isnan(tin)) {
                 int e, r;
                 pair_of(G, k, e, r);
@@ -267,6 +278,9 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
                 n_ok += st == RT_RAY_OK;
                 n_max += st == RT_RAY_MAXITER;
                 n_cap += st == RT_RAY_STEPCAP;
+                active = false;
+            } else if (ROUNDS && rd.stop_after && L.n_eval >= rd.stop_after) {
+                rd.aside_out[atomicAdd(rd.n_out, 1)] = L;   // next angle already chosen
                 active = false;
             } else {
                 if constexpr (REC) ns.begin(rec.runs + (size_t)L.k * rec.cap);
@@ -346,25 +360,92 @@ cudaError_t launch_fan(const Geom& G, double fan_ds, const void* field, int prec
     return cudaGetLastError();
 }
 
-template <typename T, int I, bool REC = false>
+template <typename T, int I, bool REC = false, bool ROUNDS = false>
 static void link_impl(const Geom& G, const void* field, double tol, int max_iter, double* theta, double* tof,
                       double* hit, int32_t* status, int32_t* iters, unsigned long long* counters, int* queue,
-                      int fan_rays, double* fan, int slot, cudaStream_t s, const RowRec& rec = RowRec{}) {
-    const int nb = min(persistent_blocks(k_link<T, I, REC>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
-    k_link<T, I, REC><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, tol, max_iter, theta,
-                                                tof, hit, status, iters, counters, queue, fan_rays, fan, rec);
+                      int fan_rays, double* fan, int slot, cudaStream_t s, const RowRec& rec = RowRec{},
+                      const LinkRound& rd = LinkRound{}) {
+    const int nb = min(persistent_blocks(k_link<T, I, REC, ROUNDS>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+    k_link<T, I, REC, ROUNDS><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, tol, max_iter,
+                                                        theta, tof, hit, status, iters, counters, queue, fan_rays,
+                                                        fan, rec, rd);
+}
+
+size_t link_state_bytes() { return sizeof(LinkState); }
+
+// R12 sub-fan rays of the pairs set aside after their second trace: item
+// (slot, q) traces ray q of pair slot at the fan's step (Gf) and stores its
+// misfit (NaN when it does not reach the ring, or for a pair that was not
+// fan-started).
+template <typename T, int I>
+__global__ void __launch_bounds__(kBlock) k_subfan(Geom Gf, const typename Samp<T, I>::Field* __restrict__ F,
+                                                   const LinkState* __restrict__ aside, const int* n_aside, int M,
+                                                   double* sub, unsigned long long* counters) {
+    const long long items = (long long)(*n_aside) * M;
+    long long steps = 0;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int slot = (int)(it / M), q = (int)(it - (long long)slot * M) + 1;
+        const LinkState& L = aside[slot];
+        double v = nan("");
+        if (L.fan_k0 >= -1 && L.n_eval == 2) {
+            auto C = make_cell<T, I>(Gf, F);
+            NoSink ns;
+            const TraceOut o = trace_ray<T>(C, Gf, L.xe, L.ye, subfan_theta(L, q, M), L.xe, L.ye, ns);
+            if (!(o.flags & 3)) v = Gf.R * (mod_2pi(atan2(o.hy, o.hx) - L.phi_e) - L.psi_r);
+            steps += o.steps;
+        }
+        sub[(size_t)slot * M + (q - 1)] = v;
+    }
+    __syncwarp();
+    unsigned long long v = (unsigned long long)steps;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&counters[7], v);
+}
+
+template <typename T, int I, bool REC>
+static cudaError_t link_rounds(const Geom& G, const void* field, double tol, int max_iter, double* theta,
+                               double* tof, double* hit, int32_t* status, int32_t* iters,
+                               unsigned long long* counters, int fan_rays, double fan_ds, double* fan, int slot,
+                               const LinkWork& W, cudaStream_t s, const RowRec& rec) {
+    // counters: queues of the three rounds, then the two set-aside counts
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 5 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    LinkRound r1{1, W.aside_a, W.ctr + 3, nullptr, nullptr, nullptr, 0};
+    link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr, fan_rays,
+                               fan, slot, s, rec, r1);
+    LinkRound r2{2, W.aside_b, W.ctr + 4, W.aside_a, W.ctr + 3, nullptr, 0};
+    link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr + 1,
+                               fan_rays, fan, slot, s, rec, r2);
+    const Geom Gf = with_step(G, fan_ds > 0 ? fan_ds : G.ds);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_subfan<T, I><<<(unsigned)(sms > 0 ? sms * 8 : 1216), kBlock, 0, s>>>(
+        Gf, (const typename Samp<T, I>::Field*)field, W.aside_b, W.ctr + 4, W.subfan, W.sub, counters);
+    LinkRound r3{0, nullptr, nullptr, W.aside_b, W.ctr + 4, W.sub, W.subfan};
+    link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr + 2,
+                               fan_rays, fan, slot, s, rec, r3);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
                         unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,
-                        int* fan_need, cudaStream_t s, const RowRec* rec) {
+                        int* fan_need, cudaStream_t s, const RowRec* rec, const LinkWork* W) {
     if (G.n_pairs == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (fan_rays >= 2) {
         e = launch_fan(G, fan_ds, field, prec, fan_rays, theta, fan, fan_need, counters, s);
         if (e != cudaSuccess) return e;
+    }
+    if (W && W->subfan > 0) {   // R12 rounds: FP32-compensated, bilinear (checked by the caller)
+        if (rec)
+            return link_rounds<float, RT_BILINEAR, true>(G, field, tol, max_iter, theta, tof, hit, status, iters,
+                                                         counters, fan_rays, fan_ds, fan, 12, *W, s, *rec);
+        return link_rounds<float, RT_BILINEAR, false>(G, field, tol, max_iter, theta, tof, hit, status, iters,
+                                                      counters, fan_rays, fan_ds, fan, 13, *W, s, RowRec{});
     }
     if (rec) {   // recording: FP32-compensated, bilinear (checked by the caller)
         link_impl<float, RT_BILINEAR, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, queue,
@@ -459,42 +540,79 @@ __global__ void k_adjoint_finish(double* g, const double* __restrict__ c_mps, in
     }
 }
 
-// Adjoint from recorded rows: a warp per pair (in the work-queue order), its
-// lanes striding over the pair's runs, each run's four weights scaled by w in
-// FP32 and added with FP64 atomics exactly as AdjSink::flush adds them; pairs
-// without a row are traced again by lane 0.
+// Adjoint from recorded rows: a warp per pair (in the work-queue order). The
+// warp stages kRowSeg consecutive runs of its row in shared memory with
+// coalesced loads (16-byte loads where every row starts on a 16-byte
+// boundary), then lane l takes runs l, l + 32, ...: neighbouring lanes hold
+// neighbouring cells of the ray, so the FP64 atomics of one instruction share
+// sectors. Each weight is w * (FP32 run weight) in FP32, widened to FP64, as
+// AdjSink::flush forms it. Pairs without a row are left to
+// k_adjoint_unrecorded.
+constexpr int kRowSeg = 128;                   // runs per warp segment (2560 bytes)
+
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_adjoint_rows(Geom G, const typename Samp<T, RT_BILINEAR>::Field* __restrict__ F,
-                                                         const double* theta, const double* g_tof,
-                                                         const double* tof_ref, double* g, RowRec rec) {
+__global__ void __launch_bounds__(kBlock) k_adjoint_rows(Geom G, const double* g_tof, const double* tof_ref,
+                                                         double* g, RowRec rec, int vec) {
+    __shared__ float4 seg_buf[kBlock / 32][kRowSeg * 20 / 16];
     const long long wid = (blockIdx.x * (long long)kBlock + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= G.n_pairs) return;
     const int k = queue_pair(G, (int)wid);
+    const int n = rec.len[k];
+    if (n <= 0) return;
     const double wd = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
     if (wd == 0.0 || !isfinite(wd)) return;
     const T w = (T)wd;
-    const int n = rec.len[k];
-    if (n >= 0) {
-        const rt_run* row = rec.runs + (size_t)k * rec.cap;
-        for (int r = lane; r < n; r += 32) {
-            const rt_run u = row[r];
-            double* p = g + u.node;
-            atomicAdd(p, to_double(w * (T)u.w00));
-            atomicAdd(p + 1, to_double(w * (T)u.w10));
-            atomicAdd(p + G.nx, to_double(w * (T)u.w01));
-            atomicAdd(p + G.nx + 1, to_double(w * (T)u.w11));
+    const rt_run* row = rec.runs + (size_t)k * rec.cap;
+    const int nx = G.nx;
+    float4* buf = seg_buf[threadIdx.x >> 5];
+    const float* bw = reinterpret_cast<const float*>(buf);
+    for (int base = 0; base < n; base += kRowSeg) {
+        const int cnt = min(kRowSeg, n - base);
+        __syncwarp();
+        if (vec) {
+            // the row's capacity is a multiple of 4 runs (80 bytes), so the
+            // rounded-up segment stays inside the row
+            const float4* src = reinterpret_cast<const float4*>(row + base);
+            const int nv = (cnt * 20 + 15) >> 4;
+            for (int q = lane; q < nv; q += 32) buf[q] = src[q];
+        } else {
+            const float* src = reinterpret_cast<const float*>(row + base);
+            float* dst = reinterpret_cast<float*>(buf);
+            for (int q = lane; q < cnt * 5; q += 32) dst[q] = src[q];
         }
-    } else if (lane == 0) {
-        LinkCtx X;
-        if (!setup_pair(G, k, X)) return;
-        auto C = make_cell<T, RT_BILINEAR>(G, F);
-        AdjSink<T> sink;
-        sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
-        sink.init();
-        sink.w = w;
-        trace_ray<T>(C, G, X.xe, X.ye, theta[k], X.xr, X.yr, sink);
+        __syncwarp();
+        for (int r = lane; r < cnt; r += 32) {
+            // 5-word runs at a lane stride of 5 words: distinct banks
+            double* p = g + __float_as_int(bw[r * 5]);
+            atomicAdd(p, to_double(w * (T)bw[r * 5 + 1]));
+            atomicAdd(p + 1, to_double(w * (T)bw[r * 5 + 2]));
+            atomicAdd(p + nx, to_double(w * (T)bw[r * 5 + 3]));
+            atomicAdd(p + nx + 1, to_double(w * (T)bw[r * 5 + 4]));
+        }
     }
+}
+
+// The pairs whose row was not recorded (len < 0: a row longer than the
+// capacity, or a pair the link did not finish on its reported ray), traced
+// again at their angle, a thread per pair.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_adjoint_unrecorded(Geom G,
+                                                               const typename Samp<T, RT_BILINEAR>::Field* __restrict__ F,
+                                                               const double* theta, const double* g_tof,
+                                                               const double* tof_ref, double* g, const int32_t* len) {
+    const long long k = blockIdx.x * (long long)kBlock + threadIdx.x;
+    if (k >= G.n_pairs || len[k] >= 0) return;
+    const double wd = g_tof[k] - (tof_ref ? tof_ref[k] : 0.0);
+    if (wd == 0.0 || !isfinite(wd)) return;
+    LinkCtx X;
+    if (!setup_pair(G, (int)k, X)) return;
+    auto C = make_cell<T, RT_BILINEAR>(G, F);
+    AdjSink<T> sink;
+    sink.g = g; sink.nx = G.nx; sink.ny = G.ny;
+    sink.init();
+    sink.w = (T)wd;
+    trace_ray<T>(C, G, X.xe, X.ye, theta[k], X.xr, X.yr, sink);
 }
 
 cudaError_t launch_adjoint_rows(const Geom& G, const void* field, const double* theta, const double* g_tof,
@@ -505,8 +623,13 @@ cudaError_t launch_adjoint_rows(const Geom& G, const void* field, const double* 
     if (e != cudaSuccess) return e;
     if (G.n_pairs > 0) {
         const long long threads = (long long)G.n_pairs * 32;
-        k_adjoint_rows<float><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-            G, (const typename Samp<float, RT_BILINEAR>::Field*)field, theta, g_tof, tof_ref, g_c, rec);
+        const int vec = ((reinterpret_cast<uintptr_t>(rec.runs) & 15) == 0 && (rec.cap & 3) == 0) ? 1 : 0;
+        k_adjoint_rows<float><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, g_tof, tof_ref, g_c,
+                                                                                          rec, vec);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_adjoint_unrecorded<float><<<(unsigned)((G.n_pairs + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+            G, (const typename Samp<float, RT_BILINEAR>::Field*)field, theta, g_tof, tof_ref, g_c, rec.len);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_without_gpu(lib):
     from paper_2511_18511_gb300 import _lib
-    assert lib.rt_version() == _lib.ABI_VERSION == 3
+    assert lib.rt_version() == _lib.ABI_VERSION == 4
 
 
 def test_option_checks_without_gpu(lib):
@@ -50,6 +50,21 @@ def test_option_checks_without_gpu(lib):
     for integ, interp in ((9, 0), (0, 1), (0, 7)):
         o = _lib.RtOptions(1, 30, 0.1, 1e-4, 0, 0, 0, 0, integ, interp)
         assert lib.rt_tof_forward_noalloc(ctypes.byref(prob), ctypes.byref(o), None, None, None, None) == _lib.RT_EINVAL
+
+
+def test_rows_capacity_without_gpu(lib):
+    """rt_rows_cap: 1.15 x the diagonal cells of a diameter plus 16, rounded up
+    to a multiple of 4 (rows on 16-byte boundaries); 0 for an invalid problem."""
+    import math
+    from paper_2511_18511_gb300 import _lib
+    for n, h, R in ((1024, 0.2, 95.0), (128, 0.5, 30.0), (512, 0.2, 45.0), (32, 0.5, 7.0)):
+        prob = _lib.RtProblem(_lib.RtGrid(n, n, h, 0.0, 0.0), None, 2, None, R, 0, None)
+        cap = lib.rt_rows_cap(ctypes.byref(prob))
+        raw = math.ceil(1.15 * math.sqrt(2.0) * 2.0 * R / h + 16.0)
+        assert cap % 4 == 0 and raw <= cap < raw + 4, (n, cap, raw)
+    assert lib.rt_rows_cap(ctypes.byref(_lib.RtProblem(_lib.RtGrid(8, 8, 1.0, 0.0, 0.0), None, 2, None, 0.0,
+                                                        0, None))) == 0
+    assert lib.rt_rows_cap(None) == 0
 
 
 def test_null_arguments_are_rejected_without_gpu(lib):

@@ -223,3 +223,35 @@ def test_recorded_rows_breast(breast, rt):
           f"rows missing {(ln < 0).sum()}, gradient vs rt_tof_adjoint max rel {rel:.2e}")
     assert (ln > 0).all()
     assert rel <= 1e-11
+
+
+def test_link_rounds_breast(breast, rt):
+    """The bench's step linked in rounds with the R12 sub-fan (8 rays) on the
+    breast workload against the single launch: every pair linked, the first
+    two traces of every pair as in the single launch, travel times within the
+    FP32 linking bar (the same rays), at most as many traces per pair on
+    average, and the gradient from the recorded rows equal to the retracing
+    adjoint at the linked angles."""
+    w, prob = breast
+    one = rt.rt_link(prob, w.ds, tol=w.tol, fan_rays=768, fan_ds=0.1)
+    it1 = one["iters"].clone()
+    rows = rt.Rows.create(prob)
+    out = rt.rt_link_rows(prob, w.ds, rows, tol=w.tol, fan_rays=768, fan_ds=0.1, subfan_rays=8)
+    ok, counts = rt.rt_status_counts()
+    assert ok and counts[0] == prob.n_pairs
+    it = out["iters"]
+    early = it1 <= 2
+    assert torch.equal(it[early], it1[early])
+    rel = float((out["tof"] / one["tof"] - 1).abs().max())
+    t_ref = out["tof"] * 0.999
+    g = rt.rt_tof_adjoint_rows(prob, rows, out["theta"], out["tof"], w.ds, tof_ref=t_ref)
+    g_tr = rt.rt_tof_adjoint(prob, out["theta"], out["tof"], w.ds, tof_ref=t_ref)
+    grel = float((g - g_tr).abs().max() / g_tr.abs().max())
+    h = torch.bincount(it.long()).tolist()
+    h1 = torch.bincount(it1.long()).tolist()
+    print(f"breast rounds with sub-fan: traces/pair {it.float().mean().item():.4f} {h} (single launch "
+          f"{it1.float().mean().item():.4f} {h1}); ToF vs single launch max rel {rel:.2e}; "
+          f"gradient rows vs retrace {grel:.2e}")
+    assert rel <= 2e-6
+    assert it.float().mean() <= it1.float().mean() + 1e-3
+    assert (rows.len >= 0).all() and grel <= 1e-11

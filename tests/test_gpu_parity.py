@@ -123,6 +123,51 @@ def test_link_with_coarse_fan_matches_oracle(rt, orc, P, prec):
         assert abs(it.mean() - it_ref.mean()) <= 0.01
 
 
+@pytest.mark.parametrize("subfan", [8, 16])
+def test_link_rounds_with_subfan_match_oracle(rt, orc, P, subfan):
+    """R12 on the GPU: the link in rounds (one trace per pair, the second
+    traces, the sub-fan, the rest) with a coarse 16-ray fan, so that many
+    pairs reach a third trace, against the oracle with the same sub-fan: every
+    pair links, ToF and endpoints within the linking bars, the traces per pair
+    as the oracle's (FP32 may move a few pairs by one trace); against the GPU's
+    single launch without the sub-fan, the same rays and the same first two
+    traces; with recorded rows, the same link and an adjoint from the rows that
+    equals the retracing adjoint at the linked angles."""
+    w = P.cfg_small()
+    kw = dict(tol=w.tol, fan_rays=16, fan_ds=0.5 * w.grid.h)
+    ref = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, subfan=subfan, **kw)
+    prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
+    r = rt.rt_link(prob, w.ds, subfan_rays=subfan, **kw)
+    ok, counts = rt.rt_status_counts()
+    assert ok and counts[0] == prob.n_pairs
+    rel = np.abs(_np(r["tof"]) / ref["tof"] - 1)
+    assert rel.max() <= TOF_RTOL, rel.max()
+    pairs = P.all_pairs(w.n_tx)
+    assert np.linalg.norm(_np(r["hit"]) - w.tx[pairs[:, 1]], axis=1).max() <= w.tol
+    it, it_ref = _np(r["iters"]), ref["iters"]
+    assert (it >= 3).sum() > 1000
+    same = np.mean(it == it_ref)
+    print(f"[subfan {subfan}] GPU rounds vs oracle: max ToF rel err {rel.max():.3e}; traces/pair {it.mean():.4f} "
+          f"(oracle {it_ref.mean():.4f}), same trace count on {same:.4f} of the pairs; histogram {np.bincount(it)}")
+    assert same >= 0.99 and abs(it.mean() - it_ref.mean()) <= 0.01
+    one = rt.rt_link(prob, w.ds, **kw)
+    it1 = _np(one["iters"])
+    early = it1 <= 2
+    np.testing.assert_array_equal(it[early], it1[early])
+    assert np.abs(_np(r["tof"]) / _np(one["tof"]) - 1).max() <= TOF_RTOL
+    rows = rt.Rows.create(prob)
+    rr = rt.rt_link_rows(prob, w.ds, rows, subfan_rays=subfan, **kw)
+    for k in ("theta", "tof", "iters", "status"):
+        assert torch.equal(rr[k], r[k]), k
+    g_ref = torch.as_tensor(P.SplitMix64(5).normal(prob.n_pairs), device="cuda")
+    g_rows = rt.rt_tof_adjoint_rows(prob, rows, rr["theta"], rr["tof"], w.ds, tof_ref=g_ref)
+    g_tr = rt.rt_tof_adjoint(prob, rr["theta"], rr["tof"], w.ds, tof_ref=g_ref)
+    assert (rows.len >= 0).all()
+    assert float((g_rows - g_tr).abs().max() / g_tr.abs().max()) <= 1e-11
+    with pytest.raises(rt._L.RtError):
+        rt.rt_link(prob, w.ds, precision="fp64", subfan_rays=subfan, **kw)
+
+
 @pytest.mark.parametrize("fan", [FAN, 0])
 def test_recorded_rows_small(rt, orc, P, fan):
     """rt_link_rows links exactly as rt_link and records the linked rays' rows;
