@@ -622,11 +622,15 @@ def run_reference(args):
 
 
 def run_tof_config(args):
-    """The ToF step (rt_link + rt_tof_adjoint, cold fan start) on one of the smaller
-    configurations as its own line: the 128^2 / 64-ring Gaussian-inclusion
-    medium (4,032 pairs) or the fish-eye lens on 512^2 with a 256-ring (65,280
-    pairs); FP32-compensated and FP64 on the GPU, the oracle on all host cores
-    and on one thread (bounded samples of the same step)."""
+    """The ToF step (cold fan start) on one of the smaller configurations as its
+    own line: the 128^2 / 64-ring Gaussian-inclusion medium (4,032 pairs;
+    FP32-compensated step rt_link_rows + rt_tof_adjoint_rows, as on the
+    headline workload) or the fish-eye lens on 512^2 with a 256-ring (65,280
+    pairs; rt_link + rt_tof_adjoint: every emitter's rays meet near its
+    conjugate point, so the row adjoint's concurrent FP64 atomics pile onto a
+    few cells, 16 ms against the retracing adjoint's spread-out ones); the
+    FP64 step is rt_link + rt_tof_adjoint; the oracle on all host cores and on
+    one thread (bounded samples of the same step)."""
     import torch
     import oracle
     import paper_2511_18511_gb300 as rt
@@ -638,10 +642,21 @@ def run_tof_config(args):
     prob = rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)
     t_meas = rt.rt_link(prob, w.ds, tol=w.tol, precision="fp64", c=prob.c * 1.002, fan_rays=fan)["tof"].clone()
     s = torch.cuda.current_stream()
+    rows = rt.Rows.create(prob)
 
-    def one(prec, out, g):
-        r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, fan_rays=fan, fan_ds=fan_ds, out=out)
-        g = rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, out=g)
+    use_rows = args.workload == "small"
+
+    def one(prec, out, g, mid=None):
+        if prec == "fp32c" and use_rows:
+            r = rt.rt_link_rows(prob, w.ds, rows, tol=w.tol, fan_rays=fan, fan_ds=fan_ds, out=out)
+            if mid is not None:
+                mid.record(s)
+            g = rt.rt_tof_adjoint_rows(prob, rows, r["theta"], r["tof"], w.ds, tof_ref=t_meas, out=g)
+        else:
+            r = rt.rt_link(prob, w.ds, tol=w.tol, precision=prec, fan_rays=fan, fan_ds=fan_ds, out=out)
+            if mid is not None:
+                mid.record(s)
+            g = rt.rt_tof_adjoint(prob, r["theta"], r["tof"], w.ds, tof_ref=t_meas, precision=prec, out=g)
         return r, g
 
     def timed(prec, steps, warmup):
@@ -651,20 +666,21 @@ def run_tof_config(args):
         torch.cuda.synchronize()
         ts = []
         for _ in range(steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             a.record(s)
-            one(prec, out, g)
+            one(prec, out, g, m)
             b.record(s)
-            ts.append((a, b))
+            ts.append((a, m, b))
         torch.cuda.synchronize()
         ok, counts = rt.rt_status_counts()
-        return float(np.mean([a.elapsed_time(b) for a, b in ts])), ok, counts, out
+        split = (float(np.mean([a.elapsed_time(m) for a, m, _ in ts])), float(np.mean([m.elapsed_time(b) for _, m, b in ts])))
+        return float(np.mean([a.elapsed_time(b) for a, _, b in ts])), ok, counts, out, split
 
     clocks = Clocks(0)
     clocks.start()
-    ms, ok, counts, out = timed("fp32c", args.steps, args.warmup)
+    ms, ok, counts, out, split = timed("fp32c", args.steps, args.warmup)
     clk = clocks.stop()
-    ms64, ok64, _, _ = timed("fp64", 1, 1)
+    ms64, ok64, _, _, _ = timed("fp64", 1, 1)
     n = prob.n_pairs
     # the oracle on the same step: a bounded sample of emitters (all cores, then one thread)
     oracle.build()
@@ -694,12 +710,14 @@ def run_tof_config(args):
             "config": {"workload": w.name, "grid": f"{w.grid.nx}x{w.grid.ny}", "h_mm": w.grid.h, "ring": w.n_tx,
                        "ring_radius_mm": w.ring_radius, "pairs": n, "ds_mm": w.ds, "tol_mm": w.tol,
                        "start": f"cold: fan of {fan} rays per transducer at {fan_ds} mm",
-                       "step": "rt_link + rt_tof_adjoint (L2 misfit against times in c x 1.002)"},
+                       "step": ("rt_link_rows + rt_tof_adjoint_rows" if use_rows else "rt_link + rt_tof_adjoint")
+                               + " (L2 misfit against times in c x 1.002)"},
             "link": {"all_linked": ok, "status_counts": counts[:7],
-                     "mean_traces_per_pair": float(out["iters"].float().mean().item())},
+                     "mean_traces_per_pair": float(out["iters"].float().mean().item()),
+                     "link_ms": split[0], "adjoint_ms": split[1]},
             "fp64_gpu": {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "all_linked": ok64,
                          "speedup_fp32c_over_fp64": ms64 / ms},
-            "gpu_launches": 9 * args.steps, "clocks": clk, "peaks": peaks, "cpu_baseline": cb}
+            "gpu_launches": (10 if use_rows else 9) * args.steps, "clocks": clk, "peaks": peaks, "cpu_baseline": cb}
     print(json.dumps(line), flush=True)
 
 
@@ -887,8 +905,8 @@ def main():
                  "status_counts": res["counts"][:7], "link_ms": link_ms, "adjoint_ms": adjoint_ms},
         "e2e": {"value": n_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         # per step: rt_link_rows = k_pack, k_tx_phi, k_fan_mark, k_fan, k_link;
-        # rt_tof_adjoint_rows = k_pack, k_tx_phi, k_adjoint_rows, k_adjoint_finish
-        "gpu_launches": 9 * args.steps,
+        # rt_tof_adjoint_rows = k_pack, k_tx_phi, k_adjoint_rows, k_adjoint_unrecorded, k_adjoint_finish
+        "gpu_launches": 10 * args.steps,
         "clocks": res["clocks"],
         "peaks": peaks,
     }
