@@ -57,6 +57,9 @@ enum rt_ray_status {
     RT_RAY_OK = 0,        /* |x_hit - x_r| <= tol */
     RT_RAY_MAXITER = 1,   /* max_iter traces without reaching tol (closest ray kept) */
     RT_RAY_STEPCAP = 2,   /* no trace reached the ring within ceil(8R/ds) steps */
+    /* 3 (a failed bracket) is never written: the two ends of the inward launch
+       interval hit the ring on either side of every receiver, so the linking
+       always holds a sign-changing bracket */
     RT_RAY_BADINPUT = 4,  /* invalid pair, transducer off the ring, or c <= 0 / NaN */
 };
 
@@ -143,7 +146,7 @@ typedef struct {
                             round of a few hundred traces lasts as long as one ray
                             marched by warps whose 32 lanes hold unrelated rays,
                             while the single launch runs those chains beside the
-                            bulk. Workspace: about 0.55 KB + 8 M bytes per pair.
+                            bulk. Workspace: about 0.53 KB + 8 M bytes per pair.
                             RT_FP32_COMP and RT_BILINEAR only; rt_batch_run
                             requires 0. */
 } rt_options;
