@@ -627,10 +627,11 @@ def run_tof_config(args):
     FP32-compensated step rt_link_rows + rt_tof_adjoint_rows, as on the
     headline workload) or the fish-eye lens on 512^2 with a 256-ring (65,280
     pairs; rt_link + rt_tof_adjoint: every emitter's rays meet near its
-    conjugate point, so the row adjoint's concurrent FP64 atomics pile onto a
-    few cells, 16 ms against the retracing adjoint's spread-out ones); the
-    FP64 step is rt_link + rt_tof_adjoint; the oracle on all host cores and on
-    one thread (bounded samples of the same step)."""
+    conjugate point, where the FP64 atomics of either adjoint pile onto a few
+    cells (16 ms both ways), so the recording link's extra cost, 84.4 against
+    79.6 ms, is not paid back); the FP64 step is rt_link + rt_tof_adjoint; the
+    oracle on all host cores and on one thread (bounded samples of the same
+    step)."""
     import torch
     import oracle
     import paper_2511_18511_gb300 as rt
