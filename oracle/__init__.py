@@ -74,7 +74,7 @@ def load(path: str):
                            C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32, _dp, _dp, _dp, _ip,
                            _ip, C.c_int32]
     L.orc_subfan_angles.argtypes = [C.c_double, C.c_double, C.c_int32, _dp]
-    L.orc_subfan_predict.argtypes = [C.c_int32, _dp, _dp, _ip, _dp]
+    L.orc_subfan_predict.argtypes = [C.c_int32, _dp, _dp, _ip, C.c_double, C.c_double, _dp]
     L.orc_tof.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip, C.c_double,
                           _dp, _dp, _dp, C.c_int32]
     L.orc_path_matrix.argtypes = [G, _dp, C.c_int32, _dp, C.c_double, C.c_int32, _ip,
@@ -291,15 +291,17 @@ def subfan_angles(ta, tb, M):
     return out
 
 
-def subfan_predict(theta, m, interior):
-    """R12 prediction from the sequence (bracket end of negative misfit,
-    sub-fan rays, other end) -> dict(theta3, ta, tb, start_theta, start_m,
-    changes_sign)."""
+def subfan_predict(theta, m, pos, c3, R=1.0):
+    """R12 prediction from the sequence (bracket end of negative misfit at
+    place 0, the sub-fan rays that reached the ring at their index q, the other
+    end at M + 1) around c3, the plain rule's third angle, for ring radius R ->
+    dict(theta3, ta, tb, start_theta, start_m, changes_sign, refined)."""
     t, mm = _f64(theta).ravel(), _f64(m).ravel()
-    it = np.ascontiguousarray(interior, dtype=np.int32).ravel()
-    out = np.empty(6)
-    _check(lib().orc_subfan_predict(len(t), _d(t), _d(mm), _i(it), _d(out)), "subfan_predict")
-    return dict(theta3=out[0], ta=out[1], tb=out[2], start_theta=out[3], start_m=out[4], changes_sign=bool(out[5]))
+    it = np.ascontiguousarray(pos, dtype=np.int32).ravel()
+    out = np.empty(7)
+    _check(lib().orc_subfan_predict(len(t), _d(t), _d(mm), _i(it), float(c3), float(R), _d(out)), "subfan_predict")
+    return dict(theta3=out[0], ta=out[1], tb=out[2], start_theta=out[3], start_m=out[4], changes_sign=bool(out[5]),
+                refined=bool(out[6]))
 
 
 def tof(grid, c_mps, tx, R, ds, theta, pairs=None, nthreads=0):

@@ -588,14 +588,18 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
  * fan-started pair misses too, M more rays at fan_ds, evenly spaced strictly
  * inside the bracket, theta_q = ta + (tb - ta) q / (M + 1), q = 1..M (ta the
  * end of negative misfit), refine it before the third trace. In the sequence
- * (ta, the sub-fan rays that reach the ring, tb) the first entry of
- * non-negative misfit and the one before it become the bracket (the Illinois
- * state restarts); the third angle is the root of the inverse cubic through
- * the four sub-fan rays around that interval (when all four are sub-fan rays,
- * their misfits increase strictly along the sequence and the root falls
- * inside), else the Regula-Falsi point of the interval; the secant then
- * starts from the interval end of smaller |misfit|. Like the fan, the
- * sub-fan only predicts; the linking traces keep ds. */
+ * (ta, the sub-fan rays that reach the ring, tb) the neighbours with no
+ * missing ray between them whose misfits differ in sign by less than pi R (a
+ * crossing, not the jump where hits wrap around the emitter or rays stop
+ * reaching the ring) and hold the angle the plain rule would trace third
+ * (the secant of the two traces, else Regula Falsi) become the bracket (the
+ * Illinois state restarts); the third angle is the root of the inverse cubic
+ * through the four sub-fan rays around that interval (when all four are
+ * sub-fan rays, their misfits are strictly monotone and the root falls
+ * inside), else the Regula-Falsi point of the interval; the secant then starts
+ * from the interval end of smaller |misfit|. When no crossing holds it, the
+ * plain rule's angle is traced unchanged. Like the fan, the sub-fan only
+ * predicts; the linking traces keep ds. */
 static double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
 
 /* Value at m = 0 of the polynomial theta(m) through the n points (m_q, t_q),
@@ -646,42 +650,60 @@ static void fan_for_emitter(const Field* F, double R, const double* xe, double d
 
 /* R12 prediction from the sequence (st[i], sm[i]), i = 0..n-1, of the
  * bracket end of negative misfit, the sub-fan rays that reached the ring (in
- * angle order, interior[i] = 1) and the other bracket end: the first entry of
- * non-negative misfit and the one before it become the bracket B (Illinois
- * state restarted); returns the third angle (the inverse cubic through the
- * four sub-fan rays around the interval when they are all sub-fan rays with
- * strictly increasing misfits and the root falls inside, else the
- * Regula-Falsi point) and sets *start to the interval end of smaller
- * |misfit|, where the secant starts. */
-static double subfan_predict(const double* st, const double* sm, const int* interior, int n, Bracket* B,
-                             double* start_theta, double* start_m) {
-    int j = 1;
-    while (j < n - 1 && sm[j] < 0) ++j;
-    B->ta = st[j - 1]; B->fa = sm[j - 1];
-    B->tb = st[j]; B->fb = sm[j];
+ * angle order, interior[i] = 1) and the other bracket end, around c3, the
+ * angle the plain rule would trace next; pos[i] is the entry's place in the
+ * full sequence (the bracket ends 0 and M + 1, sub-fan ray q at q). A
+ * crossing is a pair of entries adjacent in the full sequence (no ray that
+ * missed the ring between them) whose misfits differ in sign by less than
+ * pi R (where the hit wraps around the emitter the misfit jumps by about
+ * 2 pi R, which is no root). The
+ * crossing that holds c3 becomes the bracket B (Illinois state restarted);
+ * the third angle is the root of the inverse cubic through the four sub-fan
+ * rays around it when they are all sub-fan rays with strictly monotone
+ * misfits and the root falls inside, else its Regula-Falsi point, and *start
+ * is its end of smaller |misfit|, where the secant starts. Returns 1; returns
+ * 0, leaving B alone, when no crossing holds c3 (the plain rule then traces
+ * c3 as it would have). */
+static int subfan_predict(const double* st, const double* sm, const int* interior, const int* pos, int n,
+                          double c3, double R, Bracket* B, double* th3, double* start_theta, double* start_m) {
+    int j = -1;
+    for (int i = 1; i < n && j < 0; ++i) {
+        if ((sm[i - 1] < 0) == (sm[i] < 0) || !(fabs(sm[i] - sm[i - 1]) < M_PI * R) || pos[i] != pos[i - 1] + 1)
+            continue;
+        if (c3 >= fmin(st[i - 1], st[i]) && c3 <= fmax(st[i - 1], st[i])) j = i;
+    }
+    if (j < 0) return 0;
+    const int neg = sm[j - 1] < 0 ? j - 1 : j, nonneg = sm[j - 1] < 0 ? j : j - 1;
+    B->ta = st[neg]; B->fa = sm[neg];
+    B->tb = st[nonneg]; B->fb = sm[nonneg];
     B->last = 0;
     double th = B->ta - B->fa * (B->tb - B->ta) / (B->fb - B->fa);
-    if (j - 2 >= 0 && j + 1 < n && interior[j - 2] && interior[j - 1] && interior[j] && interior[j + 1] &&
-        sm[j - 2] < sm[j - 1] && sm[j - 1] < sm[j] && sm[j] < sm[j + 1]) {
-        const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);
-        if (v > fmin(B->ta, B->tb) && v < fmax(B->ta, B->tb)) th = v;
+    if (j - 2 >= 0 && j + 1 < n && interior[j - 2] && interior[j - 1] && interior[j] && interior[j + 1]) {
+        const int up = sm[j - 2] < sm[j - 1] && sm[j - 1] < sm[j] && sm[j] < sm[j + 1];
+        const int down = sm[j - 2] > sm[j - 1] && sm[j - 1] > sm[j] && sm[j] > sm[j + 1];
+        if (up || down) {
+            const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);
+            if (v > fmin(B->ta, B->tb) && v < fmax(B->ta, B->tb)) th = v;
+        }
     }
     const int lo = fabs(B->fa) <= fabs(B->fb);
     *start_theta = lo ? B->ta : B->tb;
     *start_m = lo ? B->fa : B->fb;
-    return th;
+    *th3 = th;
+    return 1;
 }
 
 /* Angle of sub-fan ray q = 1..M inside the bracket (ta, tb). */
 static double subfan_angle(double ta, double tb, int q, int M) { return ta + (tb - ta) * q / (M + 1); }
 
-/* R12: trace the M sub-fan rays of bracket B at fan_ds and predict. */
-static double subfan_refine(const Field* F, double R, const double* xe, double phi_e, double psi_r,
-                            double fan_ds, int M, Bracket* B, Eval* start) {
+/* R12: trace the M sub-fan rays of bracket B at fan_ds and predict around
+ * c3; returns 0 (B untouched) when no crossing holds c3. */
+static int subfan_refine(const Field* F, double R, const double* xe, double phi_e, double psi_r, double fan_ds,
+                         int M, double c3, Bracket* B, double* th3, Eval* start) {
     double st[ORC_SUBFAN_MAX + 2], sm[ORC_SUBFAN_MAX + 2];
-    int interior[ORC_SUBFAN_MAX + 2];
+    int interior[ORC_SUBFAN_MAX + 2], pos[ORC_SUBFAN_MAX + 2];
     int n = 0;
-    st[n] = B->ta; sm[n] = B->fa; interior[n++] = 0;
+    st[n] = B->ta; sm[n] = B->fa; interior[n] = 0; pos[n++] = 0;
     for (int q = 1; q <= M; ++q) {
         const double th = subfan_angle(B->ta, B->tb, q, M);
         TraceRes tr;
@@ -689,10 +711,11 @@ static double subfan_refine(const Field* F, double R, const double* xe, double p
         if (tr.flags & 3) continue;
         st[n] = th;
         sm[n] = R * (mod_2pi(atan2(tr.hit[1], tr.hit[0]) - phi_e) - psi_r);
-        interior[n++] = 1;
+        interior[n] = 1;
+        pos[n++] = q;
     }
-    st[n] = B->tb; sm[n] = B->fb; interior[n++] = 0;
-    return subfan_predict(st, sm, interior, n, B, &start->theta, &start->m);
+    st[n] = B->tb; sm[n] = B->fb; interior[n] = 0; pos[n++] = M + 1;
+    return subfan_predict(st, sm, interior, pos, n, c3, R, B, th3, &start->theta, &start->m);
 }
 
 int orc_subfan_angles(double ta, double tb, int32_t M, double* theta) {
@@ -701,15 +724,20 @@ int orc_subfan_angles(double ta, double tb, int32_t M, double* theta) {
     return ORC_OK;
 }
 
-int orc_subfan_predict(int32_t n, const double* st, const double* sm, const int32_t* interior, double* out6) {
-    if (n < 2 || n > ORC_SUBFAN_MAX + 2 || !st || !sm || !interior || !out6) return ORC_EINVAL;
-    int in[ORC_SUBFAN_MAX + 2];
-    for (int i = 0; i < n; ++i) in[i] = interior[i] != 0;
-    Bracket B;
-    double s_th, s_m;
-    out6[0] = subfan_predict(st, sm, in, n, &B, &s_th, &s_m);
-    out6[1] = B.ta; out6[2] = B.tb; out6[3] = s_th; out6[4] = s_m;
-    out6[5] = (B.fa < 0 && B.fb >= 0) ? 1.0 : 0.0;
+int orc_subfan_predict(int32_t n, const double* st, const double* sm, const int32_t* pos, double c3, double R,
+                       double* out7) {
+    if (n < 2 || n > ORC_SUBFAN_MAX + 2 || !st || !sm || !pos || !out7 || !(R > 0)) return ORC_EINVAL;
+    int in[ORC_SUBFAN_MAX + 2], ps[ORC_SUBFAN_MAX + 2];
+    for (int i = 0; i < n; ++i) {
+        ps[i] = pos[i];
+        in[i] = i > 0 && i < n - 1;
+    }
+    Bracket B = {st[0], sm[0], st[n - 1], sm[n - 1], 0};
+    double th = c3, s_th = NAN, s_m = NAN;
+    const int refined = subfan_predict(st, sm, in, ps, n, c3, R, &B, &th, &s_th, &s_m);
+    out7[0] = th; out7[1] = B.ta; out7[2] = B.tb; out7[3] = s_th; out7[4] = s_m;
+    out7[5] = (B.fa < 0 && B.fb >= 0) ? 1.0 : 0.0;
+    out7[6] = refined;
     return ORC_OK;
 }
 
@@ -789,10 +817,20 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
     double next = th0;
     while (n_eval < max_iter) {
         if (n_eval == 2 && subfan > 0) {
+            /* the plain rule's third angle, around which the sub-fan refines */
+            const double den = cur.m - prev.m;
+            double c3 = (den != 0.0) ? cur.theta - cur.m * (cur.theta - prev.theta) / den : NAN;
+            if (!(isfinite(c3) && c3 > fmin(B.ta, B.tb) && c3 < fmax(B.ta, B.tb)))
+                c3 = (B.ta * B.fb - B.tb * B.fa) / (B.fb - B.fa);
             Eval s0;
-            next = subfan_refine(F, R, xe, phi_e, psi_r, fan_ds, subfan, &B, &s0);
-            prev = s0;
-            cur = s0;
+            double th3;
+            if (subfan_refine(F, R, xe, phi_e, psi_r, fan_ds, subfan, c3, &B, &th3, &s0)) {
+                next = th3;
+                prev = s0;
+                cur = s0;
+            } else {
+                next = c3;
+            }
         } else if (n_eval > 0) {
             if (n_eval == 1 && ok4 && !(cur.tr.flags & 3)) {
                 const double t5[5] = {cur.theta, t4[0], t4[1], t4[2], t4[3]};

@@ -78,12 +78,16 @@ int orc_link(const orc_grid* g, const double* c_mps, int32_t n_tx, const double*
              double* hit_xy, int32_t* status, int32_t* iters, int32_t nthreads);
 
 /* R12 sub-fan pieces, for tests: the M ray angles inside a bracket (ta, tb),
- * and the prediction from a sequence of n (angle, misfit, interior flag)
- * entries (bracket end of negative misfit, sub-fan rays, other bracket end):
- * out6 = {third angle, new ta, new tb, secant start angle and misfit, 1 when
- * the new bracket changes sign}. */
+ * and the prediction from a sequence of n (angle, misfit, place) entries
+ * (bracket end of negative misfit at place 0, the sub-fan rays that reached
+ * the ring at their ray index q, the other bracket end at M + 1) around c3,
+ * the plain rule's third angle, for ring radius R: out7 = {third
+ * angle, new ta, new tb, secant start angle and misfit, 1 when the new
+ * bracket changes sign, 1 when refined (else the angle is c3 and the bracket
+ * the sequence's ends)}. */
 int orc_subfan_angles(double ta, double tb, int32_t M, double* theta);
-int orc_subfan_predict(int32_t n, const double* st, const double* sm, const int32_t* interior, double* out6);
+int orc_subfan_predict(int32_t n, const double* st, const double* sm, const int32_t* pos, double c3, double R,
+                       double* out7);
 
 /* Travel time (and hit) of every pair at the given angles, no linking. */
 int orc_tof(const orc_grid* g, const double* c_mps, int32_t n_tx, const double* tx,

@@ -60,11 +60,15 @@ MUTANTS = {
                                 "fan_theta(a_min, step, k), ds, NULL, NULL, 0, &tr);"),
     "subfan_angles_shifted": ("{ return ta + (tb - ta) * q / (M + 1); }",
                               "{ return ta + (tb - ta) * (q - 1) / (M + 1); }"),
-    "subfan_interval_from_far_side": ("B->ta = st[j - 1]; B->fa = sm[j - 1];\n    B->tb = st[j]; B->fb = sm[j];",
-                                      "B->ta = st[j]; B->fa = sm[j];\n    B->tb = st[j + 1 < n ? j + 1 : j]; "
-                                      "B->fb = sm[j + 1 < n ? j + 1 : j];"),
-    "subfan_window_with_ends": ("interior[j - 2] && interior[j - 1] && interior[j] && interior[j + 1] &&",
-                                "1 &&"),
+    "subfan_jump_taken_for_a_crossing": ("|| !(fabs(sm[i] - sm[i - 1]) < M_PI * R) ||", "||"),
+    "subfan_candidate_ignored": ("if (c3 >= fmin(st[i - 1], st[i]) && c3 <= fmax(st[i - 1], st[i])) j = i;",
+                                 "j = i;"),
+    "subfan_bracket_orientation": ("const int neg = sm[j - 1] < 0 ? j - 1 : j, nonneg = sm[j - 1] < 0 ? j : j - 1;",
+                                   "const int neg = j - 1, nonneg = j;"),
+    "subfan_gap_taken_for_a_crossing": ("|| pos[i] != pos[i - 1] + 1)", ")"),
+    "subfan_window_with_ends": ("interior[j - 2] && interior[j - 1] && interior[j] && interior[j + 1]) {",
+                                "1) {"),
+    "subfan_only_rising_cubic": ("if (up || down) {", "if (up) {"),
     "subfan_cubic_point_dropped": ("const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);",
                                    "const double v = inverse_poly_root(st + j - 2, sm + j - 2, 3);"),
     "subfan_cubic_shifted": ("const double v = inverse_poly_root(st + j - 2, sm + j - 2, 4);",
@@ -79,7 +83,7 @@ MUTANTS = {
 PINS = [
     pins.test_subfan_angles_evenly_inside,
     pins.test_subfan_prediction_exact_for_cubic_inverse,
-    pins.test_subfan_picks_first_sign_change_and_nearer_end,
+    pins.test_subfan_picks_the_crossing_at_the_plain_candidate,
     pins.test_bilinear_exact_for_bilinear_field,
     pins.test_homogeneous_straight_rays,
     pins.test_path_matrix_invariants,

@@ -591,36 +591,74 @@ def test_subfan_prediction_exact_for_cubic_inverse(orc):
             seq_m = np.r_[0.5 * ta_m, m, 0.5 * tb_m]        # ends off the curve
             j = int(np.argmax(seq_m >= 0))
             assert 3 <= j <= M - 1                            # four sub-fan rays around the root
-            p = orc.subfan_predict(seq_t, seq_m, np.r_[0, np.ones(M, int), 0])
+            c3 = 0.5 * (seq_t[j - 1] + seq_t[j])                   # the plain rule's candidate
+            p = orc.subfan_predict(seq_t, seq_m, np.arange(M + 2), c3, R=10.0)
+            assert p["refined"]
             assert p["changes_sign"]
             assert (p["ta"], p["tb"]) == (seq_t[j - 1], seq_t[j])
             assert abs(p["theta3"] - coef[0]) <= 1e-12, (M, p["theta3"])
-    # the root between the last sub-fan ray and the far end: linear
+    # the root between the first two sub-fan rays: the four around it would take
+    # the bracket end (off the curve), so the Regula-Falsi point
     coef = (0.3, 0.8, 0.2, 0.05)
+    ta_m, tb_m = -1.0, 1.5
+    ta, tb = np.polyval(coef[::-1], ta_m), np.polyval(coef[::-1], tb_m)
+    th = orc.subfan_angles(ta, tb, 4)
+    m = _cubic_inverse(coef, th)
+    seq_t, seq_m = np.r_[ta, th, tb], np.r_[0.5 * ta_m, m, 0.5 * tb_m]
+    j = int(np.argmax(seq_m >= 0))
+    assert j == 2, seq_m
+    p = orc.subfan_predict(seq_t, seq_m, [0, 1, 2, 3, 4, 5], seq_t[1], R=10.0)
+    rf = seq_t[1] - seq_m[1] * (seq_t[2] - seq_t[1]) / (seq_m[2] - seq_m[1])
+    assert (p["ta"], p["tb"]) == (seq_t[1], seq_t[2]) and abs(p["theta3"] - rf) <= 1e-15
+    # the root between the last sub-fan ray and the far end: linear
     ta_m, tb_m = -2.0, 0.05
     ta, tb = np.polyval(coef[::-1], ta_m), np.polyval(coef[::-1], tb_m)
     th = orc.subfan_angles(ta, tb, 4)
     m = _cubic_inverse(coef, th)
     assert (m < 0).all()
     seq_t, seq_m = np.r_[ta, th, tb], np.r_[0.5 * ta_m, m, 0.5 * tb_m]
-    p = orc.subfan_predict(seq_t, seq_m, [0, 1, 1, 1, 1, 0])
+    p = orc.subfan_predict(seq_t, seq_m, [0, 1, 2, 3, 4, 5], tb, R=10.0)
     rf = seq_t[4] - seq_m[4] * (seq_t[5] - seq_t[4]) / (seq_m[5] - seq_m[4])
     assert (p["ta"], p["tb"]) == (seq_t[4], seq_t[5]) and abs(p["theta3"] - rf) <= 1e-15
 
 
-def test_subfan_picks_first_sign_change_and_nearer_end(orc):
-    """Several sign changes in the sequence: the bracket is the first entry of
-    non-negative misfit from the negative end and the one before; without four
-    sub-fan rays around it the third angle is its Regula-Falsi point; the
-    secant starts from its end of smaller |misfit|; rays that did not reach the
-    ring are simply absent from the sequence."""
+def test_subfan_picks_the_crossing_at_the_plain_candidate(orc):
+    """Several sign changes in the sequence, one of them a jump of about 2 pi R
+    (the hit wrapping around the emitter): the bracket is the crossing (sign
+    change by less than pi R between entries with no missing ray between them)
+    that holds the plain rule's third angle c3, with
+    either orientation; without four sub-fan rays around it the third angle is
+    its Regula-Falsi point; the secant starts from its end of smaller |misfit|;
+    when no crossing holds c3, nothing is refined and c3 is traced."""
     t = np.array([0.0, 0.1, 0.2, 0.3, 0.4, 0.5])
     m = np.array([-1.0, -0.5, 0.3, -0.2, 0.6, 1.0])
-    p = orc.subfan_predict(t, m, [0, 1, 1, 1, 1, 0])
-    assert (p["ta"], p["tb"]) == (0.1, 0.2)
+    p = orc.subfan_predict(t, m, [0, 1, 2, 3, 4, 5], 0.13, R=1.0)
+    assert p["refined"] and (p["ta"], p["tb"]) == (0.1, 0.2) and p["changes_sign"]
     assert abs(p["theta3"] - (0.1 + 0.5 * 0.1 / 0.8)) <= 1e-15
     assert (p["start_theta"], p["start_m"]) == (0.2, 0.3)
-    m2 = np.array([-1.0, -0.5, -0.05, 0.4, 1.0])
-    p2 = orc.subfan_predict([0.0, 0.1, 0.2, 0.3, 0.4], m2, [0, 1, 1, 1, 0])
-    assert (p2["ta"], p2["tb"]) == (0.2, 0.3) and (p2["start_theta"], p2["start_m"]) == (0.2, -0.05)
-    assert abs(p2["theta3"] - (0.2 + 0.05 * 0.1 / 0.45)) <= 1e-15    # window 1..4 reaches the end: linear
+    q = orc.subfan_predict(t, m, [0, 1, 2, 3, 4, 5], 0.27, R=1.0)          # the falling crossing (0.2, 0.3)
+    assert q["refined"] and (q["ta"], q["tb"]) == (0.3, 0.2) and q["changes_sign"]
+    assert abs(q["theta3"] - (0.3 - (-0.2) * (0.2 - 0.3) / (0.3 + 0.2))) <= 1e-15
+    assert (q["start_theta"], q["start_m"]) == (0.3, -0.2)
+    r = orc.subfan_predict(t, m, [0, 1, 2, 3, 4, 5], 0.46, R=1.0)          # no crossing in (0.4, 0.5)
+    assert not r["refined"] and r["theta3"] == 0.46 and (r["ta"], r["tb"]) == (0.0, 0.5)
+    mj = np.array([-1.0, -1.5, 2.0, -0.1, 0.2, 1.0])                        # jump of 3.5 > pi at (0.1, 0.2)
+    j = orc.subfan_predict(t, mj, [0, 1, 2, 3, 4, 5], 0.15, R=1.0)
+    assert not j["refined"] and j["theta3"] == 0.15
+    j2 = orc.subfan_predict(t, mj, [0, 1, 2, 3, 4, 5], 0.15, R=2.0)        # the same sign change, 3.5 < 2 pi
+    assert j2["refined"] and (j2["ta"], j2["tb"]) == (0.1, 0.2)
+    k = orc.subfan_predict(t, mj, [0, 1, 2, 3, 4, 5], 0.34, R=1.0)
+    assert k["refined"] and (k["ta"], k["tb"]) == (0.3, 0.4)
+    # a ray that missed the ring between two entries: their sign change is no crossing
+    g = orc.subfan_predict([0.0, 0.1, 0.3, 0.4, 0.5], [-1.0, -0.5, 0.3, 0.6, 1.0], [0, 1, 3, 4, 5], 0.2, R=1.0)
+    assert not g["refined"] and g["theta3"] == 0.2
+    g2 = orc.subfan_predict([0.0, 0.1, 0.2, 0.4, 0.5], [-1.0, -0.5, 0.3, 0.6, 1.0], [0, 1, 2, 4, 5], 0.15, R=1.0)
+    assert g2["refined"] and (g2["ta"], g2["tb"]) == (0.1, 0.2)
+    # strictly falling misfits around the root: the inverse cubic applies too
+    coef = (0.3, -0.8, 0.2, -0.05)
+    th = np.array([0.0, 0.15, 0.25, 0.35, 0.45, 0.6])
+    mm = _cubic_inverse(coef, th)
+    assert (np.diff(mm) < 0).all()
+    assert int(np.argmax(mm < 0)) == 3
+    c = orc.subfan_predict(th, mm, [0, 1, 2, 3, 4, 5], 0.31, R=10.0)
+    assert c["refined"] and abs(c["theta3"] - coef[0]) <= 1e-12, c
