@@ -146,7 +146,13 @@ typedef struct {
                             round of a few hundred traces lasts as long as one ray
                             marched by warps whose 32 lanes hold unrelated rays,
                             while the single launch runs those chains beside the
-                            bulk. Workspace: about 0.53 KB + 8 M bytes per pair.
+                            bulk. An experimental option: on the fish-eye lens with
+                            M = 32, 3 of 65,280 near-tangent pairs (adjacent
+                            transducers, 4-6 FP32 traces where the oracle needs 2)
+                            end at max_iter, the narrowed bracket holding a jump
+                            of the misfit (rays that stop reaching the ring)
+                            instead of the root; M = 8 and 16 link every pair
+                            there. Workspace: about 0.53 KB + 8 M bytes per pair.
                             RT_FP32_COMP and RT_BILINEAR only; rt_batch_run
                             requires 0. */
 } rt_options;

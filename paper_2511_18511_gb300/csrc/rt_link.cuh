@@ -374,41 +374,56 @@ __device__ __forceinline__ double subfan_theta(const LinkState& L, int q, int M)
 }
 
 // R12: a fan-started pair whose second trace missed, with the misfits m[q-1]
-// of its M sub-fan rays (NaN: the ray did not reach the ring). In the
-// sequence (ta, the sub-fan rays that reached the ring, tb) the first entry of
-// non-negative misfit and the one before it become the bracket (Illinois
-// state restarted); the third angle is the root of the inverse cubic through
-// the four sub-fan rays around that interval (all four sub-fan rays, misfits
-// strictly increasing, root inside), else its Regula-Falsi point; the secant
-// starts from the interval end of smaller |misfit|.
-static __device__ __noinline__ void subfan_apply(LinkState& L, const double* __restrict__ m, int M) {
+// of its M sub-fan rays (NaN: the ray did not reach the ring) and L.next, the
+// third angle the plain rule chose. In the sequence (ta, the sub-fan rays that
+// reached the ring, tb) a crossing is a pair of neighbours with no ray that
+// missed the ring between them whose misfits differ in sign by less than
+// pi R (where hits wrap around the emitter the misfit jumps by about 2 pi R);
+// the crossing that holds L.next becomes the
+// bracket (Illinois state restarted), the third angle is the root of the
+// inverse cubic through the four sub-fan rays around it (all four sub-fan
+// rays, misfits strictly monotone, root inside), else its Regula-Falsi point,
+// and the secant starts from its end of smaller |misfit|. When no crossing
+// holds L.next the state is left as the plain rule set it.
+static __device__ __noinline__ void subfan_apply(LinkState& L, const double* __restrict__ m, int M, double R) {
     double st[kSubfanMax + 2], sm[kSubfanMax + 2];
     bool in[kSubfanMax + 2];
+    int pos[kSubfanMax + 2];
     int n = 0;
-    st[n] = L.ta; sm[n] = L.fa; in[n++] = false;
+    st[n] = L.ta; sm[n] = L.fa; in[n] = false; pos[n++] = 0;
     for (int q = 1; q <= M; ++q) {
         const double v = m[q - 1];
         if (isnan(v)) continue;
-        st[n] = subfan_theta(L, q, M); sm[n] = v; in[n++] = true;
+        st[n] = subfan_theta(L, q, M); sm[n] = v; in[n] = true; pos[n++] = q;
     }
-    st[n] = L.tb; sm[n] = L.fb; in[n++] = false;
-    int j = 1;
-    while (j < n - 1 && sm[j] < 0) ++j;
-    L.ta = st[j - 1]; L.fa = sm[j - 1];
-    L.tb = st[j]; L.fb = sm[j];
+    st[n] = L.tb; sm[n] = L.fb; in[n] = false; pos[n++] = M + 1;
+    const double c3 = L.next;
+    int j = -1;
+    for (int i = 1; i < n && j < 0; ++i) {
+        if ((sm[i - 1] < 0) == (sm[i] < 0) || !(fabs(sm[i] - sm[i - 1]) < kPi * R) || pos[i] != pos[i - 1] + 1)
+            continue;
+        if (c3 >= fmin(st[i - 1], st[i]) && c3 <= fmax(st[i - 1], st[i])) j = i;
+    }
+    if (j < 0) return;
+    const int ng = sm[j - 1] < 0 ? j - 1 : j, ps = sm[j - 1] < 0 ? j : j - 1;
+    L.ta = st[ng]; L.fa = sm[ng];
+    L.tb = st[ps]; L.fb = sm[ps];
     L.last = 0;
     double th = L.ta - L.fa * (L.tb - L.ta) / (L.fb - L.fa);
-    if (j - 2 >= 0 && j + 1 < n && in[j - 2] && in[j - 1] && in[j] && in[j + 1] && sm[j - 2] < sm[j - 1] &&
-        sm[j - 1] < sm[j] && sm[j] < sm[j + 1]) {
-        // inverse cubic through the four rays, Lagrange form at misfit 0
-        double v = 0.0;
-        for (int a = 0; a < 4; ++a) {
-            double l = 1.0;
-            for (int b = 0; b < 4; ++b)
-                if (b != a) l *= (0.0 - sm[j - 2 + b]) / (sm[j - 2 + a] - sm[j - 2 + b]);
-            v += l * st[j - 2 + a];
+    if (j - 2 >= 0 && j + 1 < n && in[j - 2] && in[j - 1] && in[j] && in[j + 1]) {
+        const bool up = sm[j - 2] < sm[j - 1] && sm[j - 1] < sm[j] && sm[j] < sm[j + 1];
+        const bool down = sm[j - 2] > sm[j - 1] && sm[j - 1] > sm[j] && sm[j] > sm[j + 1];
+        if (up || down) {
+            // inverse cubic through the four rays, Lagrange form at misfit 0
+            double v = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                double l = 1.0;
+                for (int b = 0; b < 4; ++b)
+                    if (b != a) l *= (0.0 - sm[j - 2 + b]) / (sm[j - 2 + a] - sm[j - 2 + b]);
+                v += l * st[j - 2 + a];
+            }
+            if (v > fmin(L.ta, L.tb) && v < fmax(L.ta, L.tb)) th = v;
         }
-        if (v > fmin(L.ta, L.tb) && v < fmax(L.ta, L.tb)) th = v;
     }
     const bool lo = fabs(L.fa) <= fabs(L.fb);
     L.cur_th = L.prev_th = lo ? L.ta : L.tb;

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
             const int slot = fetch_pair(queue);
             if (slot >= n_in) break;
             L = rd.aside_in[slot];
-            if (rd.sub && L.fan_k0 >= -1 && L.n_eval == 2) subfan_apply(L, rd.sub + (size_t)slot * rd.sub_m, rd.sub_m);
+            if (rd.sub && L.fan_k0 >= -1 && L.n_eval == 2) subfan_apply(L, rd.sub + (size_t)slot * rd.sub_m, rd.sub_m, G.R);
             if constexpr (REC) ns.begin(rec.runs + (size_t)L.k * rec.cap);
             trace_begin(ts, G, L.xe, L.ye, L.next);
             active = true;
