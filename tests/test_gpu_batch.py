@@ -74,6 +74,39 @@ def test_batch_equals_single_calls_and_oracle(rt, P, orc, prec):
         assert e <= 1e-5
 
 
+def test_batch_with_coarse_fan_equals_single_calls_and_oracle(rt, P, orc):
+    """The bench's batch setting, fans traced at h/2 (FP32-compensated): the
+    batch links as the single calls with the same fan step, travel times within
+    the linking bar of the oracle's with the same fan step; a sub-fan option is
+    refused (the batch links in one launch)."""
+    ds, tol = 0.05, 1e-4
+    items = _small_batch(P, rt)
+    fds = 0.5 * items[0][0].h
+    insts = [rt.BatchInstance.create(it[4], tof_ref=it[5]) for it in items]
+    rt.rt_batch_run(insts, ds, tol, fan_ds=fds)
+    ok, counts = rt.rt_status_counts()
+    assert ok and counts[0] == sum(it[4].n_pairs for it in items)
+    for k, (g, c, tx, R, prob, ref) in enumerate(items):
+        b = insts[k]
+        single = rt.rt_link(prob, ds, tol=tol, fan_ds=fds)
+        np.testing.assert_allclose(_np(b.tof), _np(single["tof"]), rtol=1e-9)
+        np.testing.assert_array_equal(_np(b.iters), _np(single["iters"]))
+        o = orc.link(g, c, tx, R, ds, tol=tol, fan_rays=rt.DEFAULT_FAN, fan_ds=fds)
+        rel = np.abs(_np(b.tof) / o["tof"] - 1).max()
+        print(f"[fan at h/2] instance {k}: ToF vs oracle {rel:.2e}, traces/pair {_np(b.iters).mean():.3f} "
+              f"(oracle {o['iters'].mean():.3f})")
+        assert rel <= 2e-6
+    o = rt._opts(ds, tol, subfan_rays=8)
+    with pytest.raises(rt._L.RtError):
+        _batch_with_opts(rt, insts, o)
+
+
+def _batch_with_opts(rt, insts, o):
+    ctx = rt.default_context(insts[0].prob.c.device.index)
+    arr = (rt._L.RtInstance * len(insts))(*[b.struct() for b in insts])
+    rt._L.check(ctx.h, ctx.lib.rt_batch_run(ctx.h, len(insts), arr, C.byref(o), None))
+
+
 def test_batch_graph_replay(rt, P):
     ds = 0.05
     items = _small_batch(P, rt)
