@@ -88,6 +88,30 @@ def test_maps_small_vs_oracle(small, P):
 
 # --------------------------------------------------------- Born map, adjoint
 
+@pytest.mark.parametrize("grad,tol_t,tol_a", [(1.0, 2e-6, 5e-5), (5.0, 2e-5, 1.5e-4)])
+def test_maps_linear_gradient_closed_form_gpu(rt, P, grad, tol_t, tol_a):
+    """The GPU fan maps in c = 1500 + grad y against the closed forms of the
+    circular rays (travel time, and amplitude from Q = |x - x_e| / |cos a|):
+    within the oracle's bounds plus the FP32 rounding of T (a few 1e-7) and A."""
+    from tests.test_oracle_born_pins import linear_gradient_maps_closed_form
+    g = P.Grid(64, 64, 0.5)
+    R = 14.0
+    tx = P.ring(8, R)
+    prob = rt.Problem.create(g, P.linear_gradient(g, 1500.0, grad), tx, R)
+    maps = rt.rtborn_maps(prob, 0.05, P.born_fan_rays(R, g.h))
+    T, A = _np(maps.T), _np(maps.A)
+    x, y = g.node_xy()
+    inside = x * x + y * y < R * R
+    worst_t = worst_a = 0.0
+    for t in range(len(tx)):
+        Tc, Ac, r, adx = linear_gradient_maps_closed_form(g, grad, tx[t])
+        m = inside & (r >= 2 * g.h) & (adx > 2 * g.h)
+        worst_t = max(worst_t, float(np.abs(T[t][m] / Tc[m] - 1).max()))
+        worst_a = max(worst_a, float(np.abs(A[t][m] / Ac[m] - 1).max()))
+    print(f"linear gradient {grad} (m/s)/mm, GPU maps vs closed form: T rel max {worst_t:.2e}, A rel max {worst_a:.2e}")
+    assert worst_t <= tol_t + 1e-6 and worst_a <= tol_a + 1e-5
+
+
 @pytest.mark.parametrize("gemm", ["fp32", "tf32x3"])
 def test_apply_adjoint_synthetic_maps_vs_oracle(rt, P, orc, gemm):
     """Born map and adjoint of the same float32 maps on both sides (128^2,

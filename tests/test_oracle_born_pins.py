@@ -249,3 +249,48 @@ def test_born_adjoint_single_datum_homogeneous(orc):
     amp = om ** 2 * g.h ** 2 / np.sqrt(re * rr)
     assert (np.abs(out[m] - want[m]) <= amp[m] * (0.1 * g.h / np.minimum(re, rr)[m] + 1e-6)).all()
     assert (out[~inside] == 0).all()
+
+
+def linear_gradient_maps_closed_form(g, grad, tx):
+    """Closed forms of the maps in c = 1500 + grad y (m/s, y in mm): the ray
+    from x_e to a node is the circle through both centred on y = -1500/grad;
+    T = arccosh(1 + grad^2 r^2 / (2 c_e c)) / grad and, with the Hessian zero,
+    Q = int c ds / c_e = |x - x_e| / |cos a| (a the launch angle to the x axis,
+    cos a = (y_e + 1500/grad) / rho), A = sqrt(c / (c_e max(Q, h)))."""
+    x, y = g.node_xy()
+    xe, ye = tx
+    r = np.hypot(x - xe, y - ye)
+    gk = 1e-3 * grad                                    # (mm/us) per mm
+    ce, cn = 1e-3 * (1500.0 + grad * ye), 1e-3 * (1500.0 + grad * y)
+    T = np.arccosh(1.0 + gk * gk * r * r / (2.0 * ce * cn)) / gk
+    y0 = 1500.0 / grad
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xc = ((x * x - xe * xe) + ((y + y0) ** 2 - (ye + y0) ** 2)) / (2.0 * (x - xe))
+    rho = np.hypot(xe - xc, ye + y0)
+    Q = np.abs(x - xe) * rho / np.abs(ye + y0)
+    A = np.sqrt(cn / (ce * np.maximum(Q, g.h)))
+    return T, A, r, np.abs(x - xe)
+
+
+@pytest.mark.parametrize("grad,tol_t,tol_a", [(1.0, 2e-6, 5e-5), (5.0, 2e-5, 1.5e-4)])
+def test_maps_linear_gradient_closed_form(orc, grad, tol_t, tol_a):
+    """Refracting medium c = 1500 + grad y (no caustics): the maps' travel times
+    and amplitudes against the closed forms of the circular rays (B3-B5 in a
+    medium where c(x) differs from c_t and rays bend): T within tol_t and A
+    within tol_a relative at every inside node at least 2h from the transducer
+    (and from its vertical, where |x - x_e| / |cos a| loses precision); the
+    error grows with the ray curvature, which the extrapolation from the foot
+    of the node neglects."""
+    g = P.Grid(64, 64, 0.5)
+    R = 14.0
+    c = P.linear_gradient(g, 1500.0, grad)
+    tx = P.ring(8, R)
+    T, A = orc.fan_maps(g, c, tx, R, 0.05, P.born_fan_rays(R, g.h))
+    x, y = g.node_xy()
+    inside = x * x + y * y < R * R
+    for t in range(len(tx)):
+        Tc, Ac, r, adx = linear_gradient_maps_closed_form(g, grad, tx[t])
+        m = inside & (r >= 2 * g.h) & (adx > 2 * g.h)
+        eT = np.abs(T[t][m] / Tc[m] - 1)
+        eA = np.abs(A[t][m] / Ac[m] - 1)
+        assert eT.max() <= tol_t and eA.max() <= tol_a, (t, eT.max(), eA.max())

@@ -168,6 +168,8 @@ BORN_MUTANTS = {
     "born_P0_is_c": ("double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, 1.0 / c_t}",
                      "double st[6] = {xe, ye, cos(theta), sin(theta), 0.0, c_t}"),
     "born_Q_missing_c": ("k[4] = f[F_C] * st[5];", "k[4] = st[5];"),
+    "born_amplitude_c_of_transducer": ("const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(Qf, h))));",
+                                       "const double A = sqrt(M->c_t / (M->c_t * fabs(clamp_q(Qf, h))));"),
     "born_amplitude_no_sqrt": ("const double A = sqrt(p->c / (M->c_t * fabs(clamp_q(Qf, h))));",
                                "const double A = p->c / (M->c_t * fabs(clamp_q(Qf, h)));"),
     "born_first_order_only": ("p->T + p->s * along + 0.5 * curv * across * across, fabs(across), A, L);",
@@ -193,6 +195,7 @@ BORN_MUTANTS = {
 
 BORN_PINS = [
     bpins.test_fan_ray_homogeneous_straight,
+    lambda orc: bpins.test_maps_linear_gradient_closed_form(orc, 1.0, 2e-6, 5e-5),
     lambda orc: bpins.test_fan_ray_linear_gradient_closed_form_Q(orc, 0.2),
     lambda orc: bpins.test_paraxial_Q_matches_auxiliary_rays(orc, 0, 0.1),
     lambda orc: bpins.test_paraxial_Q_matches_auxiliary_rays(orc, 9, -0.6),
