@@ -584,6 +584,19 @@ int rt_peak_fma(int32_t dtype, int32_t blocks, int32_t iters, void* sink, void* 
 int rt_peak_gather(const void* buf, int64_t n_vec, int32_t blocks, int32_t iters, float* sink, void* stream);
 int rt_peak_read(const void* buf, int64_t n_vec, int32_t blocks, int32_t passes, float* sink, void* stream);
 
+/*
+ * rt_wait_selftest — exercises the bounded device wait that the tensor-core
+ * Born kernels use on every pipeline barrier (wait for a barrier phase for at
+ * most a limit of global time, then record an error code and return instead
+ * of hanging). One block initialises a shared-memory barrier expecting one
+ * arrival; with arrive != 0 a thread arrives, otherwise nothing does; the
+ * thread then waits on it for at most limit_ns (1e3 .. 2e9 ns). *err (device
+ * int32) receives 0 when the phase completed and 199 when the wait gave up.
+ * Enqueues one kernel on `stream`; the caller synchronises and reads *err.
+ * Returns RT_OK, RT_EINVAL (bad argument, nothing enqueued) or RT_ECUDA.
+ */
+int rt_wait_selftest(int64_t limit_ns, int32_t arrive, int32_t* err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

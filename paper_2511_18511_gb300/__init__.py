@@ -539,3 +539,17 @@ class Born(torch.autograd.Function):
 def born(dc: torch.Tensor, maps: BornMaps, f_mhz, gemm: str = "tf32x3") -> torch.Tensor:
     """Differentiable Born data of dc (float32 [ny, nx])."""
     return Born.apply(dc, maps, f_mhz, gemm)
+
+
+def wait_selftest(limit_ns: int, arrive: bool, stream=None) -> tuple:
+    """Runs the bounded device wait of the tensor-core kernels once on a
+    barrier that completes (arrive) or never does; returns (error code, wall
+    seconds): 0 when the phase completed, 199 when the wait gave up."""
+    import time
+    lib = _L.load()
+    err = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _L.check(None, lib.rt_wait_selftest(int(limit_ns), 1 if arrive else 0, _ptr(err), _stream(stream)))
+    torch.cuda.synchronize()
+    return int(err.item()), time.perf_counter() - t0

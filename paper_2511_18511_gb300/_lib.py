@@ -22,8 +22,8 @@ EXPORTED = [
     "rt_link", "rt_tof_forward", "rt_tof_adjoint", "rt_path_matrix", "rt_status_counts",
     "rt_tof_forward_noalloc", "rt_batch_run", "rtborn_maps", "rtborn_apply", "rtborn_adjoint",
     "rt_csr_matvec", "rt_csr_rmatvec", "rt_bspline_coef", "rtborn_maps_abs", "rtborn_apply_abs",
-    "rtborn_adjoint_abs", "rt_peak_fma", "rt_peak_gather", "rt_peak_read", "rt_rows_cap", "rt_link_rows",
-    "rt_tof_adjoint_rows",
+    "rtborn_adjoint_abs", "rt_peak_fma", "rt_peak_gather", "rt_peak_read", "rt_wait_selftest", "rt_rows_cap",
+    "rt_link_rows", "rt_tof_adjoint_rows",
 ]
 RTBORN_GEMM_FP32, RTBORN_GEMM_TF32X3 = 0, 1
 ABI_VERSION = 4   # layout of RtOptions below
@@ -122,6 +122,7 @@ def load():
         L.rt_peak_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp]
         L.rt_peak_gather.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, vp, vp]
         L.rt_peak_read.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, vp, vp]
+        L.rt_wait_selftest.argtypes = [C.c_int64, C.c_int32, vp, vp]
         _lib = L
         return L
 

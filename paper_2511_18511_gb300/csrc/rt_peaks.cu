@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "rt_internal.h"
+#include "rt_tc.cuh"
 
 namespace rt {
 namespace {
@@ -81,10 +82,35 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_read(const float4* __rest
     sink[tid] = (s.x + s.y) + (s.z + s.w);
 }
 
+// Self-test of the bounded wait the tensor-core kernels use: one block inits
+// an mbarrier expecting one arrival; with `arrive` thread 0 arrives, otherwise
+// nothing does; thread 0 then waits on the phase with mbar_wait_for. err
+// receives 0 when the phase completed, kSelfTestCode when the wait gave up.
+constexpr int kSelfTestCode = 199;
+
+__global__ void k_wait_selftest(unsigned long long limit_ns, int arrive, int* err) {
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = tc::smem_u32(&bar);
+    abort_flag = 0;
+    tc::mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *err = 0;
+    if (arrive) tc::mbar_arrive(b);
+    tc::mbar_wait_for(b, 0, &abort_flag, err, kSelfTestCode, limit_ns);
+}
+
 }  // namespace
 }  // namespace rt
 
 extern "C" {
+
+int rt_wait_selftest(int64_t limit_ns, int32_t arrive, int32_t* err, void* stream) {
+    if (!err || limit_ns < 1000 || limit_ns > 2000000000ll) return RT_EINVAL;
+    rt::k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>((unsigned long long)limit_ns, arrive ? 1 : 0, err);
+    return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ECUDA;
+}
 
 int rt_peak_fma(int32_t dtype, int32_t blocks, int32_t iters, void* sink, void* stream) {
     if (blocks < 1 || iters < 8 || (iters & 7) || !sink || (dtype != 0 && dtype != 1)) return RT_EINVAL;

@@ -59,22 +59,28 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for the phase of `parity` of the barrier at `bar` to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
+// Waits for the phase of `parity` of the barrier at `bar` to complete, for at
+// most limit_ns of global time without completion.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                              int code, unsigned long long limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 15) == 0) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) {
+            if (global_ns() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicExch(err, code);
                 return false;
             }
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
+    return mbar_wait_for(bar, parity, abort_flag, err, code, kWaitNs);
 }
 
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from

@@ -67,6 +67,16 @@ def test_rows_capacity_without_gpu(lib):
     assert lib.rt_rows_cap(None) == 0
 
 
+def test_wait_selftest_arguments_without_gpu(lib):
+    """The bounded-wait self-test validates before it enqueues: no error word, or
+    a limit outside 1 us .. 2 s, is RT_EINVAL."""
+    from paper_2511_18511_gb300 import _lib
+    word = ctypes.c_int32(0)
+    assert lib.rt_wait_selftest(10_000_000, 0, None, None) == _lib.RT_EINVAL
+    assert lib.rt_wait_selftest(10, 0, ctypes.byref(word), None) == _lib.RT_EINVAL
+    assert lib.rt_wait_selftest(3_000_000_000, 0, ctypes.byref(word), None) == _lib.RT_EINVAL
+
+
 def test_null_arguments_are_rejected_without_gpu(lib):
     from paper_2511_18511_gb300 import _lib
     assert lib.rt_ctx_create(None, 0) == _lib.RT_EINVAL
