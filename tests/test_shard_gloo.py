@@ -179,3 +179,57 @@ def test_sharded_tof_step_equals_unsharded(tmp_path, orc, world):
     r = orc.link(w.grid, w.c, w.tx, w.ring_radius, w.ds, fan_rays=64)
     full = orc.adjoint(w.grid, w.c, w.tx, w.ring_radius, w.ds, r["theta"], r["tof"] - meas["tof"])
     assert np.abs(got - full).max() <= 1e-13 * np.abs(full).max()
+
+
+def _failing_rank_worker(rank, world, port, out_dir):
+    """Rank 1 fails in its link before the step's all-reduce; rank 0 must see an
+    error from its all-reduce within the process group's timeout, not hang."""
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    n_tx = 8
+
+    def link(pairs, c):
+        if rank == 1:
+            raise RuntimeError("link failed on rank 1")
+        return np.zeros(len(pairs)), np.zeros(len(pairs))
+
+    def adjoint(pairs, c, theta, tof, tof_meas):
+        return torch.ones(16, dtype=torch.float64)
+
+    step = shard.ShardedToF(rank, world, n_tx, link=link, adjoint=adjoint)
+    t0 = time.time()
+    try:
+        step.step(None, np.zeros(len(step.pairs)))
+        outcome = "completed"
+    except Exception as exc:   # the failing rank's own error, or the survivor's collective error
+        outcome = type(exc).__name__
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(f"{outcome} {time.time() - t0:.2f}\n")
+    if rank == 1:
+        os._exit(0)            # leave without the collective, as a failed rank would
+
+
+def test_sharded_step_reports_a_failed_rank(tmp_path):
+    """Failure detection on the host: a rank that raises inside the step leaves
+    before the all-reduce; the other rank's all-reduce ends with an error within
+    the process group's timeout instead of hanging."""
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=60)
+    alive = [p.is_alive() for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert not any(alive), alive
+    r0 = (tmp_path / "rank0.txt").read_text().split()
+    r1 = (tmp_path / "rank1.txt").read_text().split()
+    print(f"rank 0: {r0}, rank 1: {r1}")
+    assert r1[0] == "RuntimeError"
+    assert r0[0] != "completed" and float(r0[1]) < 30.0
