@@ -181,7 +181,7 @@ def batch_leg(args, peaks, steps: int = 3, warmup: int = 3, fp64_every: int = 4)
         return a.elapsed_time(b)
 
     ms_sub32 = timed_sub("fp32c", kw)
-    ms_sub64 = timed_sub("fp64", dict(block_threads=128, step_unroll=1, blocks_per_sm=1, fan_ds=fan_ds))
+    ms_sub64 = timed_sub("fp64", dict(block_threads=128, step_unroll=16, blocks_per_sm=1, fan_ds=fan_ds))
     fp32 = peaks["fp32_tflops"]
     return {"metric": "linked rays/s (batched link+adjoint, 32 uneven instances, one persistent launch, CUDA graph)",
             "value": total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,

@@ -111,13 +111,14 @@ typedef struct {
                             ignored by the calls that take fixed angles */
     int32_t block_threads; /* rt_batch_run only: rays (threads) per block of the
                             persistent kernel, 0 (= 128), 64, 128 or 256 */
-    int32_t step_unroll;   /* rt_batch_run only: RK4 steps per work-queue check,
-                            0 (= 1), 1 or 2 */
+    int32_t step_unroll;   /* rt_batch_run only: RK4 steps a ray takes between
+                            work-queue checks, 0 (= 16), 1 or 16 */
     int32_t blocks_per_sm; /* rt_batch_run only: resident blocks per SM the kernel
                             variant is compiled for (fewer registers, more warps),
-                            0 = 512 / block_threads. FP32 variants (threads, unroll,
-                            blocks): (64,1,8) (64,1,12) (128,1,4) (128,1,5) (128,1,6)
-                            (128,2,4) (256,1,2) (256,1,3); FP64: (128,1,1) */
+                            0 = 512 / block_threads. FP32 variants (threads, steps,
+                            blocks): (64,16,8) (64,16,12) (128,16,4) (128,16,5)
+                            (128,16,6) (128,1,5) (256,16,2) (256,16,3); FP64:
+                            (128,16,1) */
     int32_t integrator;    /* enum rt_integrator: the ray stepper of every trace of
                             the ToF calls and of the rtborn_maps fans */
     int32_t interpolator;  /* enum rt_interpolator: the field sampler of rt_link,

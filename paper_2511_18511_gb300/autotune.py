@@ -15,8 +15,8 @@ import torch
 from . import build as _build
 
 # (rays per block, RK4 steps per queue check, resident blocks per SM)
-CANDIDATES = [(64, 1, 8), (64, 1, 12), (128, 1, 4), (128, 1, 5), (128, 1, 6), (128, 2, 4), (256, 1, 2),
-              (256, 1, 3)]
+CANDIDATES = [(64, 16, 8), (64, 16, 12), (128, 16, 4), (128, 16, 5), (128, 16, 6), (128, 1, 5), (256, 16, 2),
+              (256, 16, 3)]
 CACHE = os.path.join(_build.OUT, "autotune.json")
 
 
@@ -39,10 +39,12 @@ def tune_batch(instances, ds: float, tol: float = 1e-4, precision: str = "fp32c"
     from . import rt_batch_run
     key = f"{torch.cuda.get_device_name()}|{signature(instances, precision, fan_rays, fan_ds)}"
     cache = _load()
+    cands = CANDIDATES if precision == "fp32c" else [(128, 16, 1)]
     if use_cache and key in cache:
         c = cache[key]
-        return tuple(c["best"]), {tuple(map(int, k.split(","))): v for k, v in c["ms"].items()}
-    cands = CANDIDATES if precision == "fp32c" else [(128, 1, 1)]
+        timed = {tuple(map(int, k.split(","))): v for k, v in c["ms"].items()}
+        if set(timed) == set(cands):   # an entry timed over another variant set is stale
+            return tuple(c["best"]), timed
     times = {}
     for blk, unr, occ in cands:
         rt_batch_run(instances, ds, tol, precision=precision, fan_rays=fan_rays, block_threads=blk, step_unroll=unr,
@@ -60,7 +62,7 @@ def tune_batch(instances, ds: float, tol: float = 1e-4, precision: str = "fp32c"
             best = ms if best is None else min(best, ms)
         times[(blk, unr, occ)] = best
         if verbose:
-            print(f"autotune {blk} rays/block, unroll {unr}, {occ} blocks/SM: {best:.2f} ms")
+            print(f"autotune {blk} rays/block, {unr} steps per queue check, {occ} blocks/SM: {best:.2f} ms")
     choice = min(times, key=times.get)
     cache[key] = {"best": list(choice), "ms": {",".join(map(str, k)): v for k, v in times.items()}}
     os.makedirs(os.path.dirname(CACHE), exist_ok=True)

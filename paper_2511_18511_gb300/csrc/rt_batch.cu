@@ -92,7 +92,11 @@ __device__ __forceinline__ int find_inst(const BatchParams& P, long long q) {
 
 // MINB: resident blocks per SM the kernel is compiled for (it caps the
 // registers per thread at 64K / (BLOCK * MINB); fewer registers, more warps).
-template <typename T, int BLOCK, int UNROLL, int MINB>
+// STEPS: RK4 steps a lane takes between work-queue checks (its trace may end
+// earlier; the lane then idles to the end of the iteration). The queue check
+// and the warp's reconvergence cost a lone lane about a quarter of a step, so
+// batching steps shortens the launch's tail of few active lanes.
+template <typename T, int BLOCK, int STEPS, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB)
     k_batch(const __grid_constant__ BatchParams P, long long total, double tol, int max_iter, int fan_rays,
             unsigned long long* counters, unsigned long long* queue) {
@@ -169,44 +173,47 @@ __global__ void __launch_bounds__(BLOCK, MINB)
         }
         const InstDesc& d = P.d[inst];
         const Geom& G = d.G;
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            if (!trace_step(C, G, ts, sink)) continue;
-            const TraceOut o = trace_end(C, G, ts, L.xe, L.ye, L.xr, L.yr, sink);
-            steps += o.steps;
-            if (sink.on) {                    // adjoint retrace done
-                sink.on = false;
-                active = false;
+        bool ended = false;
+#pragma unroll 1
+        for (int u = 0; u < STEPS; ++u)
+            if (trace_step(C, G, ts, sink)) {
+                ended = true;
                 break;
             }
-            if (link_update(G, L, o, tol, max_iter, fan_rays >= 2 ? d.fan : nullptr, fan_rays)) {
-                const int k = L.k;
-                const int st = (L.best_d2 <= tol * tol) ? RT_RAY_OK
-                               : (L.best_d2 == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);
-                d.theta[k] = L.best_th;
-                d.tof[k] = L.best_T;
-                if (d.hit) { d.hit[2 * k] = L.best_hx; d.hit[2 * k + 1] = L.best_hy; }
-                if (d.iters) d.iters[k] = L.n_eval;
-                if (d.status) d.status[k] = st;
-                n_ok += st == RT_RAY_OK;
-                n_max += st == RT_RAY_MAXITER;
-                n_cap += st == RT_RAY_STEPCAP;
-                const double w = d.tof_ref ? L.best_T - d.tof_ref[k] : 0.0;
-                if (d.tof_ref && w != 0.0 && isfinite(w)) {
-                    sink.on = true;
-                    L.adj_g = d.g;
-                    L.adj_w = w;
-                    L.adj_nx = G.nx;
-                    L.adj_ny = G.ny;
-                    sink.acc.reset();
-                    trace_begin(ts, G, L.xe, L.ye, L.best_th);
-                } else {
-                    active = false;
-                    break;
-                }
+        if (!ended) continue;
+        const TraceOut o = trace_end(C, G, ts, L.xe, L.ye, L.xr, L.yr, sink);
+        steps += o.steps;
+        if (sink.on) {                    // adjoint retrace done
+            sink.on = false;
+            active = false;
+            continue;
+        }
+        if (link_update(G, L, o, tol, max_iter, fan_rays >= 2 ? d.fan : nullptr, fan_rays)) {
+            const int k = L.k;
+            const int st = (L.best_d2 <= tol * tol) ? RT_RAY_OK
+                           : (L.best_d2 == DBL_MAX ? RT_RAY_STEPCAP : RT_RAY_MAXITER);
+            d.theta[k] = L.best_th;
+            d.tof[k] = L.best_T;
+            if (d.hit) { d.hit[2 * k] = L.best_hx; d.hit[2 * k + 1] = L.best_hy; }
+            if (d.iters) d.iters[k] = L.n_eval;
+            if (d.status) d.status[k] = st;
+            n_ok += st == RT_RAY_OK;
+            n_max += st == RT_RAY_MAXITER;
+            n_cap += st == RT_RAY_STEPCAP;
+            const double w = d.tof_ref ? L.best_T - d.tof_ref[k] : 0.0;
+            if (d.tof_ref && w != 0.0 && isfinite(w)) {
+                sink.on = true;
+                L.adj_g = d.g;
+                L.adj_w = w;
+                L.adj_nx = G.nx;
+                L.adj_ny = G.ny;
+                sink.acc.reset();
+                trace_begin(ts, G, L.xe, L.ye, L.best_th);
             } else {
-                trace_begin(ts, G, L.xe, L.ye, L.next);
+                active = false;
             }
+        } else {
+            trace_begin(ts, G, L.xe, L.ye, L.next);
         }
     }
     if (counters) {
@@ -244,7 +251,7 @@ using rt::InstDesc;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <typename T, int BLOCK, int UNROLL, int MINB>
+template <typename T, int BLOCK, int STEPS, int MINB>
 cudaError_t launch_batch_kernel(const rt::BatchParams& D, long long total, double tol, int max_iter,
                                 int fan_rays, unsigned long long* counters, unsigned long long* queue,
                                 cudaStream_t s) {
@@ -256,35 +263,35 @@ cudaError_t launch_batch_kernel(const rt::BatchParams& D, long long total, doubl
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     int blocks = cache[dev].load(std::memory_order_relaxed);
     if (!blocks) {
-        e = cudaFuncSetAttribute(rt::k_batch<T, BLOCK, UNROLL, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(rt::k_batch<T, BLOCK, STEPS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt::k_batch<T, BLOCK, UNROLL, MINB>, BLOCK, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt::k_batch<T, BLOCK, STEPS, MINB>, BLOCK, smem);
         blocks = sms * (per_sm > 0 ? per_sm : 1);
         cache[dev].store(blocks, std::memory_order_relaxed);
     }
     const long long need = (total + BLOCK - 1) / BLOCK;
     const int nb = (int)(need < blocks ? need : blocks);
     if (nb <= 0) return cudaSuccess;
-    rt::k_batch<T, BLOCK, UNROLL, MINB><<<nb, BLOCK, smem, s>>>(D, total, tol, max_iter, fan_rays, counters, queue);
+    rt::k_batch<T, BLOCK, STEPS, MINB><<<nb, BLOCK, smem, s>>>(D, total, tol, max_iter, fan_rays, counters, queue);
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_batch(int prec, int block, int unroll, int bpsm, const rt::BatchParams& D, long long total,
+cudaError_t dispatch_batch(int prec, int block, int steps, int bpsm, const rt::BatchParams& D, long long total,
                            double tol, int max_iter, int fan_rays, unsigned long long* counters,
                            unsigned long long* queue, cudaStream_t s, bool* ok) {
     *ok = true;
     if (prec == RT_FP64) {
-        if (block == 128 && unroll == 1 && bpsm == 1)
-            return launch_batch_kernel<double, 128, 1, 1>(D, total, tol, max_iter, fan_rays, counters, queue, s);
+        if (block == 128 && steps == 16 && bpsm == 1)
+            return launch_batch_kernel<double, 128, 16, 1>(D, total, tol, max_iter, fan_rays, counters, queue, s);
     } else {
 #define RT_BATCH_CASE(B, U, M)                                                                                      \
-    if (block == B && unroll == U && bpsm == M)                                                                     \
+    if (block == B && steps == U && bpsm == M)                                                                      \
         return launch_batch_kernel<float, B, U, M>(D, total, tol, max_iter, fan_rays, counters, queue, s);
-        RT_BATCH_CASE(64, 1, 8) RT_BATCH_CASE(64, 1, 12) RT_BATCH_CASE(128, 1, 4) RT_BATCH_CASE(128, 1, 5)
-        RT_BATCH_CASE(128, 1, 6) RT_BATCH_CASE(128, 2, 4) RT_BATCH_CASE(256, 1, 2) RT_BATCH_CASE(256, 1, 3)
+        RT_BATCH_CASE(64, 16, 8) RT_BATCH_CASE(64, 16, 12) RT_BATCH_CASE(128, 16, 4) RT_BATCH_CASE(128, 16, 5)
+        RT_BATCH_CASE(128, 16, 6) RT_BATCH_CASE(128, 1, 5) RT_BATCH_CASE(256, 16, 2) RT_BATCH_CASE(256, 16, 3)
 #undef RT_BATCH_CASE
     }
     *ok = false;
@@ -311,7 +318,7 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
         return rt::set_error(ctx, RT_EINVAL, "fan_rays must be 0 or in [2, 65536]");
     if (opt->subfan_rays != 0) return rt::set_error(ctx, RT_EINVAL, "rt_batch_run links in one launch: subfan_rays must be 0");
     const int block = opt->block_threads ? opt->block_threads : 128;
-    const int unroll = opt->step_unroll ? opt->step_unroll : 1;
+    const int steps = opt->step_unroll ? opt->step_unroll : 16;
     const int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm
                                         : (opt->precision == RT_FP64 ? 1 : 512 / block);
     const size_t nb = rt::node_bytes(opt->precision);
@@ -394,7 +401,7 @@ extern "C" int rt_batch_run(rt_ctx* ctx, int32_t n_inst, const rt_instance* inst
     e = cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return rt::set_error(ctx, RT_ECUDA, std::string("queue reset: ") + cudaGetErrorString(e));
     bool ok = true;
-    e = dispatch_batch(opt->precision, block, unroll, bpsm, params, total, opt->tol_mm, opt->max_iter, opt->fan_rays,
+    e = dispatch_batch(opt->precision, block, steps, bpsm, params, total, opt->tol_mm, opt->max_iter, opt->fan_rays,
                        ctx->counters, reinterpret_cast<unsigned long long*>(ctx->queue), s, &ok);
     if (!ok)
         return rt::set_error(ctx, RT_EINVAL, "unsupported block_threads / step_unroll / blocks_per_sm combination");
