@@ -361,7 +361,7 @@ def born_leg(args, peaks, steps: int = 2, warmup: int = 1, variants: bool = Fals
                         "peak_basis": "measured FP32 FMA rate (rt_peak_fma)"},
            "roofline_apply": tc_roof("k_born_apply_tc (+ finish)", part[1]),
            "roofline_adjoint": tc_roof("k_born_dprep + k_born_adjoint_tc (+ finish)", part[2]),
-           "maps": {"rays": w.n_tx * w.fan_rays, "rk4_steps_both_passes": steps_per_call,
+           "maps": {"rays": w.n_tx * w.fan_rays, "rk4_steps": steps_per_call,
                     "rays_per_s": w.n_tx * w.fan_rays / (part[0] / 1e3)},
            # maps: pack, fan, unpack; apply: apply_tc, finish; adjoint: dprep, adjoint_tc, finish
            "gpu_launches_per_step": 3 + 2 + 3}
@@ -478,7 +478,7 @@ def run_profile_case(args):
         g = rt.rtborn_adjoint(maps, f, d)
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": w.name, "transducers": n, "fan_rays": w.fan_rays,
-                          "rk4_steps_both_passes": counts[7], "born_frequencies": f,
+                          "rk4_steps": counts[7], "born_frequencies": f,
                           "finite": bool(torch.isfinite(d).all()) and bool(torch.isfinite(g).all())}))
         return
     import paper_2511_18511_gb300 as rt
