@@ -78,7 +78,9 @@ def parse():
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "link_traffic.json"))
     ap.add_argument("--profile", type=int, default=0, metavar="N_EMIT",
                     help="case for ncu captures: twice rt_link + rt_tof_adjoint (fp32c) over the pairs of "
-                         "the first N_EMIT emitters of the workload, then exit")
+                         "the first N_EMIT emitters of the workload, then exit; with --workload batch, twice "
+                         "rt_batch_run over its first N_EMIT instances; with --workload born, the maps of the "
+                         "first N_EMIT transducers, then the Born apply and adjoint")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"],
                     help="precision of the --profile case")
     ap.add_argument("--workload", default="breast", choices=["breast", "batch", "born", "small", "fisheye"],
@@ -192,7 +194,9 @@ def batch_leg(args, peaks, steps: int = 3, warmup: int = 3, fp64_every: int = 4)
                        "autotune_ms": {",".join(map(str, k)): round(v, 2) for k, v in times.items()},
                        "l2": "flushed between timed replays (256 MB write)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32, "unit": "TFLOP/s",
-                         "frac": achieved / fp32, "traffic": None,
+                         "frac": achieved / fp32,
+                         "traffic": (_traffic(os.path.join(ROOT, "profiles", "batch_traffic.json"), BATCH_HASH_FILES)
+                                     if tuple(best) == BATCH_PROFILE_VARIANT else None),
                          "kernel": "graph replay (pack + fan + k_batch + finish)", "flop_per_rk4_step": FLOP_PER_STEP,
                          "rk4_steps_per_launch": counts[7], "peak_basis": "measured FP32 FMA rate (rt_peak_fma)"},
             "link": {"all_linked": ok, "status_counts": counts[:7]},
@@ -461,6 +465,27 @@ def run_profile_case(args):
     with --workload born, rtborn_maps on the first N_EMIT transducers, then the
     Born apply and adjoint (tensor-core path) of those maps at two frequencies."""
     import torch
+    if args.workload == "batch":
+        import paper_2511_18511_gb300 as rt
+        from paper_2511_18511_gb300 import phantoms as P
+        ws = P.cfg_batch()[:args.profile]
+        insts = [rt.BatchInstance.create(rt.Problem.create(w.grid, w.c, w.tx, w.ring_radius)) for w in ws]
+        for b in insts:                  # "measured" times: the same media 0.5 % faster, as the batch leg
+            c0 = b.prob.c.clone()
+            b.prob.c.mul_(1.005)
+            rt.rt_batch_run([b], ws[0].ds)
+            b.prob.c.copy_(c0)
+            b.tof_ref = b.tof.clone()
+            b.g_c = torch.empty_like(b.prob.c)
+        kw = dict(zip(("block_threads", "step_unroll", "blocks_per_sm"), BATCH_PROFILE_VARIANT))
+        for _ in range(2):
+            rt.rt_batch_run(insts, ws[0].ds, fan_ds=0.5 * ws[0].grid.h, **kw)
+        torch.cuda.synchronize()
+        ok, counts = rt.rt_status_counts()
+        print(json.dumps({"profile_case": "batch32_uneven", "instances": len(insts),
+                          "pairs": sum(b.prob.n_pairs for b in insts), "variant": list(BATCH_PROFILE_VARIANT),
+                          "all_linked": ok, "rk4_steps": counts[7]}))
+        return
     if args.workload == "born":
         import paper_2511_18511_gb300 as rt
         from paper_2511_18511_gb300 import phantoms as P
@@ -1045,6 +1070,11 @@ def _kernel_hash(files=("rt_trace.cuh", "rt_link.cuh", "rt_bspline.cuh", "rt_ray
 
 
 BORN_HASH_FILES = ("rt_trace.cuh", "rt_bspline.cuh", "rt_born.cu")
+BATCH_HASH_FILES = ("rt_trace.cuh", "rt_link.cuh", "rt_batch.cu")
+# the k_batch variant (rays per block, RK4 steps per queue check, blocks per SM)
+# of the committed batch captures; the batch leg reports their traffic only when
+# the autotuner picked this variant
+BATCH_PROFILE_VARIANT = (128, 16, 5)
 
 
 def _traffic(path: str, files) -> "int | None":
