@@ -184,10 +184,13 @@ __global__ void __launch_bounds__(kBlock) k_fan(Geom G, const typename Samp<T, I
 // The iteration's bookkeeping (queue fetch, reconvergence of the warp) cost a
 // lone lane about 85 ns per step at one step per iteration: 537 against 363 ns
 // per RK4 step for the plain traced-ray kernel; at 16 steps it is 428 ns.
-// The recording variant keeps a run accumulator per lane: compiled for 5
-// resident blocks per SM (102 registers) instead of 6.
+// Resident blocks per SM the link kernel is compiled for. The recording
+// variant, which keeps a run accumulator per lane, runs 4 blocks (128
+// registers): 53.0 against 54.5 ms at 5 on the cold breast workload. The plain
+// FP32 link stays at 6 (80 registers): at 5 its cold link was no faster and
+// its warm start (one trace per pair, throughput-bound) slower.
 template <typename T, int I, bool REC> struct LinkBlocks { static constexpr int v = Occ<T, I>::blocks; };
-template <typename T, int I> struct LinkBlocks<T, I, true> { static constexpr int v = 5; };
+template <typename T, int I> struct LinkBlocks<T, I, true> { static constexpr int v = 4; };
 
 // RK4 steps per loop iteration of k_link (measured on the breast workload:
 // 1 -> 60.6 ms, 4 -> 55.1, 8 -> 54.5, 16 -> 53.6 for the recording link)
