@@ -1,6 +1,7 @@
 // rt_ray.cu — kernels of the ToF path: field packing, shooting-method linking
 // with the fused travel time, travel time at fixed angles, the adjoint scatter
 // and the explicit system-matrix rows.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cfloat>
@@ -201,7 +202,8 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
                                                      double tol, int max_iter, double* theta, double* tof,
                                                      double* hit, int32_t* status, int32_t* iters,
                                                      unsigned long long* counters, int* queue, int fan_rays,
-                                                     const double* __restrict__ fan, RowRec rec, LinkRound rd) {
+                                                     const double* __restrict__ fan, RowRec rec, LinkRound rd,
+                                                     int lanes) {
     __shared__ LinkState sh[kLinkBlock];
     // per-block tallies (status counts, RK4 steps): updated once per trace, so
     // they live in shared memory rather than in the step loop's registers
@@ -220,6 +222,10 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
         ns.begin(rec.runs);
     }
     bool active = false;
+    // Only the first `lanes` lanes of each warp take pairs (all 32 unless the
+    // problem has fewer pairs than the grid has lanes): a warp of few rays
+    // steps at a lower latency than a full one.
+    if ((threadIdx.x & 31) >= lanes) goto done;
     for (;;) {
         if (ROUNDS && !active && rd.aside_in) {
             // resume a pair set aside by the previous round (R12: refined first)
@@ -307,6 +313,7 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
             }
         }
     }
+done:
     __syncthreads();
     if (counters && threadIdx.x == 0) {
         if (tally[0]) atomicAdd(&counters[RT_RAY_OK], tally[0]);
@@ -378,10 +385,19 @@ static void link_impl(const Geom& G, const void* field, double tol, int max_iter
                       double* hit, int32_t* status, int32_t* iters, unsigned long long* counters, int* queue,
                       int fan_rays, double* fan, int slot, cudaStream_t s, const RowRec& rec = RowRec{},
                       const LinkRound& rd = LinkRound{}) {
-    const int nb = min(persistent_blocks(k_link<T, I, REC, ROUNDS>, slot), (G.n_pairs + kLinkBlock - 1) / kLinkBlock);
+    // With fewer pairs than the persistent grid has lanes, the pairs are
+    // spread over all of its warps, ceil(pairs / warps) lanes each, rather
+    // than packed 32 to a warp on a few SMs (the linking is per pair, so the
+    // results do not depend on the lanes that run them).
+    const int pb = persistent_blocks(k_link<T, I, REC, ROUNDS>, slot);
+    const long long warps = (long long)pb * (kLinkBlock / 32);
+    const long long pairs = G.n_pairs;   // an upper bound of the pairs a rounds launch resumes
+    const int lanes = (int)std::min<long long>(32, std::max<long long>(1, (pairs + warps - 1) / warps));
+    const long long per_block = (long long)lanes * (kLinkBlock / 32);
+    const int nb = (int)std::min<long long>(pb, (pairs + per_block - 1) / per_block);
     k_link<T, I, REC, ROUNDS><<<nb, kLinkBlock, 0, s>>>(G, (const typename Samp<T, I>::Field*)field, tol, max_iter,
                                                         theta, tof, hit, status, iters, counters, queue, fan_rays,
-                                                        fan, rec, rd);
+                                                        fan, rec, rd, lanes);
 }
 
 size_t link_state_bytes() { return sizeof(LinkState); }
