@@ -139,15 +139,15 @@ typedef struct {
                             predict the third angle (inverse cubic through the four
                             around the root, else Regula Falsi in the narrowed
                             bracket; reading R12, the oracle's subfan) and the link
-                            runs in rounds: one trace per pair, the second traces,
-                            the sub-fan, the rest. Only predictions change: the
-                            linked rays stay those of the straight start. On the
-                            1024^2 / 512-ring breast workload the rounds cost more
-                            than they save (77.9 against 60.7 ms with 8 rays): a
-                            round of a few hundred traces lasts as long as one ray
-                            marched by warps whose 32 lanes hold unrelated rays,
-                            while the single launch runs those chains beside the
-                            bulk. An experimental option: on the fish-eye lens with
+                            runs in rounds: every pair's first two traces in one
+                            persistent launch, the sub-fan of the pairs still
+                            unlinked, then their remaining traces, spread over
+                            all warps. Only predictions change: the linked rays
+                            stay those of the straight start. On the 1024^2 /
+                            512-ring breast workload the rounds cost more than
+                            they save (63.7 against 52.7 ms with 8 rays): the
+                            last round's chains of up to four more traces run
+                            after the bulk instead of beside it. An experimental option: on the fish-eye lens with
                             M = 32, 3 of 65,280 near-tangent pairs (adjacent
                             transducers, 4-6 FP32 traces where the oracle needs 2)
                             end at max_iter, the narrowed bracket holding a jump

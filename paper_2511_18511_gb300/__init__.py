@@ -138,8 +138,9 @@ def rt_link(prob: Problem, ds: float, tol: float = 1e-4, max_iter: int = 30, pre
     traced at step fan_ds (0 = ds), their launch angles follow ds. integrator: "rk4" or
     "heun" (the paper's default stepper); interpolator: "bilinear" or "bspline"
     (the interpolating cubic B-spline, Sec. 3.3.1). subfan_rays > 0: link in
-    rounds, with that many rays refining the third angle of a fan-started pair
-    whose second trace missed."""
+    rounds (every pair's first two traces, the sub-fan, the rest), with that many
+    rays refining the third angle of a fan-started pair whose second trace
+    missed."""
     ctx = ctx or default_context(prob.c.device.index)
     dev = prob.c.device
     n = prob.n_pairs

@@ -133,8 +133,8 @@ int ensure_fan(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, cudaS
     return RT_OK;
 }
 
-// Workspace of the R12 rounds (opt->subfan_rays > 0): two set-aside state
-// arrays, the sub-fan misfits and the round counters, 256-byte aligned parts.
+// Workspace of the R12 rounds (opt->subfan_rays > 0): the set-aside state
+// array, the sub-fan misfits and the round counters, 256-byte aligned parts.
 static int ensure_link_ws(rt_ctx* ctx, const rt_problem* prob, const rt_options* opt, cudaStream_t s,
                           rt::LinkWork* W) {
     W->subfan = 0;
@@ -146,7 +146,7 @@ static int ensure_link_ws(rt_ctx* ctx, const rt_problem* prob, const rt_options*
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t np = (size_t)prob->n_pairs;
     const size_t st = al(rt::link_state_bytes() * np), sb = al(sizeof(double) * np * (size_t)opt->subfan_rays);
-    const size_t need = 2 * st + sb + 256;
+    const size_t need = st + sb + 256;
     if (ctx->link_ws_bytes < need) {
         if (capturing(s)) return fail(ctx, RT_EINVAL, "link workspace too small during stream capture");
         if (ctx->link_ws) cudaFree(ctx->link_ws);
@@ -157,10 +157,9 @@ static int ensure_link_ws(rt_ctx* ctx, const rt_problem* prob, const rt_options*
     }
     char* b = (char*)ctx->link_ws;
     W->subfan = opt->subfan_rays;
-    W->aside_a = (rt::LinkState*)b;
-    W->aside_b = (rt::LinkState*)(b + st);
-    W->sub = (double*)(b + 2 * st);
-    W->ctr = (int*)(b + 2 * st + sb);
+    W->aside = (rt::LinkState*)b;
+    W->sub = (double*)(b + st);
+    W->ctr = (int*)(b + st + sb);
     return RT_OK;
 }
 

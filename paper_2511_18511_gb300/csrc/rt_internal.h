@@ -78,15 +78,14 @@ struct LinkState;
 // misfits [n_pairs * subfan] and five int counters.
 struct LinkWork {
     int subfan;
-    LinkState* aside_a;
-    LinkState* aside_b;
+    LinkState* aside;
     double* sub;
     int* ctr;
 };
 size_t link_state_bytes();
 // fan_ds: the fan's tracing step (0 = G.ds); its launch angles follow G.ds.
 // rec: record the rows of the system matrix (FP32-compensated bilinear only).
-// W (subfan > 0): link in rounds (one trace, a second, the sub-fan, the rest).
+// W (subfan > 0): link in rounds (two traces, the sub-fan, the rest).
 cudaError_t launch_link(const Geom& G, const void* field, int prec, double tol, int max_iter,
                         double* theta, double* tof, double* hit, int32_t* status, int32_t* iters,
                         unsigned long long* counters, int* queue, int fan_rays, double fan_ds, double* fan,

@@ -224,7 +224,12 @@ __global__ void __launch_bounds__(kLinkBlock, LinkBlocks<T, I, REC>::v) k_link(G
     bool active = false;
     // Only the first `lanes` lanes of each warp take pairs (all 32 unless the
     // problem has fewer pairs than the grid has lanes): a warp of few rays
-    // steps at a lower latency than a full one.
+    // steps at a lower latency than a full one. A round that resumes set-aside
+    // pairs learns their number only here, so it spreads them itself.
+    if (ROUNDS && rd.aside_in) {
+        const long long warps = (long long)gridDim.x * (kLinkBlock / 32);
+        lanes = (int)min(32LL, max(1LL, ((long long)n_in + warps - 1) / warps));
+    }
     if ((threadIdx.x & 31) >= lanes) goto done;
     for (;;) {
         if (ROUNDS && !active && rd.aside_in) {
@@ -437,24 +442,25 @@ static cudaError_t link_rounds(const Geom& G, const void* field, double tol, int
                                double* tof, double* hit, int32_t* status, int32_t* iters,
                                unsigned long long* counters, int fan_rays, double fan_ds, double* fan, int slot,
                                const LinkWork& W, cudaStream_t s, const RowRec& rec) {
-    // counters: queues of the three rounds, then the two set-aside counts
-    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 5 * sizeof(int), s);
+    // counters: queues of the two rounds, then the set-aside count. The first
+    // round runs every pair's first two traces in one persistent launch (the
+    // second traces fill the first ones' drain) and sets aside the pairs the
+    // second trace left unlinked; after their sub-fan the second round resumes
+    // them, spread over all warps.
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, 3 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    LinkRound r1{1, W.aside_a, W.ctr + 3, nullptr, nullptr, nullptr, 0};
+    LinkRound r1{2, W.aside, W.ctr + 2, nullptr, nullptr, nullptr, 0};
     link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr, fan_rays,
                                fan, slot, s, rec, r1);
-    LinkRound r2{2, W.aside_b, W.ctr + 4, W.aside_a, W.ctr + 3, nullptr, 0};
-    link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr + 1,
-                               fan_rays, fan, slot, s, rec, r2);
     const Geom Gf = with_step(G, fan_ds > 0 ? fan_ds : G.ds);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_subfan<T, I><<<(unsigned)(sms > 0 ? sms * 8 : 1216), kBlock, 0, s>>>(
-        Gf, (const typename Samp<T, I>::Field*)field, W.aside_b, W.ctr + 4, W.subfan, W.sub, counters);
-    LinkRound r3{0, nullptr, nullptr, W.aside_b, W.ctr + 4, W.sub, W.subfan};
-    link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr + 2,
-                               fan_rays, fan, slot, s, rec, r3);
+        Gf, (const typename Samp<T, I>::Field*)field, W.aside, W.ctr + 2, W.subfan, W.sub, counters);
+    LinkRound r2{0, nullptr, nullptr, W.aside, W.ctr + 2, W.sub, W.subfan};
+    link_impl<T, I, REC, true>(G, field, tol, max_iter, theta, tof, hit, status, iters, counters, W.ctr + 1,
+                               fan_rays, fan, slot, s, rec, r2);
     return cudaGetLastError();
 }
 
