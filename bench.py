@@ -911,7 +911,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        # one fixed problem whatever the number of ranks (each takes its emitter block)
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "grid": f"{w.grid.nx}x{w.grid.ny}", "h_mm": w.grid.h, "ring": w.n_tx,
                    "ring_radius_mm": w.ring_radius, "pairs": n_all, "ds_mm": w.ds, "tol_mm": w.tol,
                    "start": f"cold: fan of {BREAST_FAN} rays per transducer traced at {FAN_DS} mm",
