@@ -84,6 +84,9 @@ def load(path: str):
                               C.c_double, _dp, _dp, _dp, C.c_int32]
     L.orc_num_threads.argtypes = []
     L.orc_set_integrator.argtypes = [C.c_int32]
+    L.orc_set_link_rule.argtypes = [C.c_int32]
+    L.orc_r13_angle.argtypes = [_dp, _dp, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                C.c_double, C.c_double, _dp]
     L.orc_set_interpolator.argtypes = [C.c_int32]
     L.orc_bspline_coef.argtypes = [G, _dp, _dp, C.c_int32]
     L.orc_fan_angles.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, _dp, _dp]
@@ -175,6 +178,25 @@ class integrator:
 
     def __exit__(self, *exc):
         lib().orc_set_integrator(0)
+
+
+LINK_RULES = {"r8": 0, "r13": 1}
+
+
+class link_rule:
+    """Context manager: link fan-started pairs with another rule ("r8" default,
+    "r13": the fan model corrected through the traces for the second and third
+    angles)."""
+
+    def __init__(self, name: str):
+        self.k = LINK_RULES[name]
+
+    def __enter__(self):
+        _check(lib().orc_set_link_rule(self.k), "set_link_rule")
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_link_rule(0)
 
 
 INTERPOLATORS = {"bilinear": 0, "bspline": 1}
@@ -282,6 +304,18 @@ def link(grid, c_mps, tx, R, ds, tol=1e-4, max_iter=30, pairs=None, theta0=None,
                         _i(iters), nthreads)
     _check(rc, "link")
     return dict(theta=theta, tof=tof, hit=hit, status=status, iters=iters)
+
+
+def r13_angle(t, m, x1, m1, lo, hi, x2=None, m2=None):
+    """R13: the root in (lo, hi) of the fan rays' interpolating polynomial
+    moved onto the trace (x1, m1), or onto both traces when (x2, m2) is given
+    (NaN when the moved polynomial does not change sign there)."""
+    t, m = _f64(t), _f64(m)
+    out = np.empty(1)
+    two = x2 is not None
+    _check(lib().orc_r13_angle(_d(t), _d(m), t.size, float(x1), float(m1), float(x2) if two else 0.0,
+                               float(m2) if two else 0.0, int(two), float(lo), float(hi), _d(out)), "r13_angle")
+    return float(out[0])
 
 
 def subfan_angles(ta, tb, M):

@@ -43,6 +43,8 @@
  *      halving; at most max_iter traces (the probe counts); the reported ray
  *      is the evaluated one closest to the receiver;
  *   R8 fan start for cold starts (optional, see link_pair_fan);
+ *   R13 corrected fan model for the second and third angles of a fan start
+ *      (optional, orc_set_link_rule(1), see link_pair_fan);
  *   S1-S4 cubic B-spline option (orc_set_interpolator(1); Sec. 3.3.1's second
  *      scheme, the one behind the paper's Sec. 4 experiments): S1 the spline
  *      interpolates the nodal values: its control coefficients, one per node,
@@ -599,8 +601,107 @@ static void link_pair(const Field* F, double R, const double* xe, const double* 
  * inside), else the Regula-Falsi point of the interval; the secant then starts
  * from the interval end of smaller |misfit|. When no crossing holds it, the
  * plain rule's angle is traced unchanged. Like the fan, the sub-fan only
- * predicts; the linking traces keep ds. */
+ * predicts; the linking traces keep ds.
+ *
+ * R13 corrected fan model (an option, orc_set_link_rule(1); not combined with
+ * R12). The fan's misfits, traced at fan_ds, carry the shape of the misfit
+ * around the root (its curvature over the fan spacing) but are offset from the
+ * misfit of the linking traces at ds. The model is the forward interpolating
+ * polynomial P(theta) through the widest window of 8, 6, 4 or 2 fan rays
+ * centred on the bracketing interval whose misfits exist and change strictly
+ * monotonically. When the first trace (theta_1, m_1) misses, the second angle
+ * is the root of P(theta) + a with a = m_1 - P(theta_1) (the model moved onto
+ * the trace); when the second trace (theta_2, m_2) misses too, the third
+ * angle is the root of P(theta) + a + b (theta - theta_1), the offset a and
+ * tilt b fitted through both traces. Each root is sought in the current
+ * bracket, where the model must change sign; otherwise, or when a trace did
+ * not reach the ring, the R8 rule picks the angle. From the fourth angle on
+ * the secant continues as in R8. Like the fan, the model only predicts. */
 static double fan_theta(double a_min, double step, int k) { return a_min + k * step; }
+
+static int g_link_rule = 0;
+
+int orc_set_link_rule(int32_t k) {
+    if (k != 0 && k != 1) return ORC_EINVAL;
+    g_link_rule = k;
+    return ORC_OK;
+}
+
+int orc_get_link_rule(void) { return g_link_rule; }
+
+/* Forward interpolating polynomial through (t[q], m[q]), q < n, and its
+ * derivative at x (Lagrange form, derivative by the product rule). */
+static void poly_eval(const double* t, const double* m, int n, double x, double* p, double* dp) {
+    double v = 0.0, d = 0.0;
+    for (int a = 0; a < n; ++a) {
+        double l = 1.0;
+        for (int b = 0; b < n; ++b)
+            if (b != a) l *= (x - t[b]) / (t[a] - t[b]);
+        v += l * m[a];
+        double dl = 0.0;
+        for (int k = 0; k < n; ++k) {
+            if (k == a) continue;
+            double term = 1.0 / (t[a] - t[k]);
+            for (int b = 0; b < n; ++b)
+                if (b != a && b != k) term *= (x - t[b]) / (t[a] - t[b]);
+            dl += term;
+        }
+        d += dl * m[a];
+    }
+    *p = v;
+    *dp = d;
+}
+
+/* R13: root in (lo, hi) of g(x) = P(x) + a + b (x - x1), P the fan
+ * polynomial, by Newton steps kept inside the shrinking sign-change interval
+ * (bisection when a step leaves it); NAN when g does not change sign over
+ * (lo, hi). */
+static double r13_root(const double* t, const double* m, int n, double a, double b, double x1, double lo,
+                       double hi) {
+    double glo, ghi, d;
+    poly_eval(t, m, n, lo, &glo, &d);
+    glo += a + b * (lo - x1);
+    poly_eval(t, m, n, hi, &ghi, &d);
+    ghi += a + b * (hi - x1);
+    if (!(glo * ghi < 0.0)) return NAN;
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        double g, dg;
+        poly_eval(t, m, n, x, &g, &dg);
+        g += a + b * (x - x1);
+        dg += b;
+        if (g == 0.0) return x;
+        if ((g < 0.0) == (glo < 0.0)) { lo = x; glo = g; } else { hi = x; ghi = g; }
+        double xn = (dg != 0.0) ? x - g / dg : NAN;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (fabs(xn - x) <= 1e-15 * fmax(1.0, fabs(x))) return xn;
+        x = xn;
+    }
+    return x;
+}
+
+/* R13 angle: the fan model through the trace (x1, m1) (offset a) or, with
+ * two = 1, through (x1, m1) and (x2, m2) (offset a and tilt b), and its root
+ * in (lo, hi); NAN when the model does not change sign there. */
+static double r13_angle(const double* t, const double* m, int n, double x1, double m1, double x2, double m2,
+                        int two, double lo, double hi) {
+    double p1, p2, d;
+    poly_eval(t, m, n, x1, &p1, &d);
+    const double a = m1 - p1;
+    double b = 0.0;
+    if (two) {
+        poly_eval(t, m, n, x2, &p2, &d);
+        b = ((m2 - p2) - a) / (x2 - x1);
+    }
+    return r13_root(t, m, n, a, b, x1, lo, hi);
+}
+
+int orc_r13_angle(const double* t, const double* m, int32_t n, double x1, double m1, double x2, double m2,
+                  int32_t two, double lo, double hi, double* out) {
+    if (!t || !m || !out || n < 2 || n > 8) return ORC_EINVAL;
+    *out = r13_angle(t, m, n, x1, m1, x2, m2, two, lo, hi);
+    return ORC_OK;
+}
 
 /* Value at m = 0 of the polynomial theta(m) through the n points (m_q, t_q),
  * Lagrange form. */
@@ -808,8 +909,15 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
         const double v = inverse_poly_root(t4, m4, 4);
         if (v > fmin(t0, t1) && v < fmax(t0, t1)) th0 = v;
     }
+    /* R13 model window: the widest monotone one of 8, 6, 4, 2 rays around (k0, k0+1) */
+    double tw[8], mw[8];
+    int nw = 0;
+    if (g_link_rule == 1 && subfan == 0)
+        for (int n = 8; n >= 2 && !nw; n -= 2)
+            if (fan_points(psi, K, k0 - (n / 2 - 1), n, a_min, step, R, psi_r, tw, mw)) nw = n;
     if (!(th0 > fmin(B.ta, B.tb) && th0 < fmax(B.ta, B.tb))) th0 = 0.5 * (B.ta + B.tb);
     Eval prev, cur;
+    memset(&prev, 0, sizeof prev);   /* a fan interval end, not a trace */
     prev.theta = (fabs(m0) <= fabs(m1)) ? t0 : t1;
     prev.m = (fabs(m0) <= fabs(m1)) ? m0 : m1;
     cur = prev;
@@ -823,6 +931,7 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
             if (!(isfinite(c3) && c3 > fmin(B.ta, B.tb) && c3 < fmax(B.ta, B.tb)))
                 c3 = (B.ta * B.fb - B.tb * B.fa) / (B.fb - B.fa);
             Eval s0;
+            memset(&s0, 0, sizeof s0);
             double th3;
             if (subfan_refine(F, R, xe, phi_e, psi_r, fan_ds, subfan, c3, &B, &th3, &s0)) {
                 next = th3;
@@ -832,13 +941,22 @@ static void link_pair_fan(const Field* F, double R, const double* xe, const doub
                 next = c3;
             }
         } else if (n_eval > 0) {
-            if (n_eval == 1 && ok4 && !(cur.tr.flags & 3)) {
-                const double t5[5] = {cur.theta, t4[0], t4[1], t4[2], t4[3]};
-                const double m5[5] = {cur.m, m4[0], m4[1], m4[2], m4[3]};
-                next = inverse_poly_root(t5, m5, 5);
-            } else {
-                double den = cur.m - prev.m;
-                next = (den != 0.0) ? cur.theta - cur.m * (cur.theta - prev.theta) / den : NAN;
+            next = NAN;
+            /* R13: the fan model through the first trace (offset a), then through both (tilt b) */
+            if (nw && n_eval <= 2 && !(cur.tr.flags & 3) && (n_eval == 1 || !(prev.tr.flags & 3))) {
+                const double lo = fmin(B.ta, B.tb), hi = fmax(B.ta, B.tb);
+                next = (n_eval == 1) ? r13_angle(tw, mw, nw, cur.theta, cur.m, 0.0, 0.0, 0, lo, hi)
+                                     : r13_angle(tw, mw, nw, prev.theta, prev.m, cur.theta, cur.m, 1, lo, hi);
+            }
+            if (!isfinite(next)) {   /* no R13 angle: the R8 rule */
+                if (n_eval == 1 && ok4 && !(cur.tr.flags & 3)) {
+                    const double t5[5] = {cur.theta, t4[0], t4[1], t4[2], t4[3]};
+                    const double m5[5] = {cur.m, m4[0], m4[1], m4[2], m4[3]};
+                    next = inverse_poly_root(t5, m5, 5);
+                } else {
+                    double den = cur.m - prev.m;
+                    next = (den != 0.0) ? cur.theta - cur.m * (cur.theta - prev.theta) / den : NAN;
+                }
             }
             if (!(isfinite(next) && next > fmin(B.ta, B.tb) && next < fmax(B.ta, B.tb)))
                 next = (B.ta * B.fb - B.tb * B.fa) / (B.fb - B.fa);

@@ -124,6 +124,19 @@ int orc_set_interpolator(int32_t k);
 int orc_get_interpolator(void);
 int orc_get_integrator(void);
 
+/* Linking rule of every later fan-started orc_link (process-wide): 0 = R8
+ * (default), 1 = R13, the fan model corrected through the traces for the
+ * second and third angles. Returns ORC_EINVAL for other values. */
+int orc_set_link_rule(int32_t k);
+int orc_get_link_rule(void);
+
+/* R13's angle from the fan rays (t[q], m[q]), q < n <= 8: the root in (lo, hi)
+ * of their interpolating polynomial moved onto the trace (x1, m1) by an
+ * offset, or with two = 1 onto both traces (x1, m1), (x2, m2) by an offset and
+ * a tilt; *out = NAN when the moved polynomial does not change sign there. */
+int orc_r13_angle(const double* t, const double* m, int32_t n, double x1, double m1, double x2, double m2,
+                  int32_t two, double lo, double hi, double* out);
+
 /* Control coefficients a = P^-1 f of the interpolating cubic B-spline of the
  * nodal field f[ny*nx] (mirror boundary; P is the spline's value at the nodes,
  * one tridiagonal (1, 4, 1)/6 factor per axis), or a = P^-T f with transpose.

@@ -18,6 +18,7 @@ from tests import test_oracle_born_bspline_pins as bbpins
 from tests import test_oracle_born_pins as bpins
 from tests import test_oracle_bspline_pins as spins
 from tests import test_oracle_pins as pins
+from tests import test_oracle_r13_pins as r13pins
 
 MUTANTS = {
     "rk4_weight": ("2.0 * k2[q] + 2.0 * k3[q]", "k2[q] + 2.0 * k3[q]"),
@@ -213,6 +214,26 @@ BORN_PINS = [
 ]
 
 
+# reading R13 (an option of the fan-started linking), with its own pins
+R13_MUTANTS = {
+    "r13_offset_sign": ("    const double a = m1 - p1;\n", "    const double a = p1 - m1;\n"),
+    "r13_tilt_dropped": ("        b = ((m2 - p2) - a) / (x2 - x1);", "        b = 0.0 * ((m2 - p2) - a) / (x2 - x1);"),
+    "r13_window_off_centre": ("if (fan_points(psi, K, k0 - (n / 2 - 1), n, a_min, step, R, psi_r, tw, mw)) nw = n;",
+                              "if (fan_points(psi, K, k0 - n / 2, n, a_min, step, R, psi_r, tw, mw)) nw = n;"),
+    "r13_forward_poly_node_dropped": ("if (b != a) l *= (x - t[b]) / (t[a] - t[b]);",
+                                      "if (b != a && b != n - 1) l *= (x - t[b]) / (t[a] - t[b]);"),
+    "r13_third_angle_through_one_trace": ("r13_angle(tw, mw, nw, prev.theta, prev.m, cur.theta, cur.m, 1, lo, hi)",
+                                          "r13_angle(tw, mw, nw, cur.theta, cur.m, 0.0, 0.0, 0, lo, hi)"),
+}
+
+R13_PINS = [
+    lambda orc: r13pins.test_r13_angle_exact_for_moved_cubic(orc, 1.0, 8),
+    lambda orc: r13pins.test_r13_angle_exact_for_moved_cubic(orc, -1.0, 4),
+    r13pins.test_r13_angle_linear_window_and_no_sign_change,
+    r13pins.test_r13_links_the_same_rays_in_fewer_traces,
+]
+
+
 def _compile_mutant(tmp_path, name, target, old, new):
     here = os.path.dirname(oracle.__file__)
     src = open(os.path.join(here, target)).read()
@@ -242,6 +263,14 @@ def test_mutant_is_caught(name, tmp_path):
     L = _compile_mutant(tmp_path, name, "oracle.c", old, new)
     if _survives(L, PINS):
         pytest.fail(f"mutant {name} survived every pin")
+
+
+@pytest.mark.parametrize("name", sorted(R13_MUTANTS))
+def test_r13_mutant_is_caught(name, tmp_path):
+    old, new = R13_MUTANTS[name]
+    L = _compile_mutant(tmp_path, name, "oracle.c", old, new)
+    if _survives(L, R13_PINS):
+        pytest.fail(f"mutant {name} survived every R13 pin")
 
 
 @pytest.mark.parametrize("name", sorted(BSPLINE_MUTANTS))
